@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the NEP MD step (cell list -> neighbours -> descriptors -> network ->
+forces + virials -> FP64 reductions -> velocity-Verlet) on the 100,000-bead CG water
+system, reported as bead-steps/s and ns/day.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one velocity-Verlet step of the whole system.  Timed region: K steps, each
+bracketed by CUDA events on the launch stream, with a 256 MiB write between steps to
+flush the 126 MB L2 (the step's working set, ~115 MB, is smaller than L2).  Inputs are
+resident in HBM before timing.  With N > 1 (torchrun) every rank runs an independent
+replica (the method shards by independent systems; no collective on the data path);
+value = all ranks' bead-steps / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample
+of the same workload on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2603_01234_gb300 import inputs  # noqa: E402
+
+METRIC = "bead-steps/s (100k-bead CG water MD step)"
+UNIT = "bead-steps/s"
+DT_FS = 10.0
+FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock"
+
+
+def workload():
+    model = inputs.random_model(n_types=1, n_desc_radial=5, n_desc_angular=4, n_basis_radial=8,
+                                n_basis_angular=8, l_max=4, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
+    system = inputs.water_box(100_000, density=0.0334, seed=1001)
+    system.masses = np.array([18.0])
+    vel = inputs.maxwell_boltzmann(system, 300.0, seed=7)
+    return model, system, vel
+
+
+def config_dict(system):
+    return {"workload": "CG water, 100000 beads, 1 type, density 0.0334/A^3, periodic cube 144.1 A",
+            "model": "NEP4-form random weights N(0,0.1): n_R=5, n_A=4, K_R=K_A=8, l_max=4, H=30, r_c 8/5 A",
+            "n_beads": system.n, "dt_fs": DT_FS, "integrator": "velocity-Verlet NVE (FP64)",
+            "precision": "FP32 descriptors/network/forces, FP64 reductions+integration",
+            "l2": "flushed between timed steps (256 MiB write); working set < L2",
+            "data": "synthetic (seeded jittered lattice, Maxwell-Boltzmann 300 K)"}
+
+
+# ---- algorithmic work per kernel (FMA = 2 flop; sin/cos, rsqrt, tanh, div = 1) ----
+def algorithmic_flops(m, pairs_r, pairs_a, n):
+    """Flops the formulas require per launch, from the shapes and the pair counts.
+
+    descriptor+network kernel
+      radial pair   13 (pair vector, r) + basis(K_R) + 2 n_R K_R (g_n) + n_R (q_n)
+      angular pair  13 + 3 (unit vector) + basis(K_A) + 2 n_A K_A + 60 (Y_lm, l<=4)
+                    + 2 n_A 24 (A_nlm)
+      per bead      2 n_A 24 (q_nl) + H (4 N_des + 6) + 2 n_A 24 (Phi)
+    force+virial kernel
+      radial pair   13 + basis'(K_R) + 4 n_R K_R (g' both directions) + 4 n_R + 3 + 6 (F) + 18 (W)
+      angular pair  13 + 3 + basis'(K_A) + 8 n_A K_A (g, g' both directions) + 60 (Y_lm)
+                    + 24 (8 n_A + 12) (G, G', s_i, s_j) + 420 (sum_lm G grad Y_lm, both)
+                    + 12 (F, v_j) + 18 (W)
+    with basis(K) = 10 + 5 (K - 2) and basis'(K) = 14 + 11 (K - 2).
+    """
+    nR, nA, KR, KA, H = m.n_desc_radial, m.n_desc_angular, m.n_basis_radial, m.n_basis_angular, m.hidden
+    nd = nR + 4 * nA
+    basis = lambda K: 10 + 5 * (K - 2)  # noqa: E731
+    basis_d = lambda K: 14 + 11 * (K - 2)  # noqa: E731
+    d_r = 13 + basis(KR) + 2 * nR * KR + nR
+    d_a = 16 + basis(KA) + 2 * nA * KA + 60 + 2 * nA * 24
+    d_b = 2 * nA * 24 + H * (4 * nd + 6) + 2 * nA * 24
+    f_r = 13 + basis_d(KR) + 4 * nR * KR + 4 * nR + 3 + 6 + 18
+    f_a = 16 + basis_d(KA) + 8 * nA * KA + 60 + 24 * (8 * nA + 12) + 420 + 12 + 18
+    return {"descriptor_network": d_r * pairs_r + d_a * pairs_a + d_b * n,
+            "force_virial": f_r * pairs_r + f_a * pairs_a}
+
+
+# ---- clocks sampler ------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+# ---- the oracle on the host cores ---------------------------------------------
+def cpu_oracle_run(model, system, vel, steps):
+    """Velocity-Verlet steps of the whole system with the FP64 oracle (one full
+    force evaluation per step).  The step starts from zero forces, which changes
+    the trajectory but not the work.  Returns (seconds, steps, cores)."""
+    import oracle  # test infrastructure: only the baseline legs use it
+    oracle.lib()
+    f0 = np.zeros_like(system.pos)
+    t0 = time.perf_counter()
+    oracle.md(model, system, system.pos, vel, f0, steps, DT_FS)
+    return time.perf_counter() - t0, steps, os.cpu_count()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    model, _, _ = workload()
+    # bounded sample: a 10,000-bead box of the same water (same density, lattice
+    # recipe, model and neighbour counts), one full velocity-Verlet step per timed step
+    system = inputs.water_box(10_000, density=0.0334, seed=1001)
+    system.masses = np.array([18.0])
+    vel = inputs.maxwell_boltzmann(system, 300.0, seed=7)
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_run(model, system, vel, 1)
+    steps_total, secs_total = 0, 0.0
+    for k in range(args.steps):
+        s, st, cores = cpu_oracle_run(model, system, vel, 1)
+        secs_total += s
+        steps_total += st
+    v = system.n * steps_total / secs_total
+    sample = (f"{steps_total} FP64 velocity-Verlet steps of a {system.n}-bead box of the same water "
+              f"(same density and model), one per timed step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs_total / steps_total,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(workload()[1]),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---- our arm --------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2603_01234_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    binding.load(build_if_missing=True)
+
+    model, system, vel0 = workload()
+    n = system.n
+    m = binding.Model(model, "fp32", device=local)
+    types = torch.from_numpy(system.types).to(dev)
+    pos = torch.from_numpy(system.pos.copy()).to(dev)
+    vel = torch.from_numpy(vel0.copy()).to(dev)
+    force = torch.zeros(3, n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
+
+    def step(k=1, fv=1, sample=0, thermo=None):
+        binding.nep_md_step(m.h, types, system.masses, system.box, system.pbc, pos, vel, force, fv, k, DT_FS,
+                            sample, thermo, stream=sp)
+
+    # pair counts of the initial configuration (for the algorithmic work)
+    cnt_r, _, _ = binding.nep_neighbors(m.h, system.types, system.pos, system.box, system.pbc, 0, 1)
+    cnt_a, _, _ = binding.nep_neighbors(m.h, system.types, system.pos, system.box, system.pbc, 1, 1)
+    pairs_r, pairs_a = int(cnt_r.sum()), int(cnt_a.sum())
+
+    step(k=0, fv=0)  # initial forces
+    binding.nep_set_timing(m.h, 1)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    binding.nep_sync(m.h)
+    binding.nep_set_timing(m.h, 1)  # reset the stage sums
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    binding.nep_sync(m.h)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    stages, tsteps = binding.nep_get_timing(m.h)
+    binding.nep_set_timing(m.h, 0)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1000.0)
+    ms_step = ms / args.steps
+
+    # steady state: the same steps back to back through the graph-captured loop
+    steady = None
+    if not args.quick:
+        k2 = max(2 * args.steps, 20)
+        step(k=k2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(k=k2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        binding.nep_sync(m.h)
+        steady = {"value": n * k2 / (e0.elapsed_time(e1) / 1000.0), "unit": UNIT, "steps": k2,
+                  "how": "one nep_md_step call of k steps (CUDA graph chunks), no L2 flush"}
+
+    # end to end through the public API with pinned host buffers (H2D + step + D2H)
+    e2e = None
+    if not args.quick:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        h_types, h_pos = pin(system.types), pin(pos.cpu().numpy())
+        h_vel, h_force = pin(vel.cpu().numpy()), pin(force.cpu().numpy())
+        thermo = pin(np.zeros((1, 12)))
+        binding.nep_md_step(m.h, h_types, system.masses, system.box, system.pbc, h_pos, h_vel, h_force, 1, 1, DT_FS,
+                            1, thermo)
+        ke = max(3, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            binding.nep_md_step(m.h, h_types, system.masses, system.box, system.pbc, h_pos, h_vel, h_force, 1, 1,
+                                DT_FS, 1, thermo)
+        te = time.perf_counter() - t0
+        h2d = h_types.nbytes + h_pos.nbytes + h_vel.nbytes + h_force.nbytes
+        d2h = h_pos.nbytes + h_vel.nbytes + h_force.nbytes + thermo.nbytes
+        e2e = {"value": n * ke / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "steps": ke, "how": "nep_md_step(mem=HOST, 1 step, thermo row) per step, host wall clock"}
+
+    # the plain form: FP64 throughout, one configuration, no graph
+    plain = None
+    if not args.quick:
+        m64 = binding.Model(model, "fp64", device=local)
+        pos64, vel64 = pos.clone(), vel.clone()
+        f64 = torch.zeros_like(force)
+        binding.nep_md_step(m64.h, types, system.masses, system.box, system.pbc, pos64, vel64, f64, 0, 0, DT_FS,
+                            0, None, stream=sp)
+        binding.nep_set_timing(m64.h, 1)
+        kp = 3
+        binding.nep_md_step(m64.h, types, system.masses, system.box, system.pbc, pos64, vel64, f64, 1, 1, DT_FS,
+                            0, None, stream=sp)
+        binding.nep_sync(m64.h)
+        binding.nep_set_timing(m64.h, 1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        binding.nep_md_step(m64.h, types, system.masses, system.box, system.pbc, pos64, vel64, f64, 1, kp, DT_FS,
+                            0, None, stream=sp)
+        b.record(stream)
+        torch.cuda.synchronize()
+        binding.nep_sync(m64.h)
+        st64, _ = binding.nep_get_timing(m64.h)
+        plain = {"value": n * kp / (a.elapsed_time(b) / 1000.0), "unit": UNIT, "steps": kp,
+                 "dtype": "f64", "stages_ms_per_step": {k: v / kp for k, v in st64.items()},
+                 "how": "FP64 throughout, eager launches, same workload"}
+        m64.close()
+
+    m.close()
+    if rank != 0:
+        return 0
+
+    peaks = measured_peaks()
+    work = algorithmic_flops(model, pairs_r, pairs_a, n)
+    dom = max(("descriptor_network", "force_virial"), key=lambda k: stages[k])
+    dom_ms = stages[dom] / max(1, tsteps)
+    achieved = work[dom] / (dom_ms / 1000.0) / 1e12
+    sm_max = (clk.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
+    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": dom, "flop_per_launch": work[dom], "ms_per_launch": dom_ms,
+            "peak_note": FLOPS_PEAK_NOTE + f" ({sm_max:.0f} MHz max clock)"}
+    if clk.get("sm_mhz"):
+        roof["frac_at_median_clock"] = achieved / (152 * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        secs, st, cores = cpu_oracle_run(model, system, vel0, 1)
+        cpu = {"value": n * st / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{st} full FP64 velocity-Verlet step of all {n} beads on the host cores"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(system),
+            "ns_per_day": (1000.0 / ms_step) * DT_FS * 0.0864,
+            "gpu_launches": 10 * args.steps,  # per step: kick/drift, 5 cell-build, neighbours, descriptor, force, kick
+            "stages_ms_per_step": {k: v / max(1, tsteps) for k, v in stages.items()},
+            "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
+            "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
+            "steady_state_graph": steady, "plain_fp64": plain}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the steady-state, e2e and FP64 legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * nep.h -- C ABI of the GB300 (sm_103a) NEP evaluator: energy, forces and per-bead
+ * virial of a neuroevolution potential (NEP4 form) over a cell-list neighbour
+ * list, and a velocity-Verlet MD step, as used by the NEP-CG and NEP-AACG models
+ * of arXiv 2603.01234.
+ *
+ * What is computed (paper Sec. II.A, Sec. II.C):
+ *   E   = sum_i U_i                                                   (Eq. 1)
+ *   U_i = sum_mu w1_mu tanh(sum_nu w0_{mu nu} q_nu - b0_mu) - b1      (Eq. 2)
+ *   q_n   = sum_{j != i} g_n(r_ij),            0 <= n < n_R           (Eq. 3)
+ *   q_nl  = sum_m (-1)^m A_nlm A_nl(-m),        1 <= l <= l_max        (Eq. 4)
+ *   A_nlm = sum_{j != i} g_n(r_ij) Y_lm(r_ij),  0 <= n < n_A           (Eq. 5)
+ *   g_n(r) = sum_{k < K} c^{t_i t_j}_{nk} f_k(r)                        (Eq. 6)
+ *   f_k(r) = 1/2 [T_k(2 (r/r_c - 1)^2 - 1) + 1] f_c(r)                  (Eq. 7)
+ *   f_c(r) = 1/2 [1 + cos(pi r / r_c)] for r < r_c, else 0              (Eq. 8)
+ *   F_i = -dE/dr_i
+ *   W_i = sum_{j != i} r_ij (x) dU_j/dr_ji,  r_ij = r_j - r_i           (Eq. 15)
+ *   W   = sum_i W_i                                                    (Eq. 16)
+ * The radial descriptors use the radial cutoff and basis size, the angular ones
+ * the angular cutoff and basis size (Sec. II.A).  Type information enters only
+ * through c^{t_i t_j}, the per-type network and the per-pair cutoffs.
+ *
+ * Conventions
+ *   - Units: Angstrom, eV, amu, fs.  Outputs are always double precision.
+ *   - Arrays of particles are structure-of-arrays: pos[3][n] means x[0..n), then
+ *     y, then z.  Per-bead virials are [9][n] with component 3*alpha + beta.
+ *   - Particle types are 0-based int32 < n_types.
+ *   - Boxes are orthorhombic: box[3] side lengths, pbc[3] (1 = periodic).  On a
+ *     periodic axis positions may lie anywhere (they are wrapped to [0, L)
+ *     internally); an open axis uses [0, L) only to bin particles.
+ *   - A pair is a neighbour when r < r_c(t_i, t_j).  Periodic images count,
+ *     including images of the particle itself; r_c may exceed L/2 but not 2 L on a
+ *     periodic axis (NEP_ERR_BOX_TOO_SMALL otherwise).
+ *   - The caller owns every buffer it passes.  The library owns the model handle,
+ *     the device copies of the parameters and a grow-only device workspace.
+ *   - Calls on one handle must not overlap (the workspace is per handle); handles
+ *     are independent.
+ *   - Every call returns NEP_OK (0) or a negative NEP_ERR_* code and never
+ *     throws; nep_last_error() returns a message for the last failure.
+ */
+#ifndef NEP_GB300_H
+#define NEP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEP_OK 0
+#define NEP_ERR_ARG (-1)                /* invalid argument (message in nep_last_error) */
+#define NEP_ERR_OOM (-2)                /* device allocation failed */
+#define NEP_ERR_NEIGHBOR_OVERFLOW (-3)  /* a neighbour list outgrew its capacity during MD */
+#define NEP_ERR_BOX_TOO_SMALL (-4)      /* r_c > 2 L on a periodic axis */
+#define NEP_ERR_TIMEOUT (-5)            /* a bounded device wait ran out */
+#define NEP_ERR_CUDA (-6)               /* a CUDA runtime error (message in nep_last_error) */
+#define NEP_ERR_UNSUPPORTED (-7)        /* basis / descriptor sizes without a compiled kernel */
+
+/* precision of the evaluation */
+#define NEP_FP64 0  /* every step in double precision: the plain reference form */
+#define NEP_FP32 1  /* FP32 descriptors, network and pair forces; FP64 reductions,
+                       positions, velocities and integration */
+
+/* memory kind of the caller's particle arrays */
+#define NEP_HOST 0
+#define NEP_DEVICE 1
+
+typedef struct nep_model nep_model;
+
+/* Library version, (major << 16) | minor. */
+int nep_version(void);
+
+/* Text of a status code; static storage. */
+const char* nep_error_string(int code);
+
+/* Message of the last failed call on this thread; static thread-local storage. */
+const char* nep_last_error(void);
+
+/*
+ * Create a model on CUDA device `device` (Sec. II.A, Eq. 2-8).
+ *   n_types            T >= 1
+ *   rc_radial[T*T]     radial cutoff of the pair (t_i, t_j); must be symmetric
+ *   rc_angular[T*T]    angular cutoff of the pair; must be symmetric
+ *   n_basis_radial     K_R = N_bas^R + 1 Chebyshev basis functions (Eq. 6-7)
+ *   n_basis_angular    K_A = N_bas^A + 1
+ *   n_desc_radial      n_R = n_max^R + 1 radial descriptors (Eq. 3)
+ *   n_desc_angular     n_A = n_max^A + 1 radial functions of the angular part
+ *   l_max              l_max^3b (Eq. 4); currently 4
+ *   hidden             N_neu, hidden-layer width (Eq. 2)
+ *   c_radial[T][T][n_R][K_R], c_angular[T][T][n_A][K_A]   c^{t_i t_j}_{nk} (Eq. 6)
+ *   w0[T][H][N_des], b0[T][H], w1[T][H], b1[T]            per-type network (Eq. 2)
+ *     with N_des = n_R + n_A * l_max, descriptor order q_0..q_{n_R-1}, then for
+ *     l = 1..l_max, n = 0..n_A-1: q_nl.
+ *   precision          NEP_FP64 or NEP_FP32
+ * All arrays are host memory, row-major double, read during the call only.
+ * Returns NEP_ERR_UNSUPPORTED for (n_R, n_A, K_R, K_A, l_max) without a compiled
+ * kernel; the compiled set is listed by nep_supported_shape().
+ */
+int nep_create(nep_model** out, int n_types, const double* rc_radial, const double* rc_angular,
+               int n_basis_radial, int n_basis_angular, int n_desc_radial, int n_desc_angular,
+               int l_max, int hidden, const double* c_radial, const double* c_angular,
+               const double* w0, const double* b0, const double* w1, const double* b1,
+               int precision, int device);
+
+/* 1 if kernels for these sizes are compiled in, else 0. */
+int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial,
+                        int n_basis_angular, int l_max);
+
+/* Free the model and its device workspace.  NULL is accepted. */
+int nep_destroy(nep_model* m);
+
+/*
+ * Energy, forces and virials of one configuration (Eq. 1-8, 15, 16).
+ *   n                 number of particles, 1 <= n < 2^23
+ *   types[n], pos[3][n]                    inputs
+ *   box[3], pbc[3]    host arrays
+ *   mem               NEP_HOST: every array pointer below is host memory;
+ *                     NEP_DEVICE: every array pointer is device memory on the
+ *                     model's device (box and pbc stay host arrays)
+ *   stream            cudaStream_t to run on (NULL = the legacy default stream)
+ *   energy_total[1], virial_total[9]       E and W (FP64 sums); may be NULL
+ *   site_energy[n]    U_i; may be NULL
+ *   force[3][n]       F_i; may be NULL
+ *   virial[9][n]      W_i; may be NULL
+ * The call returns when the results are written (it synchronises `stream`).
+ * Neighbour-list capacity grows automatically.
+ */
+int nep_compute(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                const int32_t pbc[3], int mem, void* stream, double* energy_total, double* virial_total,
+                double* site_energy, double* force, double* virial);
+
+/*
+ * n_steps velocity-Verlet NVE steps (the MD loop of Sec. III.D):
+ *   v += dt/2 F/m;  r += dt v;  wrap periodic axes;  F = F(r);  v += dt/2 F/m.
+ *   masses[T]         host, amu per type
+ *   pos[3][n], vel[3][n] (Angstrom/fs), force[3][n]   state, updated in place
+ *   forces_valid      1: `force` holds F(pos) on entry; 0: it is computed first
+ *   dt_fs             time step in fs
+ *   sample_every      > 0: after every sample_every-th step one thermo row is
+ *                     written; 0: no rows
+ *   thermo            host [n_steps / sample_every][12]: step, E_pot, E_kin,
+ *                     W_tot[9] (eV); may be NULL when sample_every == 0
+ *   mem, stream       as in nep_compute (box, pbc, masses, thermo: host)
+ * The steps run in chunks (sample_every steps, else up to 50); one chunk is
+ * captured as a CUDA graph, cached on the handle by its arguments, and replayed.
+ * Synchrony: with mem = NEP_DEVICE and a non-NULL stream the call only enqueues
+ * work on `stream` and returns; device-side status (neighbour overflow,
+ * non-finite positions) is then reported by the next call on the handle or by
+ * nep_sync(), and thermo rows are valid after nep_sync().  Otherwise the call
+ * returns when the steps are done.
+ * Neighbour-list capacity is probed synchronously once per configuration shape
+ * (n and cell grid) with 30% headroom, and raised when a later call sees counts
+ * above 90% of it.  NEP_ERR_NEIGHBOR_OVERFLOW means a list outgrew its capacity:
+ * the state of that call is undefined and the capacity is raised for the next.
+ */
+int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid,
+                int n_steps, double dt_fs, int sample_every, double* thermo, int mem, void* stream);
+
+/* Wait for the handle's asynchronous MD work and return its deferred status. */
+int nep_sync(nep_model* m);
+
+/* pos[3][n] *= scale[3] per axis (affine box strain); same memory rules as above. */
+int nep_scale_positions(nep_model* m, int n, double* pos, const double scale[3], int mem, void* stream);
+
+/*
+ * Neighbour lists as built by the library (for inspection and tests).
+ *   kind        0 = radial (r < r_c^R), 1 = angular (r < r_c^A)
+ *   capacity    entries per particle in the output arrays
+ *   count[n]    number of neighbours of each particle (may exceed capacity)
+ *   j[n][capacity], shift[n][capacity][3]   neighbour index and periodic image
+ *               shift in box lengths, relative to the wrapped positions
+ * Host buffers; inputs as in nep_compute with mem = NEP_HOST.
+ */
+int nep_neighbors(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                  const int32_t pbc[3], int kind, int capacity, int32_t* count, int32_t* j, int32_t* shift);
+
+/*
+ * Per-stage device timing of MD steps (CUDA events on the launch stream).  While
+ * enabled, nep_md_step runs its steps without graph capture and records events
+ * around each stage of every step.  Enabling (or re-enabling) resets the sums.
+ */
+int nep_set_timing(nep_model* m, int enable);
+
+/*
+ * Summed device time in ms of each stage over the timed steps, waiting for the
+ * pending events first:  stage_ms[6] = kick+drift, cell build, neighbour lists,
+ * descriptor+network, force+virial, kick(+sample);  steps = steps timed.
+ */
+int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
+
+/* Current neighbour-list capacities (entries per particle). */
+int nep_get_capacity(nep_model* m, int* radial, int* angular);
+
+/* Set the neighbour-list capacities (entries per particle, >= 1). */
+int nep_set_capacity(nep_model* m, int radial, int angular);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEP_GB300_H */

@@ -1,0 +1,287 @@
+"""Thin Python binding of the C ABI in include/nep.h (argument marshalling only).
+
+Every step of the evaluation runs in the CUDA library libnep_gb300.so; this module
+only converts arrays to pointers.  Host arrays are numpy; device arrays are torch
+CUDA tensors (torch supplies device memory and streams).  If the library is not
+built, load() raises -- there is no CPU fallback.
+
+Module-level functions carry the C names (nep_create, nep_compute, nep_md_step,
+nep_neighbors, ...); `Model` wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NEP_OK = 0
+NEP_ERR_ARG = -1
+NEP_ERR_OOM = -2
+NEP_ERR_NEIGHBOR_OVERFLOW = -3
+NEP_ERR_BOX_TOO_SMALL = -4
+NEP_ERR_TIMEOUT = -5
+NEP_ERR_CUDA = -6
+NEP_ERR_UNSUPPORTED = -7
+NEP_FP64 = 0
+NEP_FP32 = 1
+NEP_HOST = 0
+NEP_DEVICE = 1
+
+EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "nep_supported_shape",
+            "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
+            "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing"]
+
+_lib = None
+
+
+class NepError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = f"{where}: {_lib.nep_error_string(code).decode()} ({code})"
+        detail = _lib.nep_last_error().decode()
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libnep_gb300.so; raise if it is not built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_2603_01234_gb300/build.py)")
+    lib = C.CDLL(path)
+    i, d, p = C.c_int, C.c_double, C.c_void_p
+    lib.nep_version.restype = i
+    lib.nep_error_string.argtypes = [i]
+    lib.nep_error_string.restype = C.c_char_p
+    lib.nep_last_error.restype = C.c_char_p
+    lib.nep_create.argtypes = [C.POINTER(p), i, p, p, i, i, i, i, i, i, p, p, p, p, p, p, i, i]
+    lib.nep_create.restype = i
+    lib.nep_supported_shape.argtypes = [i, i, i, i, i]
+    lib.nep_supported_shape.restype = i
+    lib.nep_destroy.argtypes = [p]
+    lib.nep_destroy.restype = i
+    lib.nep_compute.argtypes = [p, i, p, p, p, p, i, p, p, p, p, p, p]
+    lib.nep_compute.restype = i
+    lib.nep_md_step.argtypes = [p, i, p, p, p, p, p, p, p, i, i, d, i, p, i, p]
+    lib.nep_md_step.restype = i
+    lib.nep_scale_positions.argtypes = [p, i, p, p, i, p]
+    lib.nep_scale_positions.restype = i
+    lib.nep_neighbors.argtypes = [p, i, p, p, p, p, i, i, p, p, p]
+    lib.nep_neighbors.restype = i
+    lib.nep_get_capacity.argtypes = [p, C.POINTER(i), C.POINTER(i)]
+    lib.nep_get_capacity.restype = i
+    lib.nep_set_capacity.argtypes = [p, i, i]
+    lib.nep_set_capacity.restype = i
+    lib.nep_sync.argtypes = [p]
+    lib.nep_sync.restype = i
+    lib.nep_set_timing.argtypes = [p, i]
+    lib.nep_set_timing.restype = i
+    lib.nep_get_timing.argtypes = [p, p, C.POINTER(C.c_longlong)]
+    lib.nep_get_timing.restype = i
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != NEP_OK:
+        raise NepError(code, where)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        return C.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(C.c_void_p)
+
+
+def _stream_of(x, stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    if x is not None and _is_torch(x) and x.is_cuda:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return None
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ---- C-named functions ---------------------------------------------------------
+def nep_version():
+    return load().nep_version()
+
+
+def nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max):
+    return bool(load().nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
+
+
+def nep_create(params, precision=NEP_FP32, device=0):
+    """params: an inputs.ModelParams.  Returns an opaque handle (c_void_p)."""
+    lib = load()
+    h = C.c_void_p()
+    arrs = [_host(params.rc_radial, np.float64), _host(params.rc_angular, np.float64),
+            _host(params.c_radial, np.float64), _host(params.c_angular, np.float64),
+            _host(params.w0, np.float64), _host(params.b0, np.float64), _host(params.w1, np.float64),
+            _host(params.b1, np.float64)]
+    _check(lib.nep_create(C.byref(h), params.n_types, _ptr(arrs[0]), _ptr(arrs[1]), params.n_basis_radial,
+                          params.n_basis_angular, params.n_desc_radial, params.n_desc_angular, params.l_max,
+                          params.hidden, *[_ptr(a) for a in arrs[2:]], int(precision), int(device)), "nep_create")
+    return h
+
+
+def nep_destroy(h):
+    if h:
+        _check(load().nep_destroy(h), "nep_destroy")
+
+
+def nep_compute(h, types, pos, box, pbc, energy_total=None, virial_total=None, site_energy=None, force=None,
+                virial=None, stream=None):
+    """All arrays numpy (host) or all torch CUDA tensors (device); box/pbc host."""
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    n = int(types.shape[0])
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    _check(load().nep_compute(h, n, _ptr(types), _ptr(pos), _ptr(box), _ptr(pbc), mem, _stream_of(pos, stream),
+                              _ptr(energy_total), _ptr(virial_total), _ptr(site_energy), _ptr(force), _ptr(virial)),
+           "nep_compute")
+
+
+def nep_md_step(h, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs, sample_every=0,
+                thermo=None, stream=None):
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    n = int(types.shape[0])
+    masses = _host(masses, np.float64)
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    _check(load().nep_md_step(h, n, _ptr(types), _ptr(masses), _ptr(box), _ptr(pbc), _ptr(pos), _ptr(vel),
+                              _ptr(force), int(forces_valid), int(n_steps), float(dt_fs), int(sample_every),
+                              _ptr(thermo), mem, _stream_of(pos, stream)), "nep_md_step")
+
+
+STAGES = ["kick_drift", "cell_build", "neighbor_lists", "descriptor_network", "force_virial", "kick_sample"]
+
+
+def nep_set_timing(h, enable):
+    _check(load().nep_set_timing(h, int(enable)), "nep_set_timing")
+
+
+def nep_get_timing(h):
+    """Returns ({stage: summed ms}, steps)."""
+    ms = np.zeros(6)
+    steps = C.c_longlong()
+    _check(load().nep_get_timing(h, _ptr(ms), C.byref(steps)), "nep_get_timing")
+    return dict(zip(STAGES, ms.tolist())), steps.value
+
+
+def nep_sync(h):
+    _check(load().nep_sync(h), "nep_sync")
+
+
+def nep_scale_positions(h, pos, scale, stream=None):
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    n = int(pos.shape[1])
+    scale = _host(scale, np.float64)
+    _check(load().nep_scale_positions(h, n, _ptr(pos), _ptr(scale), mem, _stream_of(pos, stream)),
+           "nep_scale_positions")
+
+
+def nep_neighbors(h, types, pos, box, pbc, kind, capacity):
+    """Host arrays.  Returns (count[n], j[n][cap], shift[n][cap][3])."""
+    n = int(types.shape[0])
+    types = _host(types, np.int32)
+    pos = _host(pos, np.float64)
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    cnt = np.zeros(n, np.int32)
+    j = np.full((n, capacity), -1, np.int32)
+    sh = np.zeros((n, capacity, 3), np.int32)
+    _check(load().nep_neighbors(h, n, _ptr(types), _ptr(pos), _ptr(box), _ptr(pbc), int(kind), int(capacity),
+                                _ptr(cnt), _ptr(j), _ptr(sh)), "nep_neighbors")
+    return cnt, j, sh
+
+
+def nep_get_capacity(h):
+    r, a = C.c_int(), C.c_int()
+    _check(load().nep_get_capacity(h, C.byref(r), C.byref(a)), "nep_get_capacity")
+    return r.value, a.value
+
+
+def nep_set_capacity(h, radial, angular):
+    _check(load().nep_set_capacity(h, int(radial), int(angular)), "nep_set_capacity")
+
+
+# ---- convenience wrapper -------------------------------------------------------
+class Model:
+    """A model handle.  precision: "fp32" or "fp64"."""
+
+    def __init__(self, params, precision="fp32", device=0):
+        self.params = params
+        self.precision = precision
+        self.device = device
+        self.h = nep_create(params, NEP_FP64 if precision == "fp64" else NEP_FP32, device)
+
+    def close(self):
+        if self.h:
+            nep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def compute(self, system_or_types, pos=None, box=None, pbc=None, stream=None):
+        """Host evaluation; returns dict(energy, virial_total, site_energy, force, virial)."""
+        if pos is None:
+            s = system_or_types
+            types, pos, box, pbc = s.types, s.pos, s.box, s.pbc
+        else:
+            types = system_or_types
+        n = int(types.shape[0])
+        e = np.zeros(1)
+        wt = np.zeros(9)
+        U = np.zeros(n)
+        F = np.zeros((3, n))
+        W = np.zeros((9, n))
+        nep_compute(self.h, _host(types, np.int32), _host(pos, np.float64), box, pbc, e, wt, U, F, W, stream=stream)
+        return {"energy": float(e[0]), "virial_total": wt, "site_energy": U, "force": F, "virial": W}
+
+    def compute_device(self, types, pos, box, pbc, out=None, stream=None):
+        """Device evaluation on torch CUDA tensors; returns dict of tensors."""
+        import torch
+        n = int(types.shape[0])
+        dev = pos.device
+        if out is None:
+            out = {"energy": torch.zeros(1, dtype=torch.float64, device=dev),
+                   "virial_total": torch.zeros(9, dtype=torch.float64, device=dev),
+                   "site_energy": torch.zeros(n, dtype=torch.float64, device=dev),
+                   "force": torch.zeros(3, n, dtype=torch.float64, device=dev),
+                   "virial": torch.zeros(9, n, dtype=torch.float64, device=dev)}
+        nep_compute(self.h, types, pos, box, pbc, out["energy"], out["virial_total"], out["site_energy"],
+                    out["force"], out["virial"], stream=stream)
+        return out
+
+    def neighbors(self, system, kind=0, capacity=None):
+        cap = capacity or max(nep_get_capacity(self.h)) or 256
+        return nep_neighbors(self.h, system.types, system.pos, system.box, system.pbc, kind, max(cap, 8))

@@ -1,0 +1,1002 @@
+// C ABI (include/nep.h) and the runtime behind it: model parameters on the device,
+// a grow-only workspace per handle, the per-configuration pipeline
+//   cell build -> neighbour lists -> descriptor + network -> forces + virials + FP64 totals
+// and the velocity-Verlet loop captured as a CUDA graph.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/nep.h"
+#include "nep_common.cuh"
+
+using namespace nep;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define NEP_CUDA(call)                                                                                 \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            return fail(e_ == cudaErrorMemoryAllocation ? NEP_ERR_OOM : NEP_ERR_CUDA,                  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+        }                                                                                              \
+    } while (0)
+
+#define NEP_TRY(call)              \
+    do {                           \
+        int r_ = (call);           \
+        if (r_ != NEP_OK) return r_; \
+    } while (0)
+
+constexpr double kAcc = 9.648533212e-3;  // 1 eV/(A amu) in A/fs^2
+
+template <typename T>
+int grow(T*& p, size_t& cap, size_t want)
+{
+    if (want <= cap && p) return NEP_OK;
+    size_t nc = std::max(want, cap + cap / 4);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void**)&p, nc * sizeof(T) + 16);
+    if (e != cudaSuccess) return fail(NEP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    cap = nc;
+    return NEP_OK;
+}
+
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;  // bytes
+    int ensure(size_t bytes)
+    {
+        if (bytes <= cap && p) return NEP_OK;
+        size_t nc = std::max(bytes, cap + cap / 4);
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, nc + 256);
+        if (e != cudaSuccess) return fail(NEP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cap = nc;
+        return NEP_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Per-stage device timing of MD steps: a ring of event sets, one set per step.
+// Stage k of a step lies between events k and k+1:
+//   0 kick+drift, 1 cell build, 2 neighbour lists, 3 descriptor+network,
+//   4 force+virial, 5 kick (+ sample)
+struct StageTimer {
+    static constexpr int kRing = 64, kEv = 7;
+    bool on = false;
+    bool created = false;
+    cudaEvent_t ev[kRing][kEv];
+    bool pending[kRing] = {};
+    int head = 0;
+    double acc[kEv - 1] = {};
+    long long steps = 0;
+    int create()
+    {
+        if (created) return 0;
+        for (int r = 0; r < kRing; ++r)
+            for (int k = 0; k < kEv; ++k)
+                if (cudaEventCreate(&ev[r][k]) != cudaSuccess) return -1;
+        created = true;
+        return 0;
+    }
+    void collect(int r)
+    {
+        if (!pending[r]) return;
+        cudaEventSynchronize(ev[r][kEv - 1]);
+        for (int k = 0; k + 1 < kEv; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[r][k], ev[r][k + 1]) == cudaSuccess) acc[k] += ms;
+        }
+        ++steps;
+        pending[r] = false;
+    }
+    void drain()
+    {
+        for (int r = 0; r < kRing; ++r) collect((head + r) % kRing);
+    }
+    void reset()
+    {
+        drain();
+        for (double& a : acc) a = 0.0;
+        steps = 0;
+    }
+    void destroy()
+    {
+        if (!created) return;
+        drain();
+        for (int r = 0; r < kRing; ++r)
+            for (int k = 0; k < kEv; ++k) cudaEventDestroy(ev[r][k]);
+        created = false;
+    }
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+};
+
+}  // namespace
+
+struct nep_model {
+    int device = 0;
+    int precision = NEP_FP32;
+    int T = 1, nR = 0, nA = 0, KR = 0, KA = 0, L = 4, H = 0, ND = 0, NRP = 0;
+    double rc_max = 0.0;
+    std::vector<double> rcR, rcA;
+    ParamLayout off{};
+    Buf params;
+    size_t real_size = 4;
+    size_t smem_desc = 0, smem_force = 0;
+    int mnR = 0, mnA = 0;  // neighbour capacities
+    cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
+    cudaStream_t cur = nullptr;  // stream of the call in progress
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_flags = nullptr;
+    int* h_async = nullptr;      // pinned copy of the status words after an asynchronous MD call
+    bool async_pending = false;
+    cudaStream_t async_stream = nullptr;
+    // MD sizing state: the last configuration the capacities were checked for
+    int md_n = -1;
+    CellGrid md_grid{};
+    // workspace
+    Buf cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, dq, phi;
+    Buf cell_count, cell_local, block_off, cell_fill, cell_start;
+    Buf partial, partial2, counters, totals, flags, thermo, sample_index;
+    Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp;
+    int* h_flags = nullptr;  // pinned: maxcnt[2], err
+    double* h_totals = nullptr;  // pinned [10]
+    size_t n_lists = 0;  // n the lists were sized for
+    GraphCache graph;
+    StageTimer timer;
+};
+
+namespace {
+
+struct Guard {  // make the device current for the duration of a call
+    int prev = -1;
+    explicit Guard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~Guard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int make_grid(const nep_model* m, const double box[3], const int32_t pbc[3], CellGrid& g)
+{
+    long long ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !isfinite(box[a])) return fail(NEP_ERR_ARG, "box lengths must be positive and finite");
+        g.pbc[a] = pbc[a] ? 1 : 0;
+        g.box[a] = box[a];
+        int nc = (int)floor(box[a] / m->rc_max);
+        if (nc < 1) nc = 1;
+        if (nc > 1024) nc = 1024;
+        g.nc[a] = nc;
+        g.len[a] = box[a] / nc;
+        if (g.pbc[a]) {
+            int S = (int)ceil(m->rc_max / g.len[a] - 1e-12);
+            if (S < 1) S = 1;
+            if (S > kMaxS) return fail(NEP_ERR_BOX_TOO_SMALL, "cutoff exceeds twice the box length on a periodic axis");
+            g.S[a] = S;
+        } else {
+            g.S[a] = 1;
+            if (g.len[a] < m->rc_max && nc > 1) return fail(NEP_ERR_ARG, "internal: open-axis cell below cutoff");
+        }
+        ncell *= nc;
+    }
+    if (ncell > (long long)kScanItems * kScanItems) return fail(NEP_ERR_ARG, "cell grid too large");
+    g.ncell = (int)ncell;
+    return NEP_OK;
+}
+
+int ensure_particles(nep_model* m, int n)
+{
+    const size_t rs = m->real_size;
+    const size_t rec_sz = 4 * rs;
+    NEP_TRY(m->cell_of.ensure(sizeof(int) * n));
+    NEP_TRY(m->rec_user.ensure(rec_sz * n));
+    NEP_TRY(m->perm.ensure(sizeof(int) * n));
+    NEP_TRY(m->rec_s.ensure(rec_sz * n));
+    NEP_TRY(m->cell_s.ensure(sizeof(int) * n));
+    NEP_TRY(m->cntR.ensure(sizeof(int) * n));
+    NEP_TRY(m->cntA.ensure(sizeof(int) * n));
+    NEP_TRY(m->U.ensure(rs * n));
+    NEP_TRY(m->dq.ensure(rs * m->NRP * (size_t)n));
+    NEP_TRY(m->phi.ensure(rs * 24 * m->nA * (size_t)n));
+    const size_t nb = (n + kBlock - 1) / kBlock;
+    NEP_TRY(m->partial.ensure(sizeof(double) * 10 * nb));
+    NEP_TRY(m->partial2.ensure(sizeof(double) * nb));
+    NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
+    return NEP_OK;
+}
+
+int ensure_lists(nep_model* m, int n)
+{
+    NEP_TRY(m->nlR.ensure(sizeof(uint32_t) * (size_t)m->mnR * n));
+    NEP_TRY(m->nlA.ensure(sizeof(uint32_t) * (size_t)m->mnA * n));
+    m->n_lists = n;
+    return NEP_OK;
+}
+
+int ensure_cells(nep_model* m, int ncell)
+{
+    NEP_TRY(m->cell_count.ensure(sizeof(int) * ncell));
+    NEP_TRY(m->cell_local.ensure(sizeof(int) * ncell));
+    NEP_TRY(m->block_off.ensure(sizeof(int) * (kScanItems + 1)));
+    NEP_TRY(m->cell_fill.ensure(sizeof(int) * ncell));
+    NEP_TRY(m->cell_start.ensure(sizeof(int) * (ncell + 1)));
+    return NEP_OK;
+}
+
+// Estimated neighbour counts from the density of the box (first sizing only).
+void initial_capacity(nep_model* m, int n, const double box[3])
+{
+    if (m->mnR > 0 && m->mnA > 0) return;
+    double V = box[0] * box[1] * box[2];
+    double rho = n / V;
+    double rR = 0, rA = 0;
+    for (double v : m->rcR) rR = std::max(rR, v);
+    for (double v : m->rcA) rA = std::max(rA, v);
+    auto est = [&](double rc) {
+        double c = 4.18879 * rc * rc * rc * rho * 1.3 + 16;
+        int k = (int)std::min(c, 4096.0);
+        return (k + 7) & ~7;
+    };
+    if (m->mnR <= 0) m->mnR = est(rR);
+    if (m->mnA <= 0) m->mnA = est(rA);
+}
+
+template <typename real>
+int run_cells(nep_model* m, int n, const int* types_d, const double* pos_d, const CellGrid& g)
+{
+    cudaError_t e = launch_cell_build<real>(n, pos_d, types_d, m->T, g, m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(),
+                                            m->cell_count.as<int>(), m->cell_local.as<int>(), m->block_off.as<int>(),
+                                            m->cell_fill.as<int>(), m->perm.as<int>(), m->cell_start.as<int>(),
+                                            m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(), m->flags.as<int>() + 2,
+                                            m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
+    return NEP_OK;
+}
+
+template <typename real>
+int run_neighbors(nep_model* m, int n, const CellGrid& g)
+{
+    NeighborArgs<real> a;
+    a.n = n;
+    a.T = m->T;
+    a.mnR = m->mnR;
+    a.mnA = m->mnA;
+    a.g = g;
+    a.cell_start = m->cell_start.as<int>();
+    a.cell_s = m->cell_s.as<int>();
+    a.rec = m->rec_s.as<PosRec<real>>();
+    a.params = m->params.as<real>();
+    a.off = m->off;
+    a.nlR = m->nlR.as<uint32_t>();
+    a.nlA = m->nlA.as<uint32_t>();
+    a.cntR = m->cntR.as<int>();
+    a.cntA = m->cntA.as<int>();
+    a.maxcnt = m->flags.as<int>();
+    cudaError_t e = launch_neighbors<real>(a, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
+    return NEP_OK;
+}
+
+template <typename real>
+int run_evaluate(nep_model* m, int n, const CellGrid& g, double* force, double* virial, double* site,
+                 cudaEvent_t mid = nullptr)
+{
+    EvalArgs<real> a;
+    a.n = n;
+    a.T = m->T;
+    a.H = m->H;
+    a.mnR = m->mnR;
+    a.mnA = m->mnA;
+    for (int k = 0; k < 3; ++k) a.len[k] = (real)g.len[k];
+    a.rec = m->rec_s.as<PosRec<real>>();
+    a.nlR = m->nlR.as<uint32_t>();
+    a.nlA = m->nlA.as<uint32_t>();
+    a.cntR = m->cntR.as<int>();
+    a.cntA = m->cntA.as<int>();
+    a.params = m->params.as<real>();
+    a.off = m->off;
+    a.U = m->U.as<real>();
+    a.dq = m->dq.as<real>();
+    a.phi = m->phi.as<real>();
+    a.perm = m->perm.as<int>();
+    a.force = force;
+    a.virial = virial;
+    a.site = site;
+    a.partial = m->partial.as<double>();
+    a.counter = m->counters.as<unsigned int>();
+    a.totals = m->totals.as<double>();
+    cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, m->smem_desc, m->smem_force, m->cur, mid);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
+    return NEP_OK;
+}
+
+template <typename real>
+int check_lists(nep_model* m, int n, const CellGrid& g, bool* regrown)
+{
+    // read maxcnt and the error word; grow and rebuild on overflow
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaStreamSynchronize(m->cur));
+        if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
+        if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+        int needR = m->h_flags[0], needA = m->h_flags[1];
+        if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
+        if (regrown) *regrown = true;
+        if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
+        if (needA > m->mnA) m->mnA = ((int)(needA * 1.25) + 8 + 7) & ~7;
+        NEP_TRY(ensure_lists(m, n));
+        NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 2 * sizeof(int), m->cur));
+        NEP_TRY(run_neighbors<real>(m, n, g));
+    }
+    return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity did not converge");
+}
+
+// Full evaluation on device arrays (caller order).  force must be non-null.
+template <typename real>
+int evaluate_device(nep_model* m, int n, const int* types_d, const double* pos_d, const CellGrid& g, double* force,
+                    double* virial, double* site)
+{
+    NEP_TRY(ensure_particles(m, n));
+    NEP_TRY(ensure_cells(m, g.ncell));
+    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
+    NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+    NEP_TRY(run_cells<real>(m, n, types_d, pos_d, g));
+    NEP_TRY(run_neighbors<real>(m, n, g));
+    NEP_TRY(check_lists<real>(m, n, g, nullptr));
+    NEP_TRY(run_evaluate<real>(m, n, g, force, virial, site));
+    return NEP_OK;
+}
+
+int validate_common(nep_model* m, int n, const void* types, const void* pos, const double* box, const int32_t* pbc,
+                    int mem)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if (n < 1 || n > kMaxN) return fail(NEP_ERR_ARG, "n out of range [1, 2^23)");
+    if (!types || !pos || !box || !pbc) return fail(NEP_ERR_ARG, "null input array");
+    if (mem != NEP_HOST && mem != NEP_DEVICE) return fail(NEP_ERR_ARG, "mem must be NEP_HOST or NEP_DEVICE");
+    return NEP_OK;
+}
+
+// Order the internal stream after the caller's stream.
+// Work runs on the caller's stream; a NULL stream (the legacy default stream, which
+// cannot be captured into a graph) is replaced by the handle's internal stream,
+// ordered after the legacy stream on entry and before it on exit.
+int enter(nep_model* m, void* stream)
+{
+    if (stream) {
+        m->cur = (cudaStream_t)stream;
+        return NEP_OK;
+    }
+    m->cur = m->st;
+    NEP_CUDA(cudaEventRecord(m->ev_in, (cudaStream_t)0));
+    NEP_CUDA(cudaStreamWaitEvent(m->st, m->ev_in, 0));
+    return NEP_OK;
+}
+
+int leave(nep_model* m, void* stream, bool sync = true)
+{
+    if (!stream) {
+        NEP_CUDA(cudaEventRecord(m->ev_out, m->st));
+        NEP_CUDA(cudaStreamWaitEvent((cudaStream_t)0, m->ev_out, 0));
+    }
+    if (sync) NEP_CUDA(cudaStreamSynchronize(m->cur));
+    return NEP_OK;
+}
+
+template <typename real>
+int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                 const int32_t pbc[3], int mem, void* stream, double* energy_total, double* virial_total,
+                 double* site_energy, double* force, double* virial)
+{
+    CellGrid g;
+    NEP_TRY(make_grid(m, box, pbc, g));
+    NEP_TRY(enter(m, stream));
+    initial_capacity(m, n, box);
+    const int* types_d = types;
+    const double* pos_d = pos;
+    double *force_d = force, *virial_d = virial, *site_d = site_energy;
+    if (mem == NEP_HOST) {
+        NEP_TRY(m->types_d.ensure(sizeof(int) * n));
+        NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        types_d = m->types_d.as<int>();
+        pos_d = m->pos_d.as<double>();
+        NEP_TRY(m->force_d.ensure(sizeof(double) * 3 * (size_t)n));
+        force_d = m->force_d.as<double>();
+        virial_d = nullptr;
+        site_d = nullptr;
+        if (virial) {
+            NEP_TRY(m->virial_d.ensure(sizeof(double) * 9 * (size_t)n));
+            virial_d = m->virial_d.as<double>();
+        }
+        if (site_energy) {
+            NEP_TRY(m->site_d.ensure(sizeof(double) * (size_t)n));
+            site_d = m->site_d.as<double>();
+        }
+    } else if (!force_d) {
+        NEP_TRY(ensure_particles(m, n));
+        force_d = m->force_tmp.as<double>();
+    }
+    NEP_TRY(evaluate_device<real>(m, n, types_d, pos_d, g, force_d, virial_d, site_d));
+    if (mem == NEP_HOST) {
+        if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+        if (virial) NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
+        if (site_energy)
+            NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->h_totals, m->totals.p, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
+        NEP_TRY(leave(m, stream));
+        if (energy_total) *energy_total = m->h_totals[0];
+        if (virial_total)
+            for (int k = 0; k < 9; ++k) virial_total[k] = m->h_totals[1 + k];
+    } else {
+        if (energy_total)
+            NEP_CUDA(cudaMemcpyAsync(energy_total, m->totals.p, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
+        if (virial_total)
+            NEP_CUDA(cudaMemcpyAsync(virial_total, m->totals.as<double>() + 1, sizeof(double) * 9,
+                                     cudaMemcpyDeviceToDevice, m->cur));
+        NEP_TRY(leave(m, stream));
+    }
+    return NEP_OK;
+}
+
+// One MD step's launches (used eagerly and under stream capture).
+template <typename real>
+int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_m_acc, const double* mass,
+                     const CellGrid& g, double* pos, double* vel, double* force, double dt, bool sample,
+                     int step_stride)
+{
+    cudaEvent_t* ev = nullptr;
+    if (m->timer.on) {
+        const int r = m->timer.head;
+        m->timer.collect(r);  // reuse of a ring slot waits for its previous step
+        ev = m->timer.ev[r];
+        m->timer.pending[r] = true;
+        m->timer.head = (r + 1) % StageTimer::kRing;
+        NEP_CUDA(cudaEventRecord(ev[0], m->cur));
+    }
+    cudaError_t e = launch_kick_drift(n, types_d, inv_m_acc, m->T, 0.5 * dt, dt, g, pos, vel, force, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick/drift: ") + cudaGetErrorString(e));
+    if (ev) NEP_CUDA(cudaEventRecord(ev[1], m->cur));
+    NEP_TRY(run_cells<real>(m, n, types_d, pos, g));
+    if (ev) NEP_CUDA(cudaEventRecord(ev[2], m->cur));
+    NEP_TRY(run_neighbors<real>(m, n, g));
+    if (ev) NEP_CUDA(cudaEventRecord(ev[3], m->cur));
+    NEP_TRY(run_evaluate<real>(m, n, g, force, nullptr, nullptr, ev ? ev[4] : nullptr));
+    if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
+    e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
+    if (sample) {
+        e = launch_sample(n, types_d, mass, m->T, vel, m->totals.as<double>(), m->partial2.as<double>(),
+                          m->counters.as<unsigned int>() + 1, m->thermo.as<double>(), m->sample_index.as<int>(),
+                          step_stride, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("sample: ") + cudaGetErrorString(e));
+    }
+    if (ev) NEP_CUDA(cudaEventRecord(ev[6], m->cur));
+    return NEP_OK;
+}
+
+// Deferred status of asynchronous MD calls: maxima of the neighbour counts and the
+// error word accumulate on the device; after each asynchronous call they are copied
+// to pinned memory and inspected at the next call (or by nep_sync).
+int inspect_async(nep_model* m, bool wait)
+{
+    if (!m->async_pending) return NEP_OK;
+    if (wait) {
+        NEP_CUDA(cudaEventSynchronize(m->ev_flags));
+    } else if (cudaEventQuery(m->ev_flags) != cudaSuccess) {
+        (void)cudaGetLastError();  // cudaErrorNotReady is not an error
+        return NEP_OK;
+    }
+    m->async_pending = false;
+    const int needR = m->h_async[0], needA = m->h_async[1], err = m->h_async[2];
+    bool grow_now = needR * 10 > m->mnR * 9 || needA * 10 > m->mnA * 9;
+    if (err || grow_now) {
+        // a later call on this stream runs after the current work; reset the words there
+        NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->async_stream));
+    }
+    if (err) return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
+    if (grow_now) {
+        const bool overflow = needR > m->mnR || needA > m->mnA;
+        m->mnR = std::max(m->mnR, ((int)(needR * 1.3) + 8 + 7) & ~7);
+        m->mnA = std::max(m->mnA, ((int)(needA * 1.3) + 8 + 7) & ~7);
+        m->n_lists = 0;
+        m->graph.reset();
+        if (overflow) return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "a neighbour list outgrew its capacity during MD");
+    }
+    return NEP_OK;
+}
+
+template <typename real>
+int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+            const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+            double dt, int sample_every, double* thermo, int mem, void* stream)
+{
+    CellGrid g;
+    NEP_TRY(make_grid(m, box, pbc, g));
+    if (n_steps < 0) return fail(NEP_ERR_ARG, "n_steps < 0");
+    if (sample_every < 0) return fail(NEP_ERR_ARG, "sample_every < 0");
+    if (sample_every > 0 && !thermo) return fail(NEP_ERR_ARG, "thermo is NULL");
+    if (!masses || !vel || !force) return fail(NEP_ERR_ARG, "null masses, velocity or force");
+    std::vector<double> inv_m(m->T), mass(m->T);
+    for (int t = 0; t < m->T; ++t) {
+        if (!(masses[t] > 0.0)) return fail(NEP_ERR_ARG, "masses must be positive");
+        inv_m[t] = kAcc / masses[t];
+        mass[t] = masses[t];
+    }
+    NEP_TRY(inspect_async(m, false));
+    NEP_TRY(enter(m, stream));
+    const bool async = (mem == NEP_DEVICE && stream != nullptr);
+    initial_capacity(m, n, box);
+    const int* types_d = types;
+    double *pos_d = pos, *vel_d = vel, *force_d = force;
+    if (mem == NEP_HOST) {
+        NEP_TRY(m->types_d.ensure(sizeof(int) * n));
+        NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_TRY(m->vel_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_TRY(m->force_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->vel_d.p, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        if (forces_valid)
+            NEP_CUDA(cudaMemcpyAsync(m->force_d.p, force, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        types_d = m->types_d.as<int>();
+        pos_d = m->pos_d.as<double>();
+        vel_d = m->vel_d.as<double>();
+        force_d = m->force_d.as<double>();
+    }
+    NEP_TRY(ensure_particles(m, n));
+    NEP_TRY(ensure_cells(m, g.ncell));
+    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
+
+    // Size the neighbour lists (one synchronous probe) only for a new
+    // configuration shape; continuation calls rely on the deferred status.
+    const bool new_shape = (n != m->md_n) || memcmp(&g, &m->md_grid, sizeof g) != 0;
+    if (new_shape || !forces_valid) {
+        NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+        NEP_TRY(run_cells<real>(m, n, types_d, pos_d, g));
+        NEP_TRY(run_neighbors<real>(m, n, g));
+        if (new_shape) {
+            NEP_TRY(check_lists<real>(m, n, g, nullptr));
+            const int wantR = ((int)(m->h_flags[0] * 1.3) + 8 + 7) & ~7;
+            const int wantA = ((int)(m->h_flags[1] * 1.3) + 8 + 7) & ~7;
+            if (wantR > m->mnR || wantA > m->mnA) {
+                m->mnR = std::max(m->mnR, wantR);
+                m->mnA = std::max(m->mnA, wantA);
+                NEP_TRY(ensure_lists(m, n));
+                NEP_TRY(run_neighbors<real>(m, n, g));
+            }
+            m->md_n = n;
+            m->md_grid = g;
+            NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+        }
+        if (!forces_valid) NEP_TRY(run_evaluate<real>(m, n, g, force_d, nullptr, nullptr));
+    }
+    const int n_samples = sample_every > 0 ? n_steps / sample_every : 0;
+    NEP_TRY(m->thermo.ensure(sizeof(double) * 12 * std::max(1, n_samples)));
+    NEP_TRY(m->sample_index.ensure(sizeof(int)));
+    if (n_samples > 0) NEP_CUDA(cudaMemsetAsync(m->sample_index.p, 0, sizeof(int), m->cur));
+
+    // the steps run in chunks; one chunk is captured once as a CUDA graph (cached
+    // by its arguments) and replayed
+    const int chunk = sample_every > 0 ? sample_every : std::max(1, std::min(n_steps, 50));
+    int done = 0;
+    if (n_steps >= chunk && !m->timer.on) {  // stage timing runs the steps eagerly
+        std::vector<unsigned char> key;
+        auto put = [&](const void* p, size_t sz) {
+            const unsigned char* b = (const unsigned char*)p;
+            key.insert(key.end(), b, b + sz);
+        };
+        const void* ptrs[] = {types_d, pos_d, vel_d, force_d, m->nlR.p, m->nlA.p, m->cell_start.p, m->thermo.p,
+                              m->partial.p, m->rec_s.p, m->phi.p, m->cur};
+        put(ptrs, sizeof ptrs);
+        put(&n, sizeof n);
+        put(&g, sizeof g);
+        put(&dt, sizeof dt);
+        put(&chunk, sizeof chunk);
+        put(&sample_every, sizeof sample_every);
+        put(&m->mnR, sizeof m->mnR);
+        put(&m->mnA, sizeof m->mnA);
+        put(inv_m.data(), sizeof(double) * m->T);
+        if (!m->graph.exec || m->graph.key != key) {
+            m->graph.reset();
+            NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
+            int rc = NEP_OK;
+            for (int s = 0; s < chunk && rc == NEP_OK; ++s)
+                rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
+                                            sample_every > 0 && s == chunk - 1, sample_every);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
+            if (rc != NEP_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+            ec = cudaGraphInstantiate(&m->graph.exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+            m->graph.key = key;
+        }
+        for (; done + chunk <= n_steps; done += chunk) NEP_CUDA(cudaGraphLaunch(m->graph.exec, m->cur));
+    }
+    for (; done < n_steps; ++done)
+        NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
+                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every));
+    NEP_CUDA(cudaMemcpyAsync(m->h_async, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
+    NEP_CUDA(cudaEventRecord(m->ev_flags, m->cur));
+    m->async_pending = true;
+    m->async_stream = m->cur;
+    if (n_samples > 0)
+        NEP_CUDA(cudaMemcpyAsync(thermo, m->thermo.p, sizeof(double) * 12 * n_samples, cudaMemcpyDeviceToHost, m->cur));
+    if (mem == NEP_HOST) {
+        NEP_CUDA(cudaMemcpyAsync(pos, pos_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(vel, vel_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+    }
+    NEP_TRY(leave(m, stream, !async));
+    if (!async) NEP_TRY(inspect_async(m, true));
+    return NEP_OK;
+}
+
+template <typename real>
+int neighbors_impl(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                   const int32_t pbc[3], int kind, int capacity, int32_t* count, int32_t* jout, int32_t* shift)
+{
+    CellGrid g;
+    NEP_TRY(make_grid(m, box, pbc, g));
+    NEP_TRY(enter(m, nullptr));
+    initial_capacity(m, n, box);
+    NEP_TRY(m->types_d.ensure(sizeof(int) * n));
+    NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
+    NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+    NEP_TRY(ensure_particles(m, n));
+    NEP_TRY(ensure_cells(m, g.ncell));
+    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
+    NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+    NEP_TRY(run_cells<real>(m, n, m->types_d.as<int>(), m->pos_d.as<double>(), g));
+    NEP_TRY(run_neighbors<real>(m, n, g));
+    NEP_TRY(check_lists<real>(m, n, g, nullptr));
+    const int mn = kind == 0 ? m->mnR : m->mnA;
+    std::vector<uint32_t> nl((size_t)mn * n);
+    std::vector<int> cnt(n), perm(n), cell_s(n);
+    NEP_CUDA(cudaMemcpyAsync(nl.data(), kind == 0 ? m->nlR.p : m->nlA.p, sizeof(uint32_t) * nl.size(),
+                             cudaMemcpyDeviceToHost, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(cnt.data(), kind == 0 ? m->cntR.p : m->cntA.p, sizeof(int) * n, cudaMemcpyDeviceToHost,
+                             m->cur));
+    NEP_CUDA(cudaMemcpyAsync(perm.data(), m->perm.p, sizeof(int) * n, cudaMemcpyDeviceToHost, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(cell_s.data(), m->cell_s.p, sizeof(int) * n, cudaMemcpyDeviceToHost, m->cur));
+    NEP_TRY(leave(m, nullptr));
+    for (int i = 0; i < n; ++i) {
+        const int ui = perm[i];
+        const int c = cell_s[i];
+        const int ci[3] = {c % g.nc[0], (c / g.nc[0]) % g.nc[1], c / (g.nc[0] * g.nc[1])};
+        count[ui] = cnt[i];
+        for (int s = 0; s < std::min(cnt[i], std::min(mn, capacity)); ++s) {
+            const uint32_t e = nl[(size_t)s * n + i];
+            const int k = (int)(e & kJMask);
+            const uint32_t code = e >> kJBits;
+            const int d[3] = {(int)(code & 7u) - 2, (int)((code >> 3) & 7u) - 2, (int)((code >> 6) & 7u) - 2};
+            const int cj = cell_s[k];
+            const int cjv[3] = {cj % g.nc[0], (cj / g.nc[0]) % g.nc[1], cj / (g.nc[0] * g.nc[1])};
+            jout[(size_t)ui * capacity + s] = perm[k];
+            for (int a = 0; a < 3; ++a) {
+                int sh = 0;
+                if (g.pbc[a]) {
+                    const int v = ci[a] + d[a] - cjv[a];  // multiple of nc
+                    sh = (v >= 0 ? v / g.nc[a] : -((-v) / g.nc[a]));
+                }
+                shift[((size_t)ui * capacity + s) * 3 + a] = sh;
+            }
+        }
+    }
+    return NEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nep_version(void) { return (0 << 16) | 1; }
+
+const char* nep_error_string(int code)
+{
+    switch (code) {
+    case NEP_OK: return "ok";
+    case NEP_ERR_ARG: return "invalid argument";
+    case NEP_ERR_OOM: return "device out of memory";
+    case NEP_ERR_NEIGHBOR_OVERFLOW: return "neighbour list overflow";
+    case NEP_ERR_BOX_TOO_SMALL: return "box too small for the cutoff";
+    case NEP_ERR_TIMEOUT: return "device wait timed out";
+    case NEP_ERR_CUDA: return "CUDA error";
+    case NEP_ERR_UNSUPPORTED: return "unsupported descriptor or basis sizes";
+    default: return "unknown status";
+    }
+}
+
+const char* nep_last_error(void) { return g_last_error.c_str(); }
+
+int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial, int n_basis_angular, int l_max)
+{
+    return l_max == 4 && evaluate_shape_supported<float>(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular);
+}
+
+int nep_create(nep_model** out, int n_types, const double* rc_radial, const double* rc_angular, int n_basis_radial,
+               int n_basis_angular, int n_desc_radial, int n_desc_angular, int l_max, int hidden,
+               const double* c_radial, const double* c_angular, const double* w0, const double* b0, const double* w1,
+               const double* b1, int precision, int device)
+{
+    if (!out) return fail(NEP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_types < 1 || n_types > kMaxTypes) return fail(NEP_ERR_ARG, "n_types out of range [1, 16]");
+    if (hidden < 1 || hidden > 4096) return fail(NEP_ERR_ARG, "hidden out of range");
+    if (precision != NEP_FP32 && precision != NEP_FP64) return fail(NEP_ERR_ARG, "unknown precision");
+    if (!rc_radial || !rc_angular || !c_radial || !c_angular || !w0 || !b0 || !w1 || !b1)
+        return fail(NEP_ERR_ARG, "null parameter array");
+    if (!nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
+        return fail(NEP_ERR_UNSUPPORTED, "no compiled kernel for these descriptor / basis sizes");
+    const int T = n_types;
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const double r1 = rc_radial[a * T + b], r2 = rc_angular[a * T + b];
+            if (!(r1 > 0.0) || !(r2 > 0.0) || !isfinite(r1) || !isfinite(r2))
+                return fail(NEP_ERR_ARG, "cutoffs must be positive and finite");
+            if (r1 != rc_radial[b * T + a] || r2 != rc_angular[b * T + a])
+                return fail(NEP_ERR_ARG, "cutoff tables must be symmetric");
+        }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(NEP_ERR_CUDA, "no CUDA device");
+    if (device < 0 || device >= ndev) return fail(NEP_ERR_ARG, "device out of range");
+    Guard guard(device);
+
+    nep_model* m = new nep_model();
+    m->device = device;
+    m->precision = precision;
+    m->T = T;
+    m->nR = n_desc_radial;
+    m->nA = n_desc_angular;
+    m->KR = n_basis_radial;
+    m->KA = n_basis_angular;
+    m->L = l_max;
+    m->H = hidden;
+    m->ND = m->nR + m->nA * m->L;
+    m->NRP = (m->nR + 3) & ~3;
+    m->rcR.assign(rc_radial, rc_radial + T * T);
+    m->rcA.assign(rc_angular, rc_angular + T * T);
+    for (int k = 0; k < T * T; ++k) m->rc_max = std::max(m->rc_max, std::max(m->rcR[k], m->rcA[k]));
+    m->real_size = precision == NEP_FP64 ? 8 : 4;
+
+    // parameter layout: cutoffs and coefficient tables first (the force kernel
+    // stages only that prefix), then the network
+    ParamLayout& o = m->off;
+    int p = 0;
+    const int TT = T * T;
+    o.rcR2 = p; p += TT;
+    o.rcA2 = p; p += TT;
+    o.rcR = p; p += TT;
+    o.rcA = p; p += TT;
+    o.cR = p; p += TT * m->nR * m->KR;
+    o.cA = p; p += TT * m->nA * m->KA;
+    o.n_cut_coef = p;
+    o.w0 = p; p += T * hidden * m->ND;
+    o.b0 = p; p += T * hidden;
+    o.w1 = p; p += T * hidden;
+    o.b1 = p; p += T;
+    o.total = p;
+    std::vector<double> h(p);
+    for (int k = 0; k < TT; ++k) {
+        h[o.rcR2 + k] = m->rcR[k] * m->rcR[k];
+        h[o.rcA2 + k] = m->rcA[k] * m->rcA[k];
+        h[o.rcR + k] = m->rcR[k];
+        h[o.rcA + k] = m->rcA[k];
+    }
+    std::copy(c_radial, c_radial + TT * m->nR * m->KR, h.begin() + o.cR);
+    std::copy(c_angular, c_angular + TT * m->nA * m->KA, h.begin() + o.cA);
+    std::copy(w0, w0 + T * hidden * m->ND, h.begin() + o.w0);
+    std::copy(b0, b0 + T * hidden, h.begin() + o.b0);
+    std::copy(w1, w1 + T * hidden, h.begin() + o.w1);
+    std::copy(b1, b1 + T, h.begin() + o.b1);
+
+    auto cleanup = [&](int code) {
+        nep_destroy(m);
+        return code;
+    };
+    if (m->params.ensure(m->real_size * p) != NEP_OK) return cleanup(NEP_ERR_OOM);
+    if (precision == NEP_FP64) {
+        if (cudaMemcpy(m->params.p, h.data(), sizeof(double) * p, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
+    } else {
+        std::vector<float> hf(h.begin(), h.end());
+        if (cudaMemcpy(m->params.p, hf.data(), sizeof(float) * p, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
+    }
+    m->smem_desc = m->real_size * o.total;
+    m->smem_force = m->real_size * o.n_cut_coef;
+    if (m->smem_desc > 200 * 1024) return cleanup(fail(NEP_ERR_ARG, "model too large for shared-memory staging"));
+    // the attribute is per kernel, shared by all handles: allow the largest staging size
+    const size_t smem_cap = 200 * 1024;
+    cudaError_t e = precision == NEP_FP64
+                        ? evaluate_set_smem<double>(m->nR, m->nA, m->KR, m->KA, smem_cap, smem_cap)
+                        : evaluate_set_smem<float>(m->nR, m->nA, m->KR, m->KA, smem_cap, smem_cap);
+    if (e != cudaSuccess) return cleanup(fail(NEP_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e)));
+    if (cudaStreamCreateWithFlags(&m->cur, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_flags, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(NEP_ERR_CUDA, "stream/event creation failed"));
+    if (m->counters.ensure(sizeof(unsigned int) * 4) != NEP_OK || m->totals.ensure(sizeof(double) * 10) != NEP_OK ||
+        m->flags.ensure(sizeof(int) * 4) != NEP_OK)
+        return cleanup(NEP_ERR_OOM);
+    if (cudaMemset(m->counters.p, 0, sizeof(unsigned int) * 4) != cudaSuccess ||
+        cudaMemset(m->flags.p, 0, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_flags, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_totals, sizeof(double) * 10) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_async, sizeof(int) * 4) != cudaSuccess)
+        return cleanup(fail(NEP_ERR_CUDA, "workspace initialisation failed"));
+    *out = m;
+    return NEP_OK;
+}
+
+int nep_destroy(nep_model* m)
+{
+    if (!m) return NEP_OK;
+    Guard guard(m->device);
+    if (m->cur) cudaStreamSynchronize(m->cur);
+    m->graph.reset();
+    m->timer.destroy();
+    Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm, &m->rec_s, &m->cell_s, &m->cntR, &m->cntA,
+                   &m->nlR, &m->nlA, &m->U, &m->dq, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
+                   &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
+                   &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
+                   &m->site_d, &m->force_tmp};
+    for (Buf* b : bufs) b->release();
+    if (m->h_flags) cudaFreeHost(m->h_flags);
+    if (m->h_totals) cudaFreeHost(m->h_totals);
+    if (m->h_async) cudaFreeHost(m->h_async);
+    if (m->ev_flags) cudaEventDestroy(m->ev_flags);
+    if (m->ev_in) cudaEventDestroy(m->ev_in);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    if (m->cur) cudaStreamDestroy(m->cur);
+    delete m;
+    return NEP_OK;
+}
+
+int nep_compute(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                const int32_t pbc[3], int mem, void* stream, double* energy_total, double* virial_total,
+                double* site_energy, double* force, double* virial)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
+    Guard guard(m->device);
+    return m->precision == NEP_FP64
+               ? compute_impl<double>(m, n, types, pos, box, pbc, mem, stream, energy_total, virial_total, site_energy,
+                                      force, virial)
+               : compute_impl<float>(m, n, types, pos, box, pbc, mem, stream, energy_total, virial_total, site_energy,
+                                     force, virial);
+}
+
+int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+                double dt_fs, int sample_every, double* thermo, int mem, void* stream)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
+    if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return fail(NEP_ERR_ARG, "dt must be positive");
+    Guard guard(m->device);
+    return m->precision == NEP_FP64
+               ? md_impl<double>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                 sample_every, thermo, mem, stream)
+               : md_impl<float>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                sample_every, thermo, mem, stream);
+}
+
+int nep_sync(nep_model* m)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    Guard guard(m->device);
+    return inspect_async(m, true);
+}
+
+int nep_scale_positions(nep_model* m, int n, double* pos, const double scale[3], int mem, void* stream)
+{
+    if (!m || !pos || !scale || n < 1) return fail(NEP_ERR_ARG, "bad argument");
+    if (mem == NEP_HOST) {
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < n; ++i) pos[(size_t)a * n + i] *= scale[a];
+        return NEP_OK;
+    }
+    Guard guard(m->device);
+    cudaError_t e = launch_scale(n, pos, scale[0], scale[1], scale[2], (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, cudaGetErrorString(e));
+    return NEP_OK;
+}
+
+int nep_neighbors(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                  const int32_t pbc[3], int kind, int capacity, int32_t* count, int32_t* j, int32_t* shift)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, NEP_HOST));
+    if (kind != 0 && kind != 1) return fail(NEP_ERR_ARG, "kind must be 0 or 1");
+    if (capacity < 1 || !count || !j || !shift) return fail(NEP_ERR_ARG, "bad output buffers");
+    Guard guard(m->device);
+    return m->precision == NEP_FP64 ? neighbors_impl<double>(m, n, types, pos, box, pbc, kind, capacity, count, j, shift)
+                                    : neighbors_impl<float>(m, n, types, pos, box, pbc, kind, capacity, count, j, shift);
+}
+
+int nep_set_timing(nep_model* m, int enable)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    Guard guard(m->device);
+    if (enable && m->timer.create() != 0) return fail(NEP_ERR_CUDA, "event creation failed");
+    m->timer.reset();
+    m->timer.on = enable != 0;
+    return NEP_OK;
+}
+
+int nep_get_timing(nep_model* m, double* stage_ms, long long* steps)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    Guard guard(m->device);
+    m->timer.drain();
+    if (stage_ms)
+        for (int k = 0; k < StageTimer::kEv - 1; ++k) stage_ms[k] = m->timer.acc[k];
+    if (steps) *steps = m->timer.steps;
+    return NEP_OK;
+}
+
+int nep_get_capacity(nep_model* m, int* radial, int* angular)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if (radial) *radial = m->mnR;
+    if (angular) *angular = m->mnA;
+    return NEP_OK;
+}
+
+int nep_set_capacity(nep_model* m, int radial, int angular)
+{
+    if (!m || radial < 1 || angular < 1) return fail(NEP_ERR_ARG, "bad capacity");
+    m->mnR = (radial + 7) & ~7;
+    m->mnA = (angular + 7) & ~7;
+    m->n_lists = 0;
+    m->graph.reset();
+    return NEP_OK;
+}
+
+}  // extern "C"

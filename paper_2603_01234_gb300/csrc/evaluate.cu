@@ -1,0 +1,465 @@
+// Descriptor + network kernel and force + virial kernel (Eq. 1-8, 15, 16).
+//
+// k_descriptor (one thread per sorted particle i):
+//   radial   q_n   = sum_j g_n(r_ij)                              (Eq. 3, 6-8)
+//   angular  A_nlm = sum_j g_n(r_ij) Y_lm(u_ij), q_nl = sum_m A^2  (Eq. 4-5)
+//            with real orthonormal Y_lm (for real g_n, sum_m (-1)^m A_m A_-m of
+//            the complex harmonics equals sum_m A_m^2 of the real ones)
+//   network  U_i (Eq. 2) and dU_i/dq
+//   stores   U_i, dU_i/dq_n (radial), Phi_nlm = dU_i/dA_nlm = 2 dU_i/dq_nl A_nlm
+//
+// k_force (one thread per sorted particle i, gather form, no atomics):
+//   for every neighbour j the pair gradients f_ij = dU_i/dr_ij and
+//   f_ji = dU_j/dr_ji are rebuilt from i's and j's stored gradients, and
+//     F_i = sum_j (f_ij - f_ji),   W_i = sum_j r_ij (x) f_ji   (Eq. 15)
+//   then E = sum U_i and W = sum W_i are reduced in FP64 (Eq. 1, 16) with a
+//   deterministic last-block pass.
+//
+// Angular pair gradient.  For A = g(r) Y(u), u = r/|r|, with Y a homogeneous
+// polynomial of degree l:  dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
+// For the reverse pair, u -> -u gives Y(-u) = (-1)^l Y(u) and
+// grad Y(-u) = (-1)^(l-1) grad Y(u), so f_ji is the same contraction with
+// Phi_j scaled by (-1)^l, negated.
+#include "nep_common.cuh"
+#include "sh_poly.cuh"
+
+namespace nep {
+
+__host__ __device__ constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
+constexpr int kNLM = 24;
+
+__device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// Chebyshev basis f_k(r) of Eq. 7 with the cutoff of Eq. 8, k = 0..K-1, by the
+// three-term recurrence T_{k+1} = 2 x T_k - T_{k-1}.
+template <typename real, int K>
+__device__ __forceinline__ void basis(real r, real inv_rc, real* f)
+{
+    real sn, cs;
+    sincospi_r(r * inv_rc, &sn, &cs);
+    const real fc = real(0.5) * (real(1) + cs);
+    const real s = r * inv_rc - real(1);
+    const real x = real(2) * s * s - real(1);
+    real t0 = real(1), t1 = x;
+    const real hf = real(0.5) * fc;
+    f[0] = fc;
+    if (K > 1) f[1] = hf * (x + real(1));
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        const real t2 = real(2) * x * t1 - t0;
+        f[k] = hf * (t2 + real(1));
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
+// f_k and df_k/dr.
+template <typename real, int K>
+__device__ __forceinline__ void basis_d(real r, real inv_rc, real* f, real* df)
+{
+    real sn, cs;
+    sincospi_r(r * inv_rc, &sn, &cs);
+    const real fc = real(0.5) * (real(1) + cs);
+    const real dfc = real(-0.5) * real(3.14159265358979323846) * inv_rc * sn;
+    const real s = r * inv_rc - real(1);
+    const real x = real(2) * s * s - real(1);
+    const real dxdr = real(4) * s * inv_rc;
+    real t0 = real(1), t1 = x, d0 = real(0), d1 = real(1);
+    f[0] = fc;
+    df[0] = dfc;
+    if (K > 1) {
+        f[1] = real(0.5) * (x + real(1)) * fc;
+        df[1] = real(0.5) * (dxdr * fc + (x + real(1)) * dfc);
+    }
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        const real t2 = real(2) * x * t1 - t0;
+        const real d2 = real(2) * t1 + real(2) * x * d1 - d0;
+        f[k] = real(0.5) * (t2 + real(1)) * fc;
+        df[k] = real(0.5) * (d2 * dxdr * fc + (t2 + real(1)) * dfc);
+        t0 = t1;
+        t1 = t2;
+        d0 = d1;
+        d1 = d2;
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void pair_vector(const EvalArgs<real>& a, const PosRec<real>& ri, uint32_t e,
+                                            PosRec<real>& rj, real& dx, real& dy, real& dz)
+{
+    const int j = (int)(e & kJMask);
+    const uint32_t code = e >> kJBits;
+    rj = a.rec[j];
+    dx = (rj.x - ri.x) + (real)((int)(code & 7u) - 2) * a.len[0];
+    dy = (rj.y - ri.y) + (real)((int)((code >> 3) & 7u) - 2) * a.len[1];
+    dz = (rj.z - ri.z) + (real)((int)((code >> 6) & 7u) - 2) * a.len[2];
+}
+
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
+template <typename real>
+__device__ __forceinline__ void stage_params(const real* __restrict__ src, real* dst, int count)
+{
+    for (int k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+template <typename real, int NR, int NA, int KR, int KA>
+__global__ void __launch_bounds__(kBlock) k_descriptor(EvalArgs<real> a)
+{
+    constexpr int ND = NR + NA * 4;
+    constexpr int NRP = (NR + 3) & ~3;
+    extern __shared__ unsigned char smem_raw[];
+    real* P = reinterpret_cast<real*>(smem_raw);
+    stage_params(a.params, P, a.off.total);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int T = a.T;
+    const PosRec<real> ri = a.rec[i];
+    const int ti = ri.t;
+    real q[ND];
+#pragma unroll
+    for (int v = 0; v < ND; ++v) q[v] = real(0);
+
+    // ---- radial descriptors (Eq. 3, 6-8) ----
+    const int cR = min(a.cntR[i], a.mnR);
+    for (int s = 0; s < cR; ++s) {
+        const uint32_t e = a.nlR[(size_t)s * a.n + i];
+        PosRec<real> rj;
+        real dx, dy, dz;
+        pair_vector(a, ri, e, rj, dx, dy, dz);
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        const real inv_r = rsqrt_r(r2);
+        const real r = r2 * inv_r;
+        const int tp = ti * T + rj.t;
+        real f[KR];
+        basis<real, KR>(r, real(1) / P[a.off.rcR + tp], f);
+        const real* c = P + a.off.cR + tp * NR * KR;
+#pragma unroll
+        for (int nn = 0; nn < NR; ++nn) {
+            real g = real(0);
+#pragma unroll
+            for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * f[k];
+            q[nn] += g;
+        }
+    }
+
+    // ---- angular moments A_nlm (Eq. 5) ----
+    real A[NA][kNLM];
+#pragma unroll
+    for (int nn = 0; nn < NA; ++nn)
+#pragma unroll
+        for (int k = 0; k < kNLM; ++k) A[nn][k] = real(0);
+    const int cA = min(a.cntA[i], a.mnA);
+    for (int s = 0; s < cA; ++s) {
+        const uint32_t e = a.nlA[(size_t)s * a.n + i];
+        PosRec<real> rj;
+        real dx, dy, dz;
+        pair_vector(a, ri, e, rj, dx, dy, dz);
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        const real inv_r = rsqrt_r(r2);
+        const real r = r2 * inv_r;
+        const int tp = ti * T + rj.t;
+        real f[KA];
+        basis<real, KA>(r, real(1) / P[a.off.rcA + tp], f);
+        const real* c = P + a.off.cA + tp * NA * KA;
+        real Y[kNLM];
+        sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) {
+            real g = real(0);
+#pragma unroll
+            for (int k = 0; k < KA; ++k) g += c[nn * KA + k] * f[k];
+#pragma unroll
+            for (int k = 0; k < kNLM; ++k) A[nn][k] += g * Y[k];
+        }
+    }
+    // q_nl (Eq. 4)
+#pragma unroll
+    for (int nn = 0; nn < NA; ++nn)
+#pragma unroll
+        for (int k = 0; k < kNLM; ++k) q[NR + (l_of(k) - 1) * NA + nn] += A[nn][k] * A[nn][k];
+
+    // ---- network (Eq. 2) and dU/dq ----
+    const real* w0 = P + a.off.w0 + ti * a.H * ND;
+    const real* b0 = P + a.off.b0 + ti * a.H;
+    const real* w1 = P + a.off.w1 + ti * a.H;
+    real U = -P[a.off.b1 + ti];
+    real dq[ND];
+#pragma unroll
+    for (int v = 0; v < ND; ++v) dq[v] = real(0);
+    for (int mu = 0; mu < a.H; ++mu) {
+        real x = -b0[mu];
+#pragma unroll
+        for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
+        const real h = tanh(x);
+        U += w1[mu] * h;
+        const real coef = w1[mu] * (real(1) - h * h);
+#pragma unroll
+        for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
+    }
+    a.U[i] = U;
+#pragma unroll
+    for (int nn = 0; nn < NRP; ++nn) a.dq[(size_t)i * NRP + nn] = nn < NR ? dq[nn] : real(0);
+    real* ph = a.phi + (size_t)i * kNLM * NA;
+#pragma unroll
+    for (int k = 0; k < kNLM; ++k)
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) ph[k * NA + nn] = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum(real v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 block partials of (E, W[9]) and a deterministic last-block total.
+__device__ __forceinline__ void reduce_totals(double (&v)[10], double* partial, unsigned int* counter,
+                                              double* totals)
+{
+    __shared__ double red[kBlock / 32][10];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) red[warp][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += red[w][threadIdx.x];
+        partial[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+        const volatile double* p = partial;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)b * 10 + threadIdx.x];
+        totals[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename real, int NR, int NA, int KR, int KA>
+__global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
+{
+    constexpr int NRP = (NR + 3) & ~3;
+    extern __shared__ unsigned char smem_raw[];
+    real* P = reinterpret_cast<real*>(smem_raw);
+    stage_params(a.params, P, a.off.n_cut_coef);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double tot[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) tot[k] = 0.0;
+    if (i < a.n) {
+        const int T = a.T;
+        const PosRec<real> ri = a.rec[i];
+        const int ti = ri.t;
+        real F[3] = {real(0), real(0), real(0)};
+        real W[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) W[k] = real(0);
+        real dqi[NR];
+#pragma unroll
+        for (int nn = 0; nn < NR; ++nn) dqi[nn] = a.dq[(size_t)i * NRP + nn];
+
+        // ---- radial pairs ----
+        const int cR = min(a.cntR[i], a.mnR);
+        for (int s = 0; s < cR; ++s) {
+            const uint32_t e = a.nlR[(size_t)s * a.n + i];
+            const int j = (int)(e & kJMask);
+            PosRec<real> rj;
+            real dx, dy, dz;
+            pair_vector(a, ri, e, rj, dx, dy, dz);
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const real inv_r = rsqrt_r(r2);
+            const real r = r2 * inv_r;
+            const int tij = ti * T + rj.t, tji = rj.t * T + ti;
+            real f[KR], df[KR];
+            basis_d<real, KR>(r, real(1) / P[a.off.rcR + tij], f, df);
+            const real* cij = P + a.off.cR + tij * NR * KR;
+            const real* cji = P + a.off.cR + tji * NR * KR;
+            real ai = real(0), bj = real(0);
+#pragma unroll
+            for (int nn = 0; nn < NR; ++nn) {
+                real gi = real(0), gj = real(0);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    gi += cij[nn * KR + k] * df[k];
+                    gj += cji[nn * KR + k] * df[k];
+                }
+                ai += dqi[nn] * gi;
+                bj += a.dq[(size_t)j * NRP + nn] * gj;
+            }
+            // f_ij = ai u,  f_ji = -bj u
+            const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+            const real fs = ai + bj;
+            F[0] += fs * ux;
+            F[1] += fs * uy;
+            F[2] += fs * uz;
+            const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) W[3 * p + q] -= bj * d[p] * u[q];
+        }
+
+        // ---- angular pairs ----
+        const real* phi_i = a.phi + (size_t)i * kNLM * NA;
+        const int cA = min(a.cntA[i], a.mnA);
+        for (int s = 0; s < cA; ++s) {
+            const uint32_t e = a.nlA[(size_t)s * a.n + i];
+            const int j = (int)(e & kJMask);
+            PosRec<real> rj;
+            real dx, dy, dz;
+            pair_vector(a, ri, e, rj, dx, dy, dz);
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const real inv_r = rsqrt_r(r2);
+            const real r = r2 * inv_r;
+            const int tij = ti * T + rj.t, tji = rj.t * T + ti;
+            real f[KA], df[KA];
+            basis_d<real, KA>(r, real(1) / P[a.off.rcA + tij], f, df);
+            const real* cij = P + a.off.cA + tij * NA * KA;
+            const real* cji = P + a.off.cA + tji * NA * KA;
+            real gi[NA], dgi[NA], gj[NA], dgj[NA];
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                real s0 = real(0), s1 = real(0), s2 = real(0), s3 = real(0);
+#pragma unroll
+                for (int k = 0; k < KA; ++k) {
+                    s0 += cij[nn * KA + k] * f[k];
+                    s1 += cij[nn * KA + k] * df[k];
+                    s2 += cji[nn * KA + k] * f[k];
+                    s3 += cji[nn * KA + k] * df[k];
+                }
+                gi[nn] = s0;
+                dgi[nn] = s1;
+                gj[nn] = s2;
+                dgj[nn] = s3;
+            }
+            const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+            real Y[kNLM], Gs[kNLM], Gj[kNLM];
+            sh_eval(ux, uy, uz, Y);
+            const real* phi_j = a.phi + (size_t)j * kNLM * NA;
+            real si = real(0), sj = real(0);
+#pragma unroll
+            for (int k = 0; k < kNLM; ++k) {
+                const real lr = real(l_of(k)) * inv_r;
+                const real sg = (l_of(k) & 1) ? real(-1) : real(1);
+                real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
+#pragma unroll
+                for (int nn = 0; nn < NA; ++nn) {
+                    const real pi_ = phi_i[k * NA + nn], pj = phi_j[k * NA + nn];
+                    Gi_ += pi_ * gi[nn];
+                    dGi += pi_ * dgi[nn];
+                    Gj_ += pj * gj[nn];
+                    dGj += pj * dgj[nn];
+                }
+                Gj_ *= sg;
+                dGj *= sg;
+                si += (dGi - lr * Gi_) * Y[k];
+                sj += (dGj - lr * Gj_) * Y[k];
+                Gs[k] = Gi_ + Gj_;
+                Gj[k] = Gj_;
+            }
+            real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
+            sh_grad2(ux, uy, uz, Gs, Gj, ga, gb);
+            // F_i += f_ij - f_ji ;  -f_ji = sj u + gb / r
+            const real u[3] = {ux, uy, uz}, d[3] = {dx, dy, dz};
+            real vj[3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                F[p] += (si + sj) * u[p] + ga[p] * inv_r;
+                vj[p] = sj * u[p] + gb[p] * inv_r;
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) W[3 * p + q] -= d[p] * vj[q];
+        }
+
+        const int ui = a.perm[i];
+        const real Ui = a.U[i];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) a.force[(size_t)p * a.n + ui] = (double)F[p];
+        if (a.virial) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) a.virial[(size_t)k * a.n + ui] = (double)W[k];
+        }
+        if (a.site) a.site[ui] = (double)Ui;
+        tot[0] = (double)Ui;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)W[k];
+    }
+    reduce_totals(tot, a.partial, a.counter, a.totals);
+}
+
+// ---- shape dispatch -----------------------------------------------------------
+#define NEP_SHAPES(X) X(5, 4, 8, 8) X(5, 5, 9, 9)
+
+template <typename real>
+bool evaluate_shape_supported(int nR, int nA, int KR, int KA)
+{
+#define NEP_CASE(a_, b_, c_, d_) \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) return true;
+    NEP_SHAPES(NEP_CASE)
+#undef NEP_CASE
+    return false;
+}
+
+template <typename real>
+cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, size_t smem_force)
+{
+#define NEP_CASE(a_, b_, c_, d_)                                                                              \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                       \
+        cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_>,                              \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
+        if (e != cudaSuccess) return e;                                                                       \
+        return cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    (int)smem_force);                                                         \
+    }
+    NEP_SHAPES(NEP_CASE)
+#undef NEP_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <typename real>
+cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, size_t smem_desc,
+                            size_t smem_force, cudaStream_t st, cudaEvent_t mid)
+{
+    const int nb = (a.n + kBlock - 1) / kBlock;
+#define NEP_CASE(a_, b_, c_, d_)                                                          \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                   \
+        k_descriptor<real, a_, b_, c_, d_><<<nb, kBlock, smem_desc, st>>>(a);             \
+        if (mid) cudaEventRecord(mid, st);                                                \
+        k_force<real, a_, b_, c_, d_><<<nb, kBlock, smem_force, st>>>(a);                 \
+        return cudaGetLastError();                                                        \
+    }
+    NEP_SHAPES(NEP_CASE)
+#undef NEP_CASE
+    return cudaErrorInvalidValue;
+}
+
+#define NEP_INSTANTIATE(real)                                                                             \
+    template bool evaluate_shape_supported<real>(int, int, int, int);                                     \
+    template cudaError_t evaluate_set_smem<real>(int, int, int, int, size_t, size_t);                     \
+    template cudaError_t launch_evaluate<real>(int, int, int, int, const EvalArgs<real>&, size_t, size_t, \
+                                               cudaStream_t, cudaEvent_t);
+NEP_INSTANTIATE(float)
+NEP_INSTANTIATE(double)
+#undef NEP_INSTANTIATE
+
+}  // namespace nep

@@ -1,0 +1,109 @@
+"""Generate sh_poly.cuh: real orthonormal spherical harmonics l = 1..4 as homogeneous
+harmonic polynomials of the unit vector, and the gradient contraction
+sum_lm G_lm grad Y_lm used by the force kernel.
+
+Run with sympy available:  python gen_sh.py > sh_poly.cuh
+The script checks harmonicity, homogeneity and orthonormality before writing.
+"""
+import sys
+
+import numpy as np
+import sympy as sp
+from numpy.polynomial import legendre as npleg
+
+x, y, z = sp.symbols("x y z", real=True)
+r2 = x * x + y * y + z * z
+pi = sp.pi
+S = sp.sqrt
+Q = sp.Rational
+
+# (l, m) -> homogeneous harmonic polynomial of degree l, normalised on the unit sphere
+Y = {
+    (1, -1): S(3 / (4 * pi)) * y, (1, 0): S(3 / (4 * pi)) * z, (1, 1): S(3 / (4 * pi)) * x,
+    (2, -2): S(15 / pi) / 2 * x * y, (2, -1): S(15 / pi) / 2 * y * z,
+    (2, 0): S(5 / pi) / 4 * (2 * z * z - x * x - y * y),
+    (2, 1): S(15 / pi) / 2 * x * z, (2, 2): S(15 / pi) / 4 * (x * x - y * y),
+    (3, -3): S(35 / (2 * pi)) / 4 * y * (3 * x * x - y * y), (3, -2): S(105 / pi) / 2 * x * y * z,
+    (3, -1): S(21 / (2 * pi)) / 4 * y * (4 * z * z - x * x - y * y),
+    (3, 0): S(7 / pi) / 4 * z * (2 * z * z - 3 * x * x - 3 * y * y),
+    (3, 1): S(21 / (2 * pi)) / 4 * x * (4 * z * z - x * x - y * y),
+    (3, 2): S(105 / pi) / 4 * z * (x * x - y * y), (3, 3): S(35 / (2 * pi)) / 4 * x * (x * x - 3 * y * y),
+    (4, -4): Q(3, 4) * S(35 / pi) * x * y * (x * x - y * y),
+    (4, -3): Q(3, 4) * S(35 / (2 * pi)) * y * z * (3 * x * x - y * y),
+    (4, -2): Q(3, 4) * S(5 / pi) * x * y * (6 * z * z - x * x - y * y),
+    (4, -1): Q(3, 4) * S(5 / (2 * pi)) * y * z * (4 * z * z - 3 * x * x - 3 * y * y),
+    (4, 0): Q(3, 16) * S(1 / pi) * (35 * z ** 4 - 30 * z * z * r2 + 3 * r2 * r2),
+    (4, 1): Q(3, 4) * S(5 / (2 * pi)) * x * z * (4 * z * z - 3 * x * x - 3 * y * y),
+    (4, 2): Q(3, 8) * S(5 / pi) * (x * x - y * y) * (6 * z * z - x * x - y * y),
+    (4, 3): Q(3, 4) * S(35 / (2 * pi)) * x * z * (x * x - 3 * y * y),
+    (4, 4): Q(3, 16) * S(35 / pi) * (x * x * (x * x - 3 * y * y) - y * y * (3 * x * x - y * y)),
+}
+KEYS = [(l, m) for l in range(1, 5) for m in range(-l, l + 1)]
+
+
+def check():
+    for k in KEYS:
+        v = Y[k]
+        assert sp.simplify(sp.diff(v, x, 2) + sp.diff(v, y, 2) + sp.diff(v, z, 2)) == 0
+        p = sp.Poly(sp.expand(v), x, y, z)
+        assert p.is_homogeneous and p.total_degree() == k[0]
+    xg, wg = npleg.leggauss(20)
+    nphi = 40
+    ph = 2 * np.pi * np.arange(nphi) / nphi
+    ct = np.repeat(xg, nphi)
+    st = np.sqrt(1 - ct ** 2)
+    pp = np.tile(ph, len(xg))
+    X, Yv, Z = st * np.cos(pp), st * np.sin(pp), ct
+    w = np.repeat(wg, nphi) * 2 * np.pi / nphi
+    M = np.array([sp.lambdify((x, y, z), Y[k], "numpy")(X, Yv, Z) * np.ones_like(X) for k in KEYS])
+    assert np.abs((M * w) @ M.T - np.eye(len(KEYS))).max() < 1e-12
+
+
+def c(expr):
+    e = sp.expand(sp.N(expr, 20))
+    s = sp.ccode(e)
+    # numeric literals -> real(...) so that float kernels stay in float
+    import re
+    s = re.sub(r"(\d+\.\d+(e[-+]?\d+)?)", r"real(\1)", s)
+    return re.sub(r"pow\(([xyz]), (\d)\)", r"\1\2", s)
+
+
+MONO = ("    const real x2 = x * x, y2 = y * y, z2 = z * z, x3 = x2 * x, y3 = y2 * y, z3 = z2 * z;\n"
+        "    const real x4 = x2 * x2, y4 = y2 * y2, z4 = z2 * z2;\n"
+        "    (void)x3; (void)y3; (void)z3; (void)x4; (void)y4; (void)z4;")
+
+
+def emit():
+    out = []
+    out.append("// Generated by gen_sh.py -- real orthonormal spherical harmonics, l = 1..4.")
+    out.append("// Index k = l*l - 1 + (m + l); each Y_k is a homogeneous harmonic polynomial of")
+    out.append("// degree l in the components of the unit vector (x, y, z).")
+    out.append("#pragma once")
+    out.append("")
+    out.append("template <typename real>")
+    out.append("__device__ __forceinline__ void sh_eval(real x, real y, real z, real* Y)")
+    out.append("{")
+    out.append(MONO)
+    for i, k in enumerate(KEYS):
+        out.append(f"    Y[{i}] = {c(Y[k])};")
+    out.append("}")
+    out.append("")
+    out.append("// ga += sum_k A[k] grad Y_k,  gb += sum_k B[k] grad Y_k  (gradient of the polynomial)")
+    out.append("template <typename real>")
+    out.append("__device__ __forceinline__ void sh_grad2(real x, real y, real z, const real* A, const real* B,")
+    out.append("                                         real* ga, real* gb)")
+    out.append("{")
+    out.append(MONO)
+    for i, k in enumerate(KEYS):
+        for d, var in enumerate((x, y, z)):
+            e = sp.diff(Y[k], var)
+            if e == 0:
+                continue
+            out.append(f"    {{ const real t = {c(e)}; ga[{d}] += A[{i}] * t; gb[{d}] += B[{i}] * t; }}")
+    out.append("}")
+    return "\n".join(out) + "\n"
+
+
+if __name__ == "__main__":
+    check()
+    sys.stdout.write(emit())

@@ -1,0 +1,147 @@
+// Velocity-Verlet NVE integration in FP64 (the MD loop in which the potential is
+// evaluated) and the kinetic-energy sample.
+//   k_kick_drift   v += dt/2 F/m ;  r += dt v ;  wrap periodic axes to [0, L)
+//   k_kick         v += dt/2 F/m
+//   k_sample       E_kin = sum 1/2 m v^2 (FP64, deterministic last-block total) and
+//                  one thermo row (step, E_pot, E_kin, W[9])
+#include "nep_common.cuh"
+
+namespace nep {
+
+// 1 eV / (Angstrom amu) in Angstrom / fs^2 (acceleration of a force in eV/A on a mass in amu)
+constexpr double kAcc = 9.648533212e-3;
+constexpr int kMdMaxTypes = 16;
+
+struct TypeTable {
+    double v[kMdMaxTypes];
+};
+
+__global__ void __launch_bounds__(kBlock) k_kick_drift(int n, const int* __restrict__ types, TypeTable inv_m_acc,
+                                                       double half_dt, double dt, CellGrid g, double* __restrict__ pos,
+                                                       double* __restrict__ vel, const double* __restrict__ force)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double im = inv_m_acc.v[types[i]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const size_t k = (size_t)a * n + i;
+        const double v = vel[k] + half_dt * force[k] * im;
+        vel[k] = v;
+        double x = pos[k] + dt * v;
+        if (g.pbc[a]) {
+            x = x - g.box[a] * floor(x / g.box[a]);
+            if (x >= g.box[a] || x < 0.0) x = 0.0;
+        }
+        pos[k] = x;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_kick(int n, const int* __restrict__ types, TypeTable inv_m_acc,
+                                                 double half_dt, double* __restrict__ vel,
+                                                 const double* __restrict__ force)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double im = inv_m_acc.v[types[i]];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const size_t k = (size_t)a * n + i;
+        vel[k] += half_dt * force[k] * im;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sample(int n, const int* __restrict__ types, TypeTable mass,
+                                                   const double* __restrict__ vel, const double* __restrict__ totals,
+                                                   double* __restrict__ partial, unsigned int* __restrict__ counter,
+                                                   double* __restrict__ thermo, int* __restrict__ sample_index,
+                                                   int step_stride)
+{
+    __shared__ double red[kBlock / 32];
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < n) {
+        const double m = mass.v[types[i]];
+        for (int a = 0; a < 3; ++a) {
+            const double v = vel[(size_t)a * n + i];
+            ke += 0.5 * m * v * v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ke;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += red[w];
+        partial[blockIdx.x] = s;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const volatile double* p = partial;
+    double s = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) s += p[b];
+    const int row = *sample_index;
+    double* t = thermo + (size_t)row * 12;
+    t[0] = (double)((row + 1) * step_stride);
+    t[1] = totals[0];
+    t[2] = s / kAcc;
+    for (int k = 0; k < 9; ++k) t[3 + k] = totals[1 + k];
+    *sample_index = row + 1;
+    *counter = 0u;
+}
+
+__global__ void k_scale(int n, double* __restrict__ pos, double sx, double sy, double sz)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pos[i] *= sx;
+    pos[(size_t)n + i] *= sy;
+    pos[(size_t)2 * n + i] *= sz;
+}
+
+static TypeTable make_table(const double* v, int T)
+{
+    TypeTable t;
+    for (int k = 0; k < kMdMaxTypes; ++k) t.v[k] = k < T ? v[k] : 0.0;
+    return t;
+}
+
+cudaError_t launch_kick_drift(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double dt,
+                              const CellGrid& g, double* pos, double* vel, const double* force, cudaStream_t st)
+{
+    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
+    k_kick_drift<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(inv_m_acc, T), half_dt, dt, g,
+                                                               pos, vel, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double* vel,
+                        const double* force, cudaStream_t st)
+{
+    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
+    k_kick<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(inv_m_acc, T), half_dt, vel, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(int n, const int* types, const double* mass, int T, const double* vel,
+                          const double* totals, double* partial, unsigned int* counter, double* thermo,
+                          int* sample_index, int step_stride, cudaStream_t st)
+{
+    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
+    k_sample<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(mass, T), vel, totals, partial,
+                                                           counter, thermo, sample_index, step_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(int n, double* pos, double sx, double sy, double sz, cudaStream_t st)
+{
+    k_scale<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, pos, sx, sy, sz);
+    return cudaGetLastError();
+}
+
+}  // namespace nep

@@ -1,0 +1,287 @@
+// Cell list and neighbour lists (the neighbour search that precedes Eq. 3-5).
+//
+// Per configuration:
+//   k_bin        wrap periodic axes, bin every particle into a cell, store its
+//                cell-relative position (FP32 or FP64) and count cell members
+//   k_scan_*     exclusive scan of the cell counts (two levels)
+//   k_scatter    counting-sort scatter of particle indices into cell order
+//   k_cell_sort  sort each cell's members by caller index (deterministic order)
+//                and gather the records into cell order
+//   k_neighbors  one thread per particle scans the (2S+1)^3 surrounding cells and
+//                writes the radial (r < r_c^R) and angular (r < r_c^A) lists
+#include "nep_common.cuh"
+
+namespace nep {
+
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_bin(int n, const double* __restrict__ pos, const int* __restrict__ types,
+                                                int T, CellGrid g, int* __restrict__ cell_of,
+                                                PosRec<real>* __restrict__ rec, int* __restrict__ cell_count,
+                                                int* __restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c3[3];
+    real xr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double x = pos[(size_t)a * n + i];
+        if (!isfinite(x)) {
+            atomicOr(err, 1);
+            x = 0.0;
+        }
+        if (g.pbc[a]) {
+            x = x - g.box[a] * floor(x / g.box[a]);
+            if (x >= g.box[a] || x < 0.0) x = 0.0;
+        }
+        double cf = floor(x / g.len[a]);
+        int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
+        c3[a] = c;
+        xr[a] = (real)(x - (double)c * g.len[a]);
+    }
+    int t = types[i];
+    if (t < 0 || t >= T) {
+        atomicOr(err, 2);
+        t = 0;
+    }
+    const int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+    cell_of[i] = cell;
+    PosRec<real> r;
+    r.x = xr[0];
+    r.y = xr[1];
+    r.z = xr[2];
+    r.t = t;
+    rec[i] = r;
+    atomicAdd(&cell_count[cell], 1);
+}
+
+// Block-local exclusive scan of kScanItems counts (4 per thread, 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan_local(int ncell, const int* __restrict__ count,
+                                                     int* __restrict__ local, int* __restrict__ block_sum)
+{
+    __shared__ int warp_tot[32];
+    const int base = blockIdx.x * kScanItems + threadIdx.x * 4;
+    int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < ncell) ? count[base + k] : 0;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) block_sum[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    int run = warp_tot[warp] + incl - s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < ncell) local[base + k] = run;
+        run += v[k];
+    }
+}
+
+// Exclusive scan of the block sums in place (one block; nb <= 4096).
+__global__ void __launch_bounds__(1024) k_scan_top(int nb, int* __restrict__ block_sum)
+{
+    __shared__ int warp_tot[32];
+    const int base = threadIdx.x * 4;
+    int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < nb) ? block_sum[base + k] : 0;
+        s += v[k];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        warp_tot[lane] = wi - w;
+    }
+    __syncthreads();
+    int run = warp_tot[warp] + incl - s;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < nb) block_sum[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scatter(int n, const int* __restrict__ cell_of,
+                                                    const int* __restrict__ local, const int* __restrict__ block_off,
+                                                    int* __restrict__ fill, int* __restrict__ perm)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell_of[i];
+    const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
+    perm[slot] = i;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_cell_sort(int ncell, int n, const int* __restrict__ count,
+                                                      const int* __restrict__ local,
+                                                      const int* __restrict__ block_off, int* __restrict__ perm,
+                                                      int* __restrict__ cell_start, int* __restrict__ cell_s,
+                                                      const PosRec<real>* __restrict__ rec,
+                                                      PosRec<real>* __restrict__ rec_s)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int b = local[c] + block_off[c / kScanItems];
+    const int e = b + count[c];
+    cell_start[c] = b;
+    if (c == ncell - 1) cell_start[ncell] = e;
+    for (int k = b + 1; k < e; ++k) {  // insertion sort by caller index
+        const int v = perm[k];
+        int q = k - 1;
+        while (q >= b && perm[q] > v) {
+            perm[q + 1] = perm[q];
+            --q;
+        }
+        perm[q + 1] = v;
+    }
+    for (int k = b; k < e; ++k) {
+        rec_s[k] = rec[perm[k]];
+        cell_s[k] = c;
+    }
+}
+
+template <typename real>
+cudaError_t launch_cell_build(int n, const double* pos, const int* types, int T, const CellGrid& g,
+                              int* cell_of, PosRec<real>* rec_user, int* cell_count, int* cell_start_local,
+                              int* block_off, int* cell_fill, int* perm, int* cell_start, int* cell_s,
+                              PosRec<real>* rec_sorted, int* err, cudaStream_t st)
+{
+    const int nb_scan = (g.ncell + kScanItems - 1) / kScanItems;
+    if (nb_scan > kScanItems) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * g.ncell, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * g.ncell, st)) != cudaSuccess) return e;
+    const int nbp = (n + kBlock - 1) / kBlock;
+    k_bin<real><<<nbp, kBlock, 0, st>>>(n, pos, types, T, g, cell_of, rec_user, cell_count, err);
+    k_scan_local<<<nb_scan, 1024, 0, st>>>(g.ncell, cell_count, cell_start_local, block_off);
+    k_scan_top<<<1, 1024, 0, st>>>(nb_scan, block_off);
+    k_scatter<<<nbp, kBlock, 0, st>>>(n, cell_of, cell_start_local, block_off, cell_fill, perm);
+    k_cell_sort<real><<<(g.ncell + kBlock - 1) / kBlock, kBlock, 0, st>>>(
+        g.ncell, n, cell_count, cell_start_local, block_off, perm, cell_start, cell_s, rec_user, rec_sorted);
+    return cudaGetLastError();
+}
+
+// One thread per sorted particle i: scan the cells at offsets [-S, S]^3 from i's
+// cell and keep every (j, offset) with r^2 < r_c^2(t_i, t_j).
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
+{
+    extern __shared__ unsigned char smem_raw[];
+    real* cut = reinterpret_cast<real*>(smem_raw);  // rcR2[T*T], rcA2[T*T]
+    const int TT = a.T * a.T;
+    for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+        cut[k] = a.params[a.off.rcR2 + k];
+        cut[TT + k] = a.params[a.off.rcA2 + k];
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nr = 0, na = 0;
+    if (i < a.n) {
+        const PosRec<real> ri = a.rec[i];
+        const int c = a.cell_s[i];
+        const int cx = c % a.g.nc[0], cy = (c / a.g.nc[0]) % a.g.nc[1], cz = c / (a.g.nc[0] * a.g.nc[1]);
+        const real* cutR = cut + ri.t * a.T;
+        const real* cutA = cut + TT + ri.t * a.T;
+        const real lx = (real)a.g.len[0], ly = (real)a.g.len[1], lz = (real)a.g.len[2];
+        for (int dz = -a.g.S[2]; dz <= a.g.S[2]; ++dz) {
+            int z = cz + dz;
+            if (a.g.pbc[2]) z = ((z % a.g.nc[2]) + a.g.nc[2]) % a.g.nc[2];
+            else if (z < 0 || z >= a.g.nc[2]) continue;
+            for (int dy = -a.g.S[1]; dy <= a.g.S[1]; ++dy) {
+                int y = cy + dy;
+                if (a.g.pbc[1]) y = ((y % a.g.nc[1]) + a.g.nc[1]) % a.g.nc[1];
+                else if (y < 0 || y >= a.g.nc[1]) continue;
+                for (int dx = -a.g.S[0]; dx <= a.g.S[0]; ++dx) {
+                    int x = cx + dx;
+                    if (a.g.pbc[0]) x = ((x % a.g.nc[0]) + a.g.nc[0]) % a.g.nc[0];
+                    else if (x < 0 || x >= a.g.nc[0]) continue;
+                    const int cell = (z * a.g.nc[1] + y) * a.g.nc[0] + x;
+                    const real ox = (real)dx * lx - ri.x, oy = (real)dy * ly - ri.y, oz = (real)dz * lz - ri.z;
+                    const bool centre = (dx == 0 && dy == 0 && dz == 0);
+                    const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+                    for (int k = kb; k < ke; ++k) {
+                        if (centre && k == i) continue;
+                        const PosRec<real> rj = a.rec[k];
+                        const real ddx = rj.x + ox, ddy = rj.y + oy, ddz = rj.z + oz;
+                        const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        const uint32_t ent = pack_entry(k, dx, dy, dz);
+                        if (r2 < cutR[rj.t]) {
+                            if (nr < a.mnR) a.nlR[(size_t)nr * a.n + i] = ent;
+                            ++nr;
+                        }
+                        if (r2 < cutA[rj.t]) {
+                            if (na < a.mnA) a.nlA[(size_t)na * a.n + i] = ent;
+                            ++na;
+                        }
+                    }
+                }
+            }
+        }
+        a.cntR[i] = nr;
+        a.cntA[i] = na;
+    }
+    // warp maxima, then one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nr = max(nr, __shfl_xor_sync(0xffffffffu, nr, o));
+        na = max(na, __shfl_xor_sync(0xffffffffu, na, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&a.maxcnt[0], nr);
+        atomicMax(&a.maxcnt[1], na);
+    }
+}
+
+template <typename real>
+cudaError_t launch_neighbors(const NeighborArgs<real>& a, cudaStream_t st)
+{
+    const size_t smem = 2 * sizeof(real) * a.T * a.T;
+    k_neighbors<real><<<(a.n + kBlock - 1) / kBlock, kBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define NEP_INSTANTIATE(real)                                                                                     \
+    template cudaError_t launch_cell_build<real>(int, const double*, const int*, int, const CellGrid&, int*,      \
+                                                 PosRec<real>*, int*, int*, int*, int*, int*, int*, int*,         \
+                                                 PosRec<real>*, int*, cudaStream_t);                              \
+    template cudaError_t launch_neighbors<real>(const NeighborArgs<real>&, cudaStream_t);
+NEP_INSTANTIATE(float)
+NEP_INSTANTIATE(double)
+#undef NEP_INSTANTIATE
+
+}  // namespace nep
