@@ -859,7 +859,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
                         ? evaluate_set_smem<double>(m->nR, m->nA, m->KR, m->KA, smem_cap, smem_cap)
                         : evaluate_set_smem<float>(m->nR, m->nA, m->KR, m->KA, smem_cap, smem_cap);
     if (e != cudaSuccess) return cleanup(fail(NEP_ERR_CUDA, std::string("smem attribute: ") + cudaGetErrorString(e)));
-    if (cudaStreamCreateWithFlags(&m->cur, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_flags, cudaEventDisableTiming) != cudaSuccess)
@@ -881,7 +881,7 @@ int nep_destroy(nep_model* m)
 {
     if (!m) return NEP_OK;
     Guard guard(m->device);
-    if (m->cur) cudaStreamSynchronize(m->cur);
+    if (m->st) cudaStreamSynchronize(m->st);
     m->graph.reset();
     m->timer.destroy();
     Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm, &m->rec_s, &m->cell_s, &m->cntR, &m->cntA,
