@@ -189,6 +189,39 @@ int nep_set_timing(nep_model* m, int enable);
  */
 int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
 
+/*
+ * nep_compute_static -- nep_compute that allocates no device memory.
+ * The paper has no counterpart: this exists for callers of this library that
+ * cannot allocate.  cudaFree, and cudaMalloc when its pool must grow, synchronise
+ * the whole device; an allocation can fail mid-simulation when other parts of the
+ * program hold the memory; and hosts that budget every byte of device memory at
+ * start-up (an MD engine, a serving process) forbid hidden allocations.
+ *
+ * The scratch is one fixed array in device global memory that is part of the
+ * library image: 11,505,408 bytes (about 11 MiB), held on every GPU that loads the
+ * library until the process exits.  Limits of one call: n <= 4096 particles, a
+ * cell grid of at most 32768 cells, at most 256 radial and 128 angular neighbours
+ * per particle.  Larger inputs are rejected with NEP_ERR_ARG (the message names
+ * the limit); more neighbours give NEP_ERR_NEIGHBOR_OVERFLOW.
+ *
+ *   m             a handle from nep_create (its parameters are read, nothing grows)
+ *   types, pos    device arrays as in nep_compute with mem = NEP_DEVICE
+ *   box, pbc      host arrays
+ *   stream        cudaStream_t, or NULL for the legacy default stream
+ *   outputs       device arrays, each may be NULL, as in nep_compute
+ * The results equal nep_compute's (same kernels, same order).  The call returns
+ * when they are written; it calls no cudaMalloc, cudaFree or other allocating
+ * routine.  Set-up: the first call on a device, with that device current, looks
+ * up the array's device address (cudaGetSymbolAddress) once; make that first call
+ * before any stream capture.  Every call on every handle shares the one array and
+ * leaves its contents behind (the words that must start at zero are cleared by
+ * each call), so calls whose GPU work overlaps -- from different handles, streams
+ * or threads -- race and give wrong results: serialise them.
+ */
+int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                       const int32_t pbc[3], void* stream, double* energy_total, double* virial_total,
+                       double* site_energy, double* force, double* virial);
+
 /* Current neighbour-list capacities (entries per particle). */
 int nep_get_capacity(nep_model* m, int* radial, int* angular);
 

@@ -32,7 +32,8 @@ NEP_DEVICE = 1
 
 EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "nep_supported_shape",
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
-            "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing"]
+            "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
+            "nep_compute_static"]
 
 _lib = None
 
@@ -91,6 +92,8 @@ def load(build_if_missing: bool = False):
     lib.nep_set_timing.restype = i
     lib.nep_get_timing.argtypes = [p, p, C.POINTER(C.c_longlong)]
     lib.nep_get_timing.restype = i
+    lib.nep_compute_static.argtypes = [p, i, p, p, p, p, p, p, p, p, p, p]
+    lib.nep_compute_static.restype = i
     _lib = lib
     return lib
 
@@ -164,6 +167,17 @@ def nep_compute(h, types, pos, box, pbc, energy_total=None, virial_total=None, s
     _check(load().nep_compute(h, n, _ptr(types), _ptr(pos), _ptr(box), _ptr(pbc), mem, _stream_of(pos, stream),
                               _ptr(energy_total), _ptr(virial_total), _ptr(site_energy), _ptr(force), _ptr(virial)),
            "nep_compute")
+
+
+def nep_compute_static(h, types, pos, box, pbc, energy_total=None, virial_total=None, site_energy=None,
+                       force=None, virial=None, stream=None):
+    """Allocation-free evaluation: torch CUDA tensors only (device memory), n <= 4096."""
+    n = int(types.shape[0])
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    _check(load().nep_compute_static(h, n, _ptr(types), _ptr(pos), _ptr(box), _ptr(pbc), _stream_of(pos, stream),
+                                     _ptr(energy_total), _ptr(virial_total), _ptr(site_energy), _ptr(force),
+                                     _ptr(virial)), "nep_compute_static")
 
 
 def nep_md_step(h, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs, sample_every=0,

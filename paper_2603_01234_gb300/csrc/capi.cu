@@ -1000,3 +1000,205 @@ int nep_set_capacity(nep_model* m, int radial, int angular)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// nep_compute_static: nep_compute without any device allocation.
+//
+// Some callers cannot let a library call cudaMalloc or cudaFree: cudaFree (and,
+// when the pool has to grow, cudaMalloc) synchronises the whole device, an
+// allocation can fail in the middle of a long simulation when another part of the
+// program holds the memory, and hosts that account for every byte of device
+// memory (an MD engine with a fixed budget, a serving process sized at start-up)
+// forbid hidden allocations.  For them this entry point takes its scratch from
+// one fixed array in device global memory that is part of the library image.
+// The array costs kStaticScratchBytes on every GPU that loads the library, until
+// the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int kStaticMaxN = 4096;        // particles per call
+constexpr int kStaticMaxCells = 32768;   // cells of the call's grid
+constexpr int kStaticMNR = 256;          // radial neighbours per particle
+constexpr int kStaticMNA = 128;          // angular neighbours per particle
+constexpr int kStaticMaxNA = 5;          // n_A of the compiled shapes
+constexpr int kStaticMaxNRP = 8;         // padded n_R
+constexpr int kStaticMaxDevices = 64;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Byte layout of the scratch for n particles, ncell cells, real of rs bytes.
+struct StaticLayout {
+    size_t cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, U, dq, phi, force;
+    size_t nlR, nlA, cell_count, cell_local, block_off, cell_fill, cell_start;
+    size_t partial, counters, totals, flags, end;
+};
+
+constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t nA, size_t nrp)
+{
+    StaticLayout L{};
+    size_t p = 0;
+    L.cell_of = p; p = align256(p + 4 * n);
+    L.rec_user = p; p = align256(p + 4 * rs * n);
+    L.perm = p; p = align256(p + 4 * n);
+    L.rec_s = p; p = align256(p + 4 * rs * n);
+    L.cell_s = p; p = align256(p + 4 * n);
+    L.cntR = p; p = align256(p + 4 * n);
+    L.cntA = p; p = align256(p + 4 * n);
+    L.U = p; p = align256(p + rs * n);
+    L.dq = p; p = align256(p + rs * nrp * n);
+    L.phi = p; p = align256(p + rs * 24 * nA * n);
+    L.force = p; p = align256(p + 8 * 3 * n);
+    L.nlR = p; p = align256(p + 4 * (size_t)kStaticMNR * n);
+    L.nlA = p; p = align256(p + 4 * (size_t)kStaticMNA * n);
+    L.cell_count = p; p = align256(p + 4 * ncell);
+    L.cell_local = p; p = align256(p + 4 * ncell);
+    L.block_off = p; p = align256(p + 4 * (kScanItems + 1));
+    L.cell_fill = p; p = align256(p + 4 * ncell);
+    L.cell_start = p; p = align256(p + 4 * (ncell + 1));
+    L.partial = p; p = align256(p + 8 * 10 * ((n + kBlock - 1) / kBlock));
+    L.counters = p; p = align256(p + 16);
+    L.totals = p; p = align256(p + 8 * 10);
+    L.flags = p; p = align256(p + 16);
+    L.end = p;
+    return L;
+}
+
+// worst case: FP64, the largest compiled n_A, every limit at its maximum
+constexpr size_t kStaticScratchBytes =
+    align256(static_layout(kStaticMaxN, kStaticMaxCells, 8, kStaticMaxNA, kStaticMaxNRP).end);
+
+// The scratch.  In host code this name is only a stand-in for the device symbol;
+// its device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mutex;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+// Device address of the scratch on `device` (current device); resolved once per device.
+int static_scratch(int device, unsigned char** out)
+{
+    if (device < 0 || device >= kStaticMaxDevices) return fail(NEP_ERR_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(NEP_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        g_static_ptr[device] = p;
+    }
+    *out = (unsigned char*)g_static_ptr[device];
+    return NEP_OK;
+}
+
+template <typename real>
+int compute_static_impl(nep_model* m, int n, const int32_t* types, const double* pos, const CellGrid& g,
+                        double* energy_total, double* virial_total, double* site_energy, double* force,
+                        double* virial)
+{
+    unsigned char* base = nullptr;
+    NEP_TRY(static_scratch(m->device, &base));
+    const StaticLayout L = static_layout(n, g.ncell, sizeof(real), m->nA, m->NRP);
+    if (L.end > kStaticScratchBytes) return fail(NEP_ERR_ARG, "static scratch too small for this call");
+    int* flags = (int*)(base + L.flags);
+    unsigned int* counters = (unsigned int*)(base + L.counters);
+    double* totals = (double*)(base + L.totals);
+    // what must start at zero: the overflow/error words and the last-block counter
+    // (the cell counters are cleared by the cell build itself)
+    NEP_CUDA(cudaMemsetAsync(flags, 0, 16, m->cur));
+    NEP_CUDA(cudaMemsetAsync(counters, 0, 16, m->cur));
+    cudaError_t e = launch_cell_build<real>(
+        n, pos, types, m->T, g, (int*)(base + L.cell_of), (PosRec<real>*)(base + L.rec_user),
+        (int*)(base + L.cell_count), (int*)(base + L.cell_local), (int*)(base + L.block_off),
+        (int*)(base + L.cell_fill), (int*)(base + L.perm), (int*)(base + L.cell_start), (int*)(base + L.cell_s),
+        (PosRec<real>*)(base + L.rec_s), flags + 2, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
+    NeighborArgs<real> na;
+    na.n = n;
+    na.T = m->T;
+    na.mnR = kStaticMNR;
+    na.mnA = kStaticMNA;
+    na.g = g;
+    na.cell_start = (int*)(base + L.cell_start);
+    na.cell_s = (int*)(base + L.cell_s);
+    na.rec = (PosRec<real>*)(base + L.rec_s);
+    na.params = m->params.as<real>();
+    na.off = m->off;
+    na.nlR = (uint32_t*)(base + L.nlR);
+    na.nlA = (uint32_t*)(base + L.nlA);
+    na.cntR = (int*)(base + L.cntR);
+    na.cntA = (int*)(base + L.cntA);
+    na.maxcnt = flags;
+    e = launch_neighbors<real>(na, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
+    EvalArgs<real> a;
+    a.n = n;
+    a.T = m->T;
+    a.H = m->H;
+    a.mnR = kStaticMNR;
+    a.mnA = kStaticMNA;
+    for (int k = 0; k < 3; ++k) a.len[k] = (real)g.len[k];
+    a.rec = na.rec;
+    a.nlR = na.nlR;
+    a.nlA = na.nlA;
+    a.cntR = na.cntR;
+    a.cntA = na.cntA;
+    a.params = na.params;
+    a.off = m->off;
+    a.U = (real*)(base + L.U);
+    a.dq = (real*)(base + L.dq);
+    a.phi = (real*)(base + L.phi);
+    a.perm = (int*)(base + L.perm);
+    a.force = force ? force : (double*)(base + L.force);
+    a.virial = virial;
+    a.site = site_energy;
+    a.partial = (double*)(base + L.partial);
+    a.counter = counters;
+    a.totals = totals;
+    e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, m->smem_desc, m->smem_force, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
+    if (energy_total) NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
+    if (virial_total)
+        NEP_CUDA(cudaMemcpyAsync(virial_total, totals + 1, 9 * sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
+    // the handle's pinned status buffer (allocated by nep_create) receives the words
+    NEP_CUDA(cudaMemcpyAsync(m->h_flags, flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
+    NEP_CUDA(cudaStreamSynchronize(m->cur));
+    if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
+    if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+    if (m->h_flags[0] > kStaticMNR || m->h_flags[1] > kStaticMNA)
+        return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "more neighbours than the static lists hold (256 radial, 128 angular)");
+    return NEP_OK;
+}
+
+}  // namespace
+
+extern "C" int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                                  const int32_t pbc[3], void* stream, double* energy_total, double* virial_total,
+                                  double* site_energy, double* force, double* virial)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if (n < 1 || n > kStaticMaxN)
+        return fail(NEP_ERR_ARG, "nep_compute_static: n must be in [1, 4096] (static scratch limit)");
+    if (!types || !pos || !box || !pbc) return fail(NEP_ERR_ARG, "null input array");
+    CellGrid g;
+    NEP_TRY(make_grid(m, box, pbc, g));
+    if (g.ncell > kStaticMaxCells)
+        return fail(NEP_ERR_ARG, "nep_compute_static: cell grid exceeds 32768 cells (static scratch limit)");
+    Guard guard(m->device);
+    m->cur = stream ? (cudaStream_t)stream : m->st;
+    if (!stream) {
+        NEP_CUDA(cudaEventRecord(m->ev_in, (cudaStream_t)0));
+        NEP_CUDA(cudaStreamWaitEvent(m->st, m->ev_in, 0));
+    }
+    int rc = m->precision == NEP_FP64
+                 ? compute_static_impl<double>(m, n, types, pos, g, energy_total, virial_total, site_energy, force,
+                                               virial)
+                 : compute_static_impl<float>(m, n, types, pos, g, energy_total, virial_total, site_energy, force,
+                                              virial);
+    if (!stream) {
+        NEP_CUDA(cudaEventRecord(m->ev_out, m->st));
+        NEP_CUDA(cudaStreamWaitEvent((cudaStream_t)0, m->ev_out, 0));
+    }
+    return rc;
+}
