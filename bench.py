@@ -64,29 +64,33 @@ def config_dict(system):
 
 # ---- algorithmic work per kernel (FMA = 2 flop; sin/cos, rsqrt, tanh, div = 1) ----
 def algorithmic_flops(m, pairs_r, pairs_a, n):
-    """Flops the formulas require per launch, from the shapes and the pair counts.
+    """Minimal flops of one evaluation per launch: every ordered pair's gradient
+    f_ij counted once (the gather form computes both directions, so it does more),
+    and the linear Chebyshev contractions of Eq. 6 moved to the bead level where
+    the sums allow it.  basis(K) = 10 + 5 (K - 2) for f_k, basis'(K) = 14 + 11 (K - 2)
+    for f_k and f_k'.
 
-    descriptor+network kernel
-      radial pair   13 (pair vector, r) + basis(K_R) + 2 n_R K_R (g_n) + n_R (q_n)
-      angular pair  13 + 3 (unit vector) + basis(K_A) + 2 n_A K_A + 60 (Y_lm, l<=4)
+    descriptor+network kernel, per
+      radial pair   13 (pair vector, r) + basis(K_R) + K_R (sum of f_k)
+      angular pair  16 (+ unit vector) + basis(K_A) + 2 n_A K_A (g_n) + 60 (Y_lm, l<=4)
                     + 2 n_A 24 (A_nlm)
-      per bead      2 n_A 24 (q_nl) + H (4 N_des + 6) + 2 n_A 24 (Phi)
-    force+virial kernel
-      radial pair   13 + basis'(K_R) + 4 n_R K_R (g' both directions) + 4 n_R + 3 + 6 (F) + 18 (W)
-      angular pair  13 + 3 + basis'(K_A) + 8 n_A K_A (g, g' both directions) + 60 (Y_lm)
-                    + 24 (8 n_A + 12) (G, G', s_i, s_j) + 420 (sum_lm G grad Y_lm, both)
-                    + 12 (F, v_j) + 18 (W)
-    with basis(K) = 10 + 5 (K - 2) and basis'(K) = 14 + 11 (K - 2).
+      bead          2 T n_R K_R (q_n) + 2 n_A 24 (q_nl) + H (4 N_des + 6) (Eq. 2 and dU/dq)
+                    + 2 T n_R K_R (radial gradient in the basis) + 2 n_A 24 (Phi)
+    force+virial kernel, per
+      radial pair   13 + basis'(K_R) + 2 K_R (f_ij) + 6 (F) + 18 (W)
+      angular pair  16 + basis'(K_A) + 4 n_A K_A (g, g') + 150 (Y_lm and grad Y_lm)
+                    + 24 (4 n_A + 10) (one direction's contraction) + 12 (F) + 18 (W)
     """
-    nR, nA, KR, KA, H = m.n_desc_radial, m.n_desc_angular, m.n_basis_radial, m.n_basis_angular, m.hidden
+    nR, nA, KR, KA, H, T = (m.n_desc_radial, m.n_desc_angular, m.n_basis_radial, m.n_basis_angular, m.hidden,
+                            m.n_types)
     nd = nR + 4 * nA
     basis = lambda K: 10 + 5 * (K - 2)  # noqa: E731
     basis_d = lambda K: 14 + 11 * (K - 2)  # noqa: E731
-    d_r = 13 + basis(KR) + 2 * nR * KR + nR
+    d_r = 13 + basis(KR) + KR
     d_a = 16 + basis(KA) + 2 * nA * KA + 60 + 2 * nA * 24
-    d_b = 2 * nA * 24 + H * (4 * nd + 6) + 2 * nA * 24
-    f_r = 13 + basis_d(KR) + 4 * nR * KR + 4 * nR + 3 + 6 + 18
-    f_a = 16 + basis_d(KA) + 8 * nA * KA + 60 + 24 * (8 * nA + 12) + 420 + 12 + 18
+    d_b = 2 * T * nR * KR + 2 * nA * 24 + H * (4 * nd + 6) + 2 * T * nR * KR + 2 * nA * 24
+    f_r = 13 + basis_d(KR) + 2 * KR + 6 + 18
+    f_a = 16 + basis_d(KA) + 4 * nA * KA + 150 + 24 * (4 * nA + 10) + 12 + 18
     return {"descriptor_network": d_r * pairs_r + d_a * pairs_a + d_b * n,
             "force_virial": f_r * pairs_r + f_a * pairs_a}
 

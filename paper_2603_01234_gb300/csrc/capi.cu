@@ -150,13 +150,13 @@ struct GraphCache {
 struct nep_model {
     int device = 0;
     int precision = NEP_FP32;
-    int T = 1, nR = 0, nA = 0, KR = 0, KA = 0, L = 4, H = 0, ND = 0, NRP = 0;
+    int T = 1, nR = 0, nA = 0, KR = 0, KA = 0, L = 4, H = 0, ND = 0, KRP = 0;
     double rc_max = 0.0;
     std::vector<double> rcR, rcA;
     ParamLayout off{};
     Buf params;
     size_t real_size = 4;
-    size_t smem_desc = 0, smem_force = 0;
+    size_t smem_desc = 0, smem_force = 0, tile_offset = 0;
     int mnR = 0, mnA = 0;  // neighbour capacities
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
@@ -168,7 +168,7 @@ struct nep_model {
     int md_n = -1;
     CellGrid md_grid{};
     // workspace
-    Buf cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, dq, phi;
+    Buf cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp;
@@ -236,7 +236,7 @@ int ensure_particles(nep_model* m, int n)
     NEP_TRY(m->cntR.ensure(sizeof(int) * n));
     NEP_TRY(m->cntA.ensure(sizeof(int) * n));
     NEP_TRY(m->U.ensure(rs * n));
-    NEP_TRY(m->dq.ensure(rs * m->NRP * (size_t)n));
+    NEP_TRY(m->e.ensure(rs * m->T * m->KRP * (size_t)n));
     NEP_TRY(m->phi.ensure(rs * 24 * m->nA * (size_t)n));
     const size_t nb = (n + kBlock - 1) / kBlock;
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * nb));
@@ -336,7 +336,8 @@ int run_evaluate(nep_model* m, int n, const CellGrid& g, double* force, double* 
     a.params = m->params.as<real>();
     a.off = m->off;
     a.U = m->U.as<real>();
-    a.dq = m->dq.as<real>();
+    a.e = m->e.as<real>();
+    a.tile_offset = (int)m->tile_offset;
     a.phi = m->phi.as<real>();
     a.perm = m->perm.as<int>();
     a.force = force;
@@ -800,7 +801,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     m->L = l_max;
     m->H = hidden;
     m->ND = m->nR + m->nA * m->L;
-    m->NRP = (m->nR + 3) & ~3;
+    m->KRP = (m->KR + 3) & ~3;
     m->rcR.assign(rc_radial, rc_radial + T * T);
     m->rcA.assign(rc_angular, rc_angular + T * T);
     for (int k = 0; k < T * T; ++k) m->rc_max = std::max(m->rc_max, std::max(m->rcR[k], m->rcA[k]));
@@ -813,8 +814,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     const int TT = T * T;
     o.rcR2 = p; p += TT;
     o.rcA2 = p; p += TT;
-    o.rcR = p; p += TT;
-    o.rcA = p; p += TT;
+    o.rcRi = p; p += TT;
+    o.rcAi = p; p += TT;
     o.cR = p; p += TT * m->nR * m->KR;
     o.cA = p; p += TT * m->nA * m->KA;
     o.n_cut_coef = p;
@@ -827,8 +828,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     for (int k = 0; k < TT; ++k) {
         h[o.rcR2 + k] = m->rcR[k] * m->rcR[k];
         h[o.rcA2 + k] = m->rcA[k] * m->rcA[k];
-        h[o.rcR + k] = m->rcR[k];
-        h[o.rcA + k] = m->rcA[k];
+        h[o.rcRi + k] = 1.0 / m->rcR[k];
+        h[o.rcAi + k] = 1.0 / m->rcA[k];
     }
     std::copy(c_radial, c_radial + TT * m->nR * m->KR, h.begin() + o.cR);
     std::copy(c_angular, c_angular + TT * m->nA * m->KA, h.begin() + o.cA);
@@ -851,7 +852,10 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
     }
     m->smem_desc = m->real_size * o.total;
-    m->smem_force = m->real_size * o.n_cut_coef;
+    // the force kernel stages the cutoff + coefficient prefix, then (FP32) a
+    // [24][n_A][block] tile of the centre particles' Phi
+    m->tile_offset = (m->real_size * o.n_cut_coef + 15) & ~(size_t)15;
+    m->smem_force = m->tile_offset + (precision == NEP_FP32 ? sizeof(float) * 24 * m->nA * kBlock : 0);
     if (m->smem_desc > 200 * 1024) return cleanup(fail(NEP_ERR_ARG, "model too large for shared-memory staging"));
     // the attribute is per kernel, shared by all handles: allow the largest staging size
     const size_t smem_cap = 200 * 1024;
@@ -885,7 +889,7 @@ int nep_destroy(nep_model* m)
     m->graph.reset();
     m->timer.destroy();
     Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm, &m->rec_s, &m->cell_s, &m->cntR, &m->cntA,
-                   &m->nlR, &m->nlA, &m->U, &m->dq, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
+                   &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
                    &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
                    &m->site_d, &m->force_tmp};
@@ -1023,19 +1027,20 @@ constexpr int kStaticMaxCells = 32768;   // cells of the call's grid
 constexpr int kStaticMNR = 256;          // radial neighbours per particle
 constexpr int kStaticMNA = 128;          // angular neighbours per particle
 constexpr int kStaticMaxNA = 5;          // n_A of the compiled shapes
-constexpr int kStaticMaxNRP = 8;         // padded n_R
+constexpr int kStaticMaxT = 4;           // particle types of the model
+constexpr int kStaticMaxKRP = 12;        // padded K_R
 constexpr int kStaticMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for n particles, ncell cells, real of rs bytes.
 struct StaticLayout {
-    size_t cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, U, dq, phi, force;
+    size_t cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, U, e, phi, force;
     size_t nlR, nlA, cell_count, cell_local, block_off, cell_fill, cell_start;
     size_t partial, counters, totals, flags, end;
 };
 
-constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t nA, size_t nrp)
+constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t nA, size_t ekrp)
 {
     StaticLayout L{};
     size_t p = 0;
@@ -1047,7 +1052,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     L.cntR = p; p = align256(p + 4 * n);
     L.cntA = p; p = align256(p + 4 * n);
     L.U = p; p = align256(p + rs * n);
-    L.dq = p; p = align256(p + rs * nrp * n);
+    L.e = p; p = align256(p + rs * ekrp * n);
     L.phi = p; p = align256(p + rs * 24 * nA * n);
     L.force = p; p = align256(p + 8 * 3 * n);
     L.nlR = p; p = align256(p + 4 * (size_t)kStaticMNR * n);
@@ -1067,7 +1072,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
 
 // worst case: FP64, the largest compiled n_A, every limit at its maximum
 constexpr size_t kStaticScratchBytes =
-    align256(static_layout(kStaticMaxN, kStaticMaxCells, 8, kStaticMaxNA, kStaticMaxNRP).end);
+    align256(static_layout(kStaticMaxN, kStaticMaxCells, 8, kStaticMaxNA, kStaticMaxT * kStaticMaxKRP).end);
 
 // The scratch.  In host code this name is only a stand-in for the device symbol;
 // its device address comes from cudaGetSymbolAddress.
@@ -1099,7 +1104,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
 {
     unsigned char* base = nullptr;
     NEP_TRY(static_scratch(m->device, &base));
-    const StaticLayout L = static_layout(n, g.ncell, sizeof(real), m->nA, m->NRP);
+    const StaticLayout L = static_layout(n, g.ncell, sizeof(real), m->nA, (size_t)m->T * m->KRP);
     if (L.end > kStaticScratchBytes) return fail(NEP_ERR_ARG, "static scratch too small for this call");
     int* flags = (int*)(base + L.flags);
     unsigned int* counters = (unsigned int*)(base + L.counters);
@@ -1147,7 +1152,8 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.params = na.params;
     a.off = m->off;
     a.U = (real*)(base + L.U);
-    a.dq = (real*)(base + L.dq);
+    a.e = (real*)(base + L.e);
+    a.tile_offset = (int)m->tile_offset;
     a.phi = (real*)(base + L.phi);
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
@@ -1180,6 +1186,7 @@ extern "C" int nep_compute_static(nep_model* m, int n, const int32_t* types, con
     if (!m) return fail(NEP_ERR_ARG, "null model");
     if (n < 1 || n > kStaticMaxN)
         return fail(NEP_ERR_ARG, "nep_compute_static: n must be in [1, 4096] (static scratch limit)");
+    if (m->T > kStaticMaxT) return fail(NEP_ERR_ARG, "nep_compute_static: models of at most 4 types");
     if (!types || !pos || !box || !pbc) return fail(NEP_ERR_ARG, "null input array");
     CellGrid g;
     NEP_TRY(make_grid(m, box, pbc, g));

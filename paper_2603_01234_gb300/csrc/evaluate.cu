@@ -6,7 +6,9 @@
 //            with real orthonormal Y_lm (for real g_n, sum_m (-1)^m A_m A_-m of
 //            the complex harmonics equals sum_m A_m^2 of the real ones)
 //   network  U_i (Eq. 2) and dU_i/dq
-//   stores   U_i, dU_i/dq_n (radial), Phi_nlm = dU_i/dA_nlm = 2 dU_i/dq_nl A_nlm
+//   stores   U_i;  e_i^t[k] = sum_n dU_i/dq_n c^{t_i t}_{nk} for every partner type t
+//            (the radial gradient folded into the basis: dU_i/dr_ij|radial =
+//            sum_k e_i^{t_j}[k] f_k'(r_ij) u_ij);  Phi_nlm = dU_i/dA_nlm = 2 dU_i/dq_nl A_nlm
 //
 // k_force (one thread per sorted particle i, gather form, no atomics):
 //   for every neighbour j the pair gradients f_ij = dU_i/dr_ij and
@@ -27,6 +29,15 @@ namespace nep {
 
 __host__ __device__ constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
 constexpr int kNLM = 24;
+// resident blocks per SM the FP32 kernels are compiled for (caps registers per thread)
+#ifndef NEP_FORCE_MIN_BLOCKS
+#define NEP_FORCE_MIN_BLOCKS 3
+#endif
+#ifndef NEP_DESC_MIN_BLOCKS
+#define NEP_DESC_MIN_BLOCKS 3
+#endif
+constexpr int kForceMinBlocks = NEP_FORCE_MIN_BLOCKS;
+constexpr int kDescMinBlocks = NEP_DESC_MIN_BLOCKS;
 
 __device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
@@ -108,11 +119,11 @@ __device__ __forceinline__ void stage_params(const real* __restrict__ src, real*
 }
 
 template <typename real, int NR, int NA, int KR, int KA>
-__global__ void __launch_bounds__(kBlock) k_descriptor(EvalArgs<real> a)
+__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1) k_descriptor(EvalArgs<real> a)
 {
     constexpr int ND = NR + NA * 4;
-    constexpr int NRP = (NR + 3) & ~3;
-    extern __shared__ unsigned char smem_raw[];
+    constexpr int KRP = (KR + 3) & ~3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
     stage_params(a.params, P, a.off.total);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,7 +147,7 @@ __global__ void __launch_bounds__(kBlock) k_descriptor(EvalArgs<real> a)
         const real r = r2 * inv_r;
         const int tp = ti * T + rj.t;
         real f[KR];
-        basis<real, KR>(r, real(1) / P[a.off.rcR + tp], f);
+        basis<real, KR>(r, P[a.off.rcRi + tp], f);
         const real* c = P + a.off.cR + tp * NR * KR;
 #pragma unroll
         for (int nn = 0; nn < NR; ++nn) {
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kBlock) k_descriptor(EvalArgs<real> a)
         const real r = r2 * inv_r;
         const int tp = ti * T + rj.t;
         real f[KA];
-        basis<real, KA>(r, real(1) / P[a.off.rcA + tp], f);
+        basis<real, KA>(r, P[a.off.rcAi + tp], f);
         const real* c = P + a.off.cA + tp * NA * KA;
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
@@ -202,8 +213,20 @@ __global__ void __launch_bounds__(kBlock) k_descriptor(EvalArgs<real> a)
         for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
     }
     a.U[i] = U;
+    // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
+    real* ei = a.e + (size_t)i * T * KRP;
+    for (int t = 0; t < T; ++t) {
+        const real* c = P + a.off.cR + (ti * T + t) * NR * KR;
 #pragma unroll
-    for (int nn = 0; nn < NRP; ++nn) a.dq[(size_t)i * NRP + nn] = nn < NR ? dq[nn] : real(0);
+        for (int k = 0; k < KRP; ++k) {
+            real v = real(0);
+            if (k < KR) {
+#pragma unroll
+                for (int nn = 0; nn < NR; ++nn) v += dq[nn] * c[nn * KR + k];
+            }
+            ei[t * KRP + k] = v;
+        }
+    }
     real* ph = a.phi + (size_t)i * kNLM * NA;
 #pragma unroll
     for (int k = 0; k < kNLM; ++k)
@@ -253,12 +276,37 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], double* partial, 
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-template <typename real, int NR, int NA, int KR, int KA>
-__global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
+// 4 consecutive reals (16-byte aligned) into registers
+__device__ __forceinline__ void load4(const float* p, float* o)
 {
-    constexpr int NRP = (NR + 3) & ~3;
-    extern __shared__ unsigned char smem_raw[];
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* o)
+{
+    const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+template <typename real, int N>
+__device__ __forceinline__ void loadN(const real* p, real* o)
+{
+#pragma unroll
+    for (int k = 0; k + 3 < N; k += 4) load4(p + k, o + k);
+#pragma unroll
+    for (int k = N & ~3; k < N; ++k) o[k] = p[k];
+}
+
+template <typename real, int NR, int NA, int KR, int KA>
+__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 1) k_force(EvalArgs<real> a)
+{
+    constexpr int KRP = (KR + 3) & ~3;
+    // FP32: i's Phi lives in a shared-memory column [24][NA][kBlock] (conflict-free);
+    // FP64 reads it from global memory (L1).
+    constexpr bool kTile = sizeof(real) == 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
+    real* tile = reinterpret_cast<real*>(smem_raw + a.tile_offset);
     stage_params(a.params, P, a.off.n_cut_coef);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double tot[10];
@@ -272,11 +320,9 @@ __global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
         real W[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) W[k] = real(0);
-        real dqi[NR];
-#pragma unroll
-        for (int nn = 0; nn < NR; ++nn) dqi[nn] = a.dq[(size_t)i * NRP + nn];
 
-        // ---- radial pairs ----
+        // ---- radial pairs: f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u ----
+        const real* e_i = a.e + (size_t)i * T * KRP;
         const int cR = min(a.cntR[i], a.mnR);
         for (int s = 0; s < cR; ++s) {
             const uint32_t e = a.nlR[(size_t)s * a.n + i];
@@ -287,24 +333,17 @@ __global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real inv_r = rsqrt_r(r2);
             const real r = r2 * inv_r;
-            const int tij = ti * T + rj.t, tji = rj.t * T + ti;
             real f[KR], df[KR];
-            basis_d<real, KR>(r, real(1) / P[a.off.rcR + tij], f, df);
-            const real* cij = P + a.off.cR + tij * NR * KR;
-            const real* cji = P + a.off.cR + tji * NR * KR;
+            basis_d<real, KR>(r, P[a.off.rcRi + ti * T + rj.t], f, df);
+            real eij[KRP], eji[KRP];
+            loadN<real, KRP>(e_i + rj.t * KRP, eij);
+            loadN<real, KRP>(a.e + ((size_t)j * T + ti) * KRP, eji);
             real ai = real(0), bj = real(0);
 #pragma unroll
-            for (int nn = 0; nn < NR; ++nn) {
-                real gi = real(0), gj = real(0);
-#pragma unroll
-                for (int k = 0; k < KR; ++k) {
-                    gi += cij[nn * KR + k] * df[k];
-                    gj += cji[nn * KR + k] * df[k];
-                }
-                ai += dqi[nn] * gi;
-                bj += a.dq[(size_t)j * NRP + nn] * gj;
+            for (int k = 0; k < KR; ++k) {
+                ai += eij[k] * df[k];
+                bj += eji[k] * df[k];
             }
-            // f_ij = ai u,  f_ji = -bj u
             const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
             const real fs = ai + bj;
             F[0] += fs * ux;
@@ -312,13 +351,19 @@ __global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
             F[2] += fs * uz;
             const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
 #pragma unroll
-            for (int p = 0; p < 3; ++p)
+            for (int p = 0; p < 3; ++p) {
+                const real bd = bj * d[p];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) W[3 * p + q] -= bj * d[p] * u[q];
+                for (int q = 0; q < 3; ++q) W[3 * p + q] -= bd * u[q];
+            }
         }
 
         // ---- angular pairs ----
         const real* phi_i = a.phi + (size_t)i * kNLM * NA;
+        if (kTile) {
+#pragma unroll
+            for (int k = 0; k < kNLM * NA; ++k) tile[k * kBlock + threadIdx.x] = phi_i[k];
+        }
         const int cA = min(a.cntA[i], a.mnA);
         for (int s = 0; s < cA; ++s) {
             const uint32_t e = a.nlA[(size_t)s * a.n + i];
@@ -331,53 +376,83 @@ __global__ void __launch_bounds__(kBlock) k_force(EvalArgs<real> a)
             const real r = r2 * inv_r;
             const int tij = ti * T + rj.t, tji = rj.t * T + ti;
             real f[KA], df[KA];
-            basis_d<real, KA>(r, real(1) / P[a.off.rcA + tij], f, df);
-            const real* cij = P + a.off.cA + tij * NA * KA;
-            const real* cji = P + a.off.cA + tji * NA * KA;
+            basis_d<real, KA>(r, P[a.off.rcAi + tij], f, df);
             real gi[NA], dgi[NA], gj[NA], dgj[NA];
+            {
+                const real* c = P + a.off.cA + tij * NA * KA;
 #pragma unroll
-            for (int nn = 0; nn < NA; ++nn) {
-                real s0 = real(0), s1 = real(0), s2 = real(0), s3 = real(0);
+                for (int nn = 0; nn < NA; ++nn) {
+                    real s0 = real(0), s1 = real(0);
 #pragma unroll
-                for (int k = 0; k < KA; ++k) {
-                    s0 += cij[nn * KA + k] * f[k];
-                    s1 += cij[nn * KA + k] * df[k];
-                    s2 += cji[nn * KA + k] * f[k];
-                    s3 += cji[nn * KA + k] * df[k];
+                    for (int k = 0; k < KA; ++k) {
+                        s0 += c[nn * KA + k] * f[k];
+                        s1 += c[nn * KA + k] * df[k];
+                    }
+                    gi[nn] = s0;
+                    dgi[nn] = s1;
                 }
-                gi[nn] = s0;
-                dgi[nn] = s1;
-                gj[nn] = s2;
-                dgj[nn] = s3;
+            }
+            if (tji == tij) {
+#pragma unroll
+                for (int nn = 0; nn < NA; ++nn) {
+                    gj[nn] = gi[nn];
+                    dgj[nn] = dgi[nn];
+                }
+            } else {
+                const real* c = P + a.off.cA + tji * NA * KA;
+#pragma unroll
+                for (int nn = 0; nn < NA; ++nn) {
+                    real s0 = real(0), s1 = real(0);
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) {
+                        s0 += c[nn * KA + k] * f[k];
+                        s1 += c[nn * KA + k] * df[k];
+                    }
+                    gj[nn] = s0;
+                    dgj[nn] = s1;
+                }
             }
             const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-            real Y[kNLM], Gs[kNLM], Gj[kNLM];
-            sh_eval(ux, uy, uz, Y);
+            const ShMono<real> mono = sh_mono(ux, uy, uz);
             const real* phi_j = a.phi + (size_t)j * kNLM * NA;
             real si = real(0), sj = real(0);
+            real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
 #pragma unroll
             for (int k = 0; k < kNLM; ++k) {
                 const real lr = real(l_of(k)) * inv_r;
-                const real sg = (l_of(k) & 1) ? real(-1) : real(1);
+                real pi_[NA], pj[NA];
+                if (kTile) {
+#pragma unroll
+                    for (int nn = 0; nn < NA; ++nn) pi_[nn] = tile[(k * NA + nn) * kBlock + threadIdx.x];
+                } else {
+                    loadN<real, NA>(phi_i + k * NA, pi_);
+                }
+                loadN<real, NA>(phi_j + k * NA, pj);
                 real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
 #pragma unroll
                 for (int nn = 0; nn < NA; ++nn) {
-                    const real pi_ = phi_i[k * NA + nn], pj = phi_j[k * NA + nn];
-                    Gi_ += pi_ * gi[nn];
-                    dGi += pi_ * dgi[nn];
-                    Gj_ += pj * gj[nn];
-                    dGj += pj * dgj[nn];
+                    Gi_ += pi_[nn] * gi[nn];
+                    dGi += pi_[nn] * dgi[nn];
+                    Gj_ += pj[nn] * gj[nn];
+                    dGj += pj[nn] * dgj[nn];
                 }
-                Gj_ *= sg;
-                dGj *= sg;
-                si += (dGi - lr * Gi_) * Y[k];
-                sj += (dGj - lr * Gj_) * Y[k];
-                Gs[k] = Gi_ + Gj_;
-                Gj[k] = Gj_;
+                if (l_of(k) & 1) {  // reverse pair: Y(-u) = (-1)^l Y(u)
+                    Gj_ = -Gj_;
+                    dGj = -dGj;
+                }
+                real y, gx, gy, gz;
+                sh_val_grad(k, mono, y, gx, gy, gz);
+                si += (dGi - lr * Gi_) * y;
+                sj += (dGj - lr * Gj_) * y;
+                const real Gs = Gi_ + Gj_;
+                ga[0] += Gs * gx;
+                ga[1] += Gs * gy;
+                ga[2] += Gs * gz;
+                gb[0] += Gj_ * gx;
+                gb[1] += Gj_ * gy;
+                gb[2] += Gj_ * gz;
             }
-            real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
-            sh_grad2(ux, uy, uz, Gs, Gj, ga, gb);
-            // F_i += f_ij - f_ji ;  -f_ji = sj u + gb / r
+            // F_i += f_ij - f_ji;  -f_ji = sj u + gb / r;  W_i += r_ij (x) f_ji
             const real u[3] = {ux, uy, uz}, d[3] = {dx, dy, dz};
             real vj[3];
 #pragma unroll

@@ -42,7 +42,7 @@ struct CellGrid {
 
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
-    int rcR2, rcA2, rcR, rcA;   // [T][T] each: squared and plain cutoffs
+    int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
     int cR, cA;                 // [T][T][nR][KR], [T][T][nA][KA]
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
     int n_cut_coef;             // elements of the cutoff + coefficient prefix
@@ -77,8 +77,9 @@ struct EvalArgs {
     const real* params;
     ParamLayout off;
     real* U;                    // [n] sorted site energies
-    real* dq;                   // [n][NRP] dU/dq of the radial descriptors
+    real* e;                    // [n][T][KRP] radial gradient folded into the basis
     real* phi;                  // [n][24][NA] dU/dA_nlm
+    int tile_offset;            // byte offset of the force kernel's Phi tile in dynamic smem
     const int* perm;            // sorted slot -> caller index
     double* force;              // [3][n] caller order (required)
     double* virial;             // [9][n] caller order or null
