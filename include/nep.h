@@ -130,6 +130,32 @@ int nep_compute(nep_model* m, int n, const int32_t* types, const double* pos, co
                 double* site_energy, double* force, double* virial);
 
 /*
+ * Many configurations in one pass of the pipeline (the batched form): one cell
+ * build, one neighbour pass, one descriptor pass and one force pass cover every
+ * request, each request with its own box, cell grid and model.
+ *   models[n_models]   handles created with the same device, precision and
+ *                      descriptor / basis sizes (their types, cutoffs, widths and
+ *                      parameters may differ); the batch uses models[0]'s workspace
+ *   n_req              number of requests; request r has req_n[r] particles and
+ *                      uses models[req_model[r]]
+ *   req_box[n_req][3], req_pbc[n_req][3]      host arrays
+ *   types, pos         the requests' particles concatenated: request r's types at
+ *                      types + o_r and its positions as an SoA block [3][n_r] at
+ *                      pos + 3 o_r, where o_r = sum_{q<r} n_q
+ *   mem, stream        as in nep_compute (all arrays below in the same memory)
+ *   energy[n_req], virial_total[n_req][9]     per-request totals (FP64 sums)
+ *   site_energy        [sum n_r] concatenated like types, or NULL
+ *   force              blocks [3][n_r] at force + 3 o_r (NULL allowed)
+ *   virial             blocks [9][n_r] at virial + 9 o_r, or NULL
+ * Results equal those of one nep_compute per request.  Synchronous like
+ * nep_compute; at most 2^23 particles in total.
+ */
+int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const int32_t* req_n,
+                      const int32_t* req_model, const double* req_box, const int32_t* req_pbc,
+                      const int32_t* types, const double* pos, int mem, void* stream, double* energy,
+                      double* virial_total, double* site_energy, double* force, double* virial);
+
+/*
  * n_steps velocity-Verlet NVE steps (the MD loop of Sec. III.D):
  *   v += dt/2 F/m;  r += dt v;  wrap periodic axes;  F = F(r);  v += dt/2 F/m.
  *   masses[T]         host, amu per type
@@ -198,11 +224,12 @@ int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
  * start-up (an MD engine, a serving process) forbid hidden allocations.
  *
  * The scratch is one fixed array in device global memory that is part of the
- * library image: 11,505,408 bytes (about 11 MiB), held on every GPU that loads the
+ * library image: 12,834,560 bytes (about 12 MiB), held on every GPU that loads the
  * library until the process exits.  Limits of one call: n <= 4096 particles, a
- * cell grid of at most 32768 cells, at most 256 radial and 128 angular neighbours
- * per particle.  Larger inputs are rejected with NEP_ERR_ARG (the message names
- * the limit); more neighbours give NEP_ERR_NEIGHBOR_OVERFLOW.
+ * model of at most 4 types, a cell grid of at most 32768 cells, at most 256
+ * radial and 128 angular neighbours per particle.  Larger inputs are rejected with
+ * NEP_ERR_ARG (the message names the limit); more neighbours give
+ * NEP_ERR_NEIGHBOR_OVERFLOW.
  *
  *   m             a handle from nep_create (its parameters are read, nothing grows)
  *   types, pos    device arrays as in nep_compute with mem = NEP_DEVICE

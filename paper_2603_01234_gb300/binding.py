@@ -33,7 +33,7 @@ NEP_DEVICE = 1
 EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "nep_supported_shape",
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
             "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
-            "nep_compute_static"]
+            "nep_compute_static", "nep_compute_batch"]
 
 _lib = None
 
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = False):
     lib.nep_get_timing.restype = i
     lib.nep_compute_static.argtypes = [p, i, p, p, p, p, p, p, p, p, p, p]
     lib.nep_compute_static.restype = i
+    lib.nep_compute_batch.argtypes = [p, i, i, p, p, p, p, p, p, i, p, p, p, p, p, p]
+    lib.nep_compute_batch.restype = i
     _lib = lib
     return lib
 
@@ -178,6 +180,42 @@ def nep_compute_static(h, types, pos, box, pbc, energy_total=None, virial_total=
     _check(load().nep_compute_static(h, n, _ptr(types), _ptr(pos), _ptr(box), _ptr(pbc), _stream_of(pos, stream),
                                      _ptr(energy_total), _ptr(virial_total), _ptr(site_energy), _ptr(force),
                                      _ptr(virial)), "nep_compute_static")
+
+
+def nep_compute_batch(handles, req_n, req_model, req_box, req_pbc, types, pos, energy=None, virial_total=None,
+                      site_energy=None, force=None, virial=None, stream=None):
+    """Batched evaluation.  handles: list of model handles; arrays concatenated per
+    request (numpy for host memory, torch CUDA tensors for device memory)."""
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    req_n = _host(req_n, np.int32)
+    req_model = _host(req_model, np.int32)
+    req_box = _host(req_box, np.float64)
+    req_pbc = _host(req_pbc, np.int32)
+    _check(load().nep_compute_batch(C.cast(arr, C.c_void_p), len(handles), int(req_n.size), _ptr(req_n),
+                                    _ptr(req_model), _ptr(req_box), _ptr(req_pbc), _ptr(types), _ptr(pos), mem,
+                                    _stream_of(pos, stream), _ptr(energy), _ptr(virial_total), _ptr(site_energy),
+                                    _ptr(force), _ptr(virial)), "nep_compute_batch")
+
+
+def pack_requests(systems):
+    """Concatenate systems into the batch layout: (req_n, req_box, req_pbc, types, pos)
+    with pos as per-request [3][n_r] blocks."""
+    req_n = np.array([s.n for s in systems], np.int32)
+    req_box = np.array([s.box for s in systems], np.float64)
+    req_pbc = np.array([s.pbc for s in systems], np.int32)
+    types = np.concatenate([s.types for s in systems]).astype(np.int32)
+    pos = np.concatenate([np.ascontiguousarray(s.pos, dtype=np.float64).reshape(-1) for s in systems])
+    return req_n, req_box, req_pbc, types, pos
+
+
+def unpack_blocks(arr, req_n, width):
+    """Split a concatenated per-request [width][n_r] block array into a list."""
+    out, o = [], 0
+    for n in req_n:
+        out.append(arr[o:o + width * n].reshape(width, n))
+        o += width * n
+    return out
 
 
 def nep_md_step(h, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs, sample_every=0,

@@ -145,6 +145,21 @@ struct GraphCache {
     }
 };
 
+
+// Host copy of one batch layout and its device tables (requests, work items, models).
+struct Plan {
+    std::vector<ReqInfo> reqs;
+    std::vector<WorkItem> items;
+    std::vector<unsigned char> models;  // ModelDesc<real> entries, raw bytes
+    int n = 0, ncell = 0, n_models = 0;
+    int Tmax = 1;
+    size_t smem_desc = 0, smem_force = 0, smem_nbr = 0;
+    size_t tile_offset = 0;             // force kernel's Phi tile: after the largest staged prefix
+    std::vector<unsigned char> key;     // identity of the uploaded tables
+    Buf dev;                            // [reqs | items | models] on the device
+    size_t off_items = 0, off_models = 0;
+};
+
 }  // namespace
 
 struct nep_model {
@@ -160,21 +175,26 @@ struct nep_model {
     int mnR = 0, mnA = 0;  // neighbour capacities
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_flags = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_flags = nullptr, ev_plan = nullptr;
     int* h_async = nullptr;      // pinned copy of the status words after an asynchronous MD call
     bool async_pending = false;
     cudaStream_t async_stream = nullptr;
+    bool plan_pending = false;   // a table upload from the pinned staging is in flight
     // MD sizing state: the last configuration the capacities were checked for
     int md_n = -1;
     CellGrid md_grid{};
     // workspace
-    Buf cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
+    Buf cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
-    Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp;
-    int* h_flags = nullptr;  // pinned: maxcnt[2], err
-    double* h_totals = nullptr;  // pinned [10]
-    size_t n_lists = 0;  // n the lists were sized for
+    Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
+    int* h_flags = nullptr;        // pinned: maxcnt[2], err
+    double* h_totals = nullptr;    // pinned [10 * requests]
+    size_t h_totals_cap = 0;
+    unsigned char* h_stage = nullptr;  // pinned staging of the plan tables
+    size_t h_stage_cap = 0;
+    size_t n_lists = 0;  // particles the lists were sized for
+    Plan plan;
     GraphCache graph;
     StageTimer timer;
 };
@@ -196,52 +216,170 @@ struct Guard {  // make the device current for the duration of a call
     }
 };
 
-int make_grid(const nep_model* m, const double box[3], const int32_t pbc[3], CellGrid& g)
+int make_grid(const nep_model* m, double rc_max, const double box[3], const int32_t pbc[3], CellGrid& g)
 {
     long long ncell = 1;
     for (int a = 0; a < 3; ++a) {
         if (!(box[a] > 0.0) || !isfinite(box[a])) return fail(NEP_ERR_ARG, "box lengths must be positive and finite");
         g.pbc[a] = pbc[a] ? 1 : 0;
         g.box[a] = box[a];
-        int nc = (int)floor(box[a] / m->rc_max);
+        int nc = (int)floor(box[a] / rc_max);
         if (nc < 1) nc = 1;
         if (nc > 1024) nc = 1024;
         g.nc[a] = nc;
         g.len[a] = box[a] / nc;
         if (g.pbc[a]) {
-            int S = (int)ceil(m->rc_max / g.len[a] - 1e-12);
+            int S = (int)ceil(rc_max / g.len[a] - 1e-12);
             if (S < 1) S = 1;
             if (S > kMaxS) return fail(NEP_ERR_BOX_TOO_SMALL, "cutoff exceeds twice the box length on a periodic axis");
             g.S[a] = S;
         } else {
             g.S[a] = 1;
-            if (g.len[a] < m->rc_max && nc > 1) return fail(NEP_ERR_ARG, "internal: open-axis cell below cutoff");
         }
         ncell *= nc;
     }
     if (ncell > (long long)kScanItems * kScanItems) return fail(NEP_ERR_ARG, "cell grid too large");
     g.ncell = (int)ncell;
+    (void)m;
     return NEP_OK;
 }
 
-int ensure_particles(nep_model* m, int n)
+int make_grid(const nep_model* m, const double box[3], const int32_t pbc[3], CellGrid& g)
+{
+    return make_grid(m, m->rc_max, box, pbc, g);
+}
+
+// ---- plans -------------------------------------------------------------------
+template <typename real>
+ModelDesc<real> model_desc(const nep_model* m)
+{
+    ModelDesc<real> d;
+    d.params = m->params.as<real>();
+    d.off = m->off;
+    d.T = m->T;
+    d.H = m->H;
+    return d;
+}
+
+// Work items: the request's particles cut into blocks of kBlock.
+void add_request(Plan& p, const CellGrid& g, int n, int model)
+{
+    ReqInfo r;
+    r.g = g;
+    r.cell_base = p.ncell;
+    r.begin = p.n;
+    r.n = n;
+    r.model = model;
+    r.item_begin = (int)p.items.size();
+    for (int b = 0; b < n; b += kBlock) p.items.push_back(WorkItem{(int)p.reqs.size(), p.n + b, p.n + std::min(n, b + kBlock)});
+    r.item_end = (int)p.items.size();
+    p.reqs.push_back(r);
+    p.n += n;
+    p.ncell += g.ncell;
+}
+
+template <typename real>
+void set_models(Plan& p, nep_model* const* models, int n_models)
+{
+    p.n_models = n_models;
+    p.models.resize(sizeof(ModelDesc<real>) * n_models);
+    p.Tmax = 1;
+    p.smem_desc = p.smem_force = p.smem_nbr = p.tile_offset = 0;
+    size_t tile_bytes = 0;
+    for (int k = 0; k < n_models; ++k) {
+        ModelDesc<real> d = model_desc<real>(models[k]);
+        memcpy(p.models.data() + k * sizeof d, &d, sizeof d);
+        p.Tmax = std::max(p.Tmax, models[k]->T);
+        p.smem_desc = std::max(p.smem_desc, models[k]->smem_desc);
+        p.tile_offset = std::max(p.tile_offset, models[k]->tile_offset);
+        tile_bytes = std::max(tile_bytes, models[k]->smem_force - models[k]->tile_offset);
+        p.smem_nbr = std::max(p.smem_nbr, 2 * sizeof(real) * models[k]->T * models[k]->T);
+    }
+    p.smem_force = p.tile_offset + tile_bytes;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Upload the plan's tables (through pinned staging) unless they are unchanged.
+int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
+{
+    std::vector<unsigned char> key;
+    auto put = [&](const void* q, size_t s) {
+        const unsigned char* b = (const unsigned char*)q;
+        key.insert(key.end(), b, b + s);
+    };
+    put(p.reqs.data(), sizeof(ReqInfo) * p.reqs.size());
+    put(p.items.data(), sizeof(WorkItem) * p.items.size());
+    put(p.models.data(), p.models.size());
+    if (!force_upload && key == p.key && p.dev.p) return NEP_OK;
+    p.off_items = align16(sizeof(ReqInfo) * p.reqs.size());
+    p.off_models = p.off_items + align16(sizeof(WorkItem) * p.items.size());
+    const size_t bytes = p.off_models + p.models.size();
+    NEP_TRY(p.dev.ensure(bytes));
+    if (m->plan_pending) NEP_CUDA(cudaEventSynchronize(m->ev_plan));  // staging free again
+    m->plan_pending = false;
+    if (bytes > m->h_stage_cap) {
+        if (m->h_stage) cudaFreeHost(m->h_stage);
+        m->h_stage = nullptr;
+        m->h_stage_cap = 0;
+        NEP_CUDA(cudaMallocHost((void**)&m->h_stage, bytes + bytes / 2));
+        m->h_stage_cap = bytes + bytes / 2;
+    }
+    memcpy(m->h_stage, p.reqs.data(), sizeof(ReqInfo) * p.reqs.size());
+    memcpy(m->h_stage + p.off_items, p.items.data(), sizeof(WorkItem) * p.items.size());
+    memcpy(m->h_stage + p.off_models, p.models.data(), p.models.size());
+    NEP_CUDA(cudaMemcpyAsync(p.dev.p, m->h_stage, bytes, cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaEventRecord(m->ev_plan, m->cur));
+    m->plan_pending = true;
+    p.key = key;
+    return NEP_OK;
+}
+
+const ReqInfo* d_reqs(const Plan& p) { return p.dev.as<ReqInfo>(); }
+const WorkItem* d_items(const Plan& p) { return (const WorkItem*)((const unsigned char*)p.dev.p + p.off_items); }
+template <typename real>
+const ModelDesc<real>* d_models(const Plan& p)
+{
+    return (const ModelDesc<real>*)((const unsigned char*)p.dev.p + p.off_models);
+}
+
+template <typename real>
+int single_plan(nep_model* m, int n, const CellGrid& g)
+{
+    Plan& p = m->plan;
+    p.reqs.clear();
+    p.items.clear();
+    p.n = p.ncell = 0;
+    add_request(p, g, n, 0);
+    nep_model* one[1] = {m};
+    set_models<real>(p, one, 1);
+    return upload_plan(m, p);
+}
+
+// ---- workspace ---------------------------------------------------------------
+int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
 {
     const size_t rs = m->real_size;
     const size_t rec_sz = 4 * rs;
     NEP_TRY(m->cell_of.ensure(sizeof(int) * n));
     NEP_TRY(m->rec_user.ensure(rec_sz * n));
+    NEP_TRY(m->perm_tmp.ensure(sizeof(int) * n));
     NEP_TRY(m->perm.ensure(sizeof(int) * n));
     NEP_TRY(m->rec_s.ensure(rec_sz * n));
     NEP_TRY(m->cell_s.ensure(sizeof(int) * n));
     NEP_TRY(m->cntR.ensure(sizeof(int) * n));
     NEP_TRY(m->cntA.ensure(sizeof(int) * n));
     NEP_TRY(m->U.ensure(rs * n));
-    NEP_TRY(m->e.ensure(rs * m->T * m->KRP * (size_t)n));
+    NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
     NEP_TRY(m->phi.ensure(rs * 24 * m->nA * (size_t)n));
-    const size_t nb = (n + kBlock - 1) / kBlock;
-    NEP_TRY(m->partial.ensure(sizeof(double) * 10 * nb));
-    NEP_TRY(m->partial2.ensure(sizeof(double) * nb));
+    NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
+    NEP_TRY(m->partial2.ensure(sizeof(double) * ((n + kBlock - 1) / kBlock)));
     NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
+    const size_t old_req = m->counters.cap / sizeof(unsigned int);
+    NEP_TRY(m->counters.ensure(sizeof(unsigned int) * (n_req + 2)));
+    if (m->counters.cap / sizeof(unsigned int) != old_req)  // fresh buffer: counters start at zero
+        NEP_CUDA(cudaMemsetAsync(m->counters.p, 0, m->counters.cap, m->cur));
+    NEP_TRY(m->totals.ensure(sizeof(double) * 10 * (size_t)n_req));
     return NEP_OK;
 }
 
@@ -263,6 +401,14 @@ int ensure_cells(nep_model* m, int ncell)
     return NEP_OK;
 }
 
+int ensure_plan_workspace(nep_model* m, const Plan& p)
+{
+    NEP_TRY(ensure_particles(m, p.n, (int)p.items.size(), (int)p.reqs.size(), p.Tmax));
+    NEP_TRY(ensure_cells(m, p.ncell));
+    if ((size_t)p.n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, p.n));
+    return NEP_OK;
+}
+
 // Estimated neighbour counts from the density of the box (first sizing only).
 void initial_capacity(nep_model* m, int n, const double box[3])
 {
@@ -281,78 +427,78 @@ void initial_capacity(nep_model* m, int n, const double box[3])
     if (m->mnA <= 0) m->mnA = est(rA);
 }
 
+// ---- pipeline stages ----------------------------------------------------------
 template <typename real>
-int run_cells(nep_model* m, int n, const int* types_d, const double* pos_d, const CellGrid& g)
+int run_cells(nep_model* m, const Plan& p, const int* types_d, const double* pos_d)
 {
-    cudaError_t e = launch_cell_build<real>(n, pos_d, types_d, m->T, g, m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(),
-                                            m->cell_count.as<int>(), m->cell_local.as<int>(), m->block_off.as<int>(),
-                                            m->cell_fill.as<int>(), m->perm.as<int>(), m->cell_start.as<int>(),
-                                            m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(), m->flags.as<int>() + 2,
-                                            m->cur);
+    cudaError_t e = launch_cell_build<real>(
+        p.n, (int)p.items.size(), p.ncell, d_items(p), d_reqs(p), d_models<real>(p), pos_d, types_d,
+        m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(), m->cell_count.as<int>(), m->cell_local.as<int>(),
+        m->block_off.as<int>(), m->cell_fill.as<int>(), m->perm_tmp.as<int>(), m->perm.as<int>(),
+        m->cell_start.as<int>(), m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(), m->flags.as<int>() + 2, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
 
 template <typename real>
-int run_neighbors(nep_model* m, int n, const CellGrid& g)
+int run_neighbors(nep_model* m, const Plan& p)
 {
     NeighborArgs<real> a;
-    a.n = n;
-    a.T = m->T;
+    a.n = p.n;
     a.mnR = m->mnR;
     a.mnA = m->mnA;
-    a.g = g;
+    a.items = d_items(p);
+    a.reqs = d_reqs(p);
+    a.models = d_models<real>(p);
     a.cell_start = m->cell_start.as<int>();
     a.cell_s = m->cell_s.as<int>();
     a.rec = m->rec_s.as<PosRec<real>>();
-    a.params = m->params.as<real>();
-    a.off = m->off;
     a.nlR = m->nlR.as<uint32_t>();
     a.nlA = m->nlA.as<uint32_t>();
     a.cntR = m->cntR.as<int>();
     a.cntA = m->cntA.as<int>();
     a.maxcnt = m->flags.as<int>();
-    cudaError_t e = launch_neighbors<real>(a, m->cur);
+    cudaError_t e = launch_neighbors<real>(a, (int)p.items.size(), p.smem_nbr, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
 
 template <typename real>
-int run_evaluate(nep_model* m, int n, const CellGrid& g, double* force, double* virial, double* site,
+int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, double* site, double* totals,
                  cudaEvent_t mid = nullptr)
 {
     EvalArgs<real> a;
-    a.n = n;
-    a.T = m->T;
-    a.H = m->H;
+    a.n = p.n;
     a.mnR = m->mnR;
     a.mnA = m->mnA;
-    for (int k = 0; k < 3; ++k) a.len[k] = (real)g.len[k];
+    a.items = d_items(p);
+    a.reqs = d_reqs(p);
+    a.models = d_models<real>(p);
     a.rec = m->rec_s.as<PosRec<real>>();
     a.nlR = m->nlR.as<uint32_t>();
     a.nlA = m->nlA.as<uint32_t>();
     a.cntR = m->cntR.as<int>();
     a.cntA = m->cntA.as<int>();
-    a.params = m->params.as<real>();
-    a.off = m->off;
     a.U = m->U.as<real>();
     a.e = m->e.as<real>();
-    a.tile_offset = (int)m->tile_offset;
+    a.e_stride = p.Tmax * m->KRP;
     a.phi = m->phi.as<real>();
+    a.tile_offset = (int)p.tile_offset;
     a.perm = m->perm.as<int>();
     a.force = force;
     a.virial = virial;
     a.site = site;
     a.partial = m->partial.as<double>();
-    a.counter = m->counters.as<unsigned int>();
-    a.totals = m->totals.as<double>();
-    cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, m->smem_desc, m->smem_force, m->cur, mid);
+    a.counter = m->counters.as<unsigned int>() + 2;
+    a.totals = totals;
+    cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, (int)p.items.size(), p.smem_desc,
+                                          p.smem_force, m->cur, mid);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
 
 template <typename real>
-int check_lists(nep_model* m, int n, const CellGrid& g, bool* regrown)
+int check_lists(nep_model* m, const Plan& p)
 {
     // read maxcnt and the error word; grow and rebuild on overflow
     for (int attempt = 0; attempt < 3; ++attempt) {
@@ -362,29 +508,26 @@ int check_lists(nep_model* m, int n, const CellGrid& g, bool* regrown)
         if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
         int needR = m->h_flags[0], needA = m->h_flags[1];
         if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
-        if (regrown) *regrown = true;
         if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
         if (needA > m->mnA) m->mnA = ((int)(needA * 1.25) + 8 + 7) & ~7;
-        NEP_TRY(ensure_lists(m, n));
+        NEP_TRY(ensure_lists(m, p.n));
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 2 * sizeof(int), m->cur));
-        NEP_TRY(run_neighbors<real>(m, n, g));
+        NEP_TRY(run_neighbors<real>(m, p));
     }
     return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity did not converge");
 }
 
-// Full evaluation on device arrays (caller order).  force must be non-null.
+// Full evaluation of the uploaded plan on device arrays.  force must be non-null.
 template <typename real>
-int evaluate_device(nep_model* m, int n, const int* types_d, const double* pos_d, const CellGrid& g, double* force,
-                    double* virial, double* site)
+int evaluate_plan(nep_model* m, const Plan& p, const int* types_d, const double* pos_d, double* force,
+                  double* virial, double* site, double* totals)
 {
-    NEP_TRY(ensure_particles(m, n));
-    NEP_TRY(ensure_cells(m, g.ncell));
-    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
+    NEP_TRY(ensure_plan_workspace(m, p));
     NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
-    NEP_TRY(run_cells<real>(m, n, types_d, pos_d, g));
-    NEP_TRY(run_neighbors<real>(m, n, g));
-    NEP_TRY(check_lists<real>(m, n, g, nullptr));
-    NEP_TRY(run_evaluate<real>(m, n, g, force, virial, site));
+    NEP_TRY(run_cells<real>(m, p, types_d, pos_d));
+    NEP_TRY(run_neighbors<real>(m, p));
+    NEP_TRY(check_lists<real>(m, p));
+    NEP_TRY(run_evaluate<real>(m, p, force, virial, site, totals));
     return NEP_OK;
 }
 
@@ -398,7 +541,6 @@ int validate_common(nep_model* m, int n, const void* types, const void* pos, con
     return NEP_OK;
 }
 
-// Order the internal stream after the caller's stream.
 // Work runs on the caller's stream; a NULL stream (the legacy default stream, which
 // cannot be captured into a graph) is replaced by the handle's internal stream,
 // ordered after the legacy stream on entry and before it on exit.
@@ -424,6 +566,17 @@ int leave(nep_model* m, void* stream, bool sync = true)
     return NEP_OK;
 }
 
+int ensure_host_totals(nep_model* m, size_t count)
+{
+    if (count <= m->h_totals_cap) return NEP_OK;
+    if (m->h_totals) cudaFreeHost(m->h_totals);
+    m->h_totals = nullptr;
+    m->h_totals_cap = 0;
+    NEP_CUDA(cudaMallocHost((void**)&m->h_totals, sizeof(double) * count));
+    m->h_totals_cap = count;
+    return NEP_OK;
+}
+
 template <typename real>
 int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
                  const int32_t pbc[3], int mem, void* stream, double* energy_total, double* virial_total,
@@ -433,6 +586,8 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
     NEP_TRY(make_grid(m, box, pbc, g));
     NEP_TRY(enter(m, stream));
     initial_capacity(m, n, box);
+    NEP_TRY(single_plan<real>(m, n, g));
+    NEP_TRY(ensure_plan_workspace(m, m->plan));
     const int* types_d = types;
     const double* pos_d = pos;
     double *force_d = force, *virial_d = virial, *site_d = site_energy;
@@ -456,26 +611,26 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
             site_d = m->site_d.as<double>();
         }
     } else if (!force_d) {
-        NEP_TRY(ensure_particles(m, n));
         force_d = m->force_tmp.as<double>();
     }
-    NEP_TRY(evaluate_device<real>(m, n, types_d, pos_d, g, force_d, virial_d, site_d));
+    double* totals = m->totals.as<double>();
+    NEP_TRY(evaluate_plan<real>(m, m->plan, types_d, pos_d, force_d, virial_d, site_d, totals));
     if (mem == NEP_HOST) {
+        NEP_TRY(ensure_host_totals(m, 10));
         if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
         if (virial) NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
         if (site_energy)
             NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
-        NEP_CUDA(cudaMemcpyAsync(m->h_totals, m->totals.p, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
         NEP_TRY(leave(m, stream));
         if (energy_total) *energy_total = m->h_totals[0];
         if (virial_total)
             for (int k = 0; k < 9; ++k) virial_total[k] = m->h_totals[1 + k];
     } else {
         if (energy_total)
-            NEP_CUDA(cudaMemcpyAsync(energy_total, m->totals.p, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
+            NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
         if (virial_total)
-            NEP_CUDA(cudaMemcpyAsync(virial_total, m->totals.as<double>() + 1, sizeof(double) * 9,
-                                     cudaMemcpyDeviceToDevice, m->cur));
+            NEP_CUDA(cudaMemcpyAsync(virial_total, totals + 1, sizeof(double) * 9, cudaMemcpyDeviceToDevice, m->cur));
         NEP_TRY(leave(m, stream));
     }
     return NEP_OK;
@@ -487,6 +642,7 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
                      const CellGrid& g, double* pos, double* vel, double* force, double dt, bool sample,
                      int step_stride)
 {
+    const Plan& p = m->plan;
     cudaEvent_t* ev = nullptr;
     if (m->timer.on) {
         const int r = m->timer.head;
@@ -499,11 +655,11 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
     cudaError_t e = launch_kick_drift(n, types_d, inv_m_acc, m->T, 0.5 * dt, dt, g, pos, vel, force, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick/drift: ") + cudaGetErrorString(e));
     if (ev) NEP_CUDA(cudaEventRecord(ev[1], m->cur));
-    NEP_TRY(run_cells<real>(m, n, types_d, pos, g));
+    NEP_TRY(run_cells<real>(m, p, types_d, pos));
     if (ev) NEP_CUDA(cudaEventRecord(ev[2], m->cur));
-    NEP_TRY(run_neighbors<real>(m, n, g));
+    NEP_TRY(run_neighbors<real>(m, p));
     if (ev) NEP_CUDA(cudaEventRecord(ev[3], m->cur));
-    NEP_TRY(run_evaluate<real>(m, n, g, force, nullptr, nullptr, ev ? ev[4] : nullptr));
+    NEP_TRY(run_evaluate<real>(m, p, force, nullptr, nullptr, m->totals.as<double>(), ev ? ev[4] : nullptr));
     if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
     e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
@@ -569,6 +725,8 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     NEP_TRY(enter(m, stream));
     const bool async = (mem == NEP_DEVICE && stream != nullptr);
     initial_capacity(m, n, box);
+    NEP_TRY(single_plan<real>(m, n, g));
+    const Plan& p = m->plan;
     const int* types_d = types;
     double *pos_d = pos, *vel_d = vel, *force_d = force;
     if (mem == NEP_HOST) {
@@ -586,32 +744,30 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         vel_d = m->vel_d.as<double>();
         force_d = m->force_d.as<double>();
     }
-    NEP_TRY(ensure_particles(m, n));
-    NEP_TRY(ensure_cells(m, g.ncell));
-    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
+    NEP_TRY(ensure_plan_workspace(m, p));
 
     // Size the neighbour lists (one synchronous probe) only for a new
     // configuration shape; continuation calls rely on the deferred status.
     const bool new_shape = (n != m->md_n) || memcmp(&g, &m->md_grid, sizeof g) != 0;
     if (new_shape || !forces_valid) {
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
-        NEP_TRY(run_cells<real>(m, n, types_d, pos_d, g));
-        NEP_TRY(run_neighbors<real>(m, n, g));
+        NEP_TRY(run_cells<real>(m, p, types_d, pos_d));
+        NEP_TRY(run_neighbors<real>(m, p));
         if (new_shape) {
-            NEP_TRY(check_lists<real>(m, n, g, nullptr));
+            NEP_TRY(check_lists<real>(m, p));
             const int wantR = ((int)(m->h_flags[0] * 1.3) + 8 + 7) & ~7;
             const int wantA = ((int)(m->h_flags[1] * 1.3) + 8 + 7) & ~7;
             if (wantR > m->mnR || wantA > m->mnA) {
                 m->mnR = std::max(m->mnR, wantR);
                 m->mnA = std::max(m->mnA, wantA);
                 NEP_TRY(ensure_lists(m, n));
-                NEP_TRY(run_neighbors<real>(m, n, g));
+                NEP_TRY(run_neighbors<real>(m, p));
             }
             m->md_n = n;
             m->md_grid = g;
             NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
         }
-        if (!forces_valid) NEP_TRY(run_evaluate<real>(m, n, g, force_d, nullptr, nullptr));
+        if (!forces_valid) NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>()));
     }
     const int n_samples = sample_every > 0 ? n_steps / sample_every : 0;
     NEP_TRY(m->thermo.ensure(sizeof(double) * 12 * std::max(1, n_samples)));
@@ -624,12 +780,13 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     int done = 0;
     if (n_steps >= chunk && !m->timer.on) {  // stage timing runs the steps eagerly
         std::vector<unsigned char> key;
-        auto put = [&](const void* p, size_t sz) {
-            const unsigned char* b = (const unsigned char*)p;
+        auto put = [&](const void* q, size_t sz) {
+            const unsigned char* b = (const unsigned char*)q;
             key.insert(key.end(), b, b + sz);
         };
         const void* ptrs[] = {types_d, pos_d, vel_d, force_d, m->nlR.p, m->nlA.p, m->cell_start.p, m->thermo.p,
-                              m->partial.p, m->rec_s.p, m->phi.p, m->cur};
+                              m->partial.p, m->rec_s.p, m->phi.p, m->e.p, m->cur, p.dev.p, m->counters.p,
+                              m->totals.p};
         put(ptrs, sizeof ptrs);
         put(&n, sizeof n);
         put(&g, sizeof g);
@@ -687,17 +844,17 @@ int neighbors_impl(nep_model* m, int n, const int32_t* types, const double* pos,
     NEP_TRY(make_grid(m, box, pbc, g));
     NEP_TRY(enter(m, nullptr));
     initial_capacity(m, n, box);
+    NEP_TRY(single_plan<real>(m, n, g));
+    const Plan& p = m->plan;
+    NEP_TRY(ensure_plan_workspace(m, p));
     NEP_TRY(m->types_d.ensure(sizeof(int) * n));
     NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
     NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
     NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
-    NEP_TRY(ensure_particles(m, n));
-    NEP_TRY(ensure_cells(m, g.ncell));
-    if ((size_t)n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, n));
     NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
-    NEP_TRY(run_cells<real>(m, n, m->types_d.as<int>(), m->pos_d.as<double>(), g));
-    NEP_TRY(run_neighbors<real>(m, n, g));
-    NEP_TRY(check_lists<real>(m, n, g, nullptr));
+    NEP_TRY(run_cells<real>(m, p, m->types_d.as<int>(), m->pos_d.as<double>()));
+    NEP_TRY(run_neighbors<real>(m, p));
+    NEP_TRY(check_lists<real>(m, p));
     const int mn = kind == 0 ? m->mnR : m->mnA;
     std::vector<uint32_t> nl((size_t)mn * n);
     std::vector<int> cnt(n), perm(n), cell_s(n);
@@ -734,11 +891,103 @@ int neighbors_impl(nep_model* m, int n, const int32_t* types, const double* pos,
     return NEP_OK;
 }
 
+// Many configurations, possibly of several models, in one pass of the pipeline.
+template <typename real>
+int batch_impl(nep_model* const* models, int n_models, int n_req, const int32_t* req_n, const int32_t* req_model,
+               const double* req_box, const int32_t* req_pbc, const int32_t* types, const double* pos, int mem,
+               void* stream, double* energy, double* virial_total, double* site_energy, double* force,
+               double* virial)
+{
+    nep_model* m = models[0];
+    double rc_max = 0.0;
+    for (int k = 0; k < n_models; ++k) rc_max = std::max(rc_max, models[k]->rc_max);
+    Plan& p = m->plan;
+    p.reqs.clear();
+    p.items.clear();
+    p.n = p.ncell = 0;
+    long long total = 0;
+    for (int r = 0; r < n_req; ++r) {
+        if (req_n[r] < 1) return fail(NEP_ERR_ARG, "every request needs at least one particle");
+        if (req_model[r] < 0 || req_model[r] >= n_models) return fail(NEP_ERR_ARG, "request model index out of range");
+        total += req_n[r];
+        if (total > kMaxN) return fail(NEP_ERR_ARG, "batch exceeds 2^23 particles");
+        CellGrid g;
+        NEP_TRY(make_grid(models[req_model[r]], models[req_model[r]]->rc_max, req_box + 3 * r, req_pbc + 3 * r, g));
+        if ((long long)p.ncell + g.ncell > (long long)kScanItems * kScanItems)
+            return fail(NEP_ERR_ARG, "batch cell grids too large");
+        add_request(p, g, req_n[r], req_model[r]);
+    }
+    set_models<real>(p, models, n_models);
+    (void)rc_max;
+    NEP_TRY(enter(m, stream));
+    {
+        double box_avg[3] = {0, 0, 0};  // first sizing of the lists from the largest request
+        int rmax = 0;
+        for (int r = 1; r < n_req; ++r)
+            if (req_n[r] > req_n[rmax]) rmax = r;
+        for (int a = 0; a < 3; ++a) box_avg[a] = req_box[3 * rmax + a];
+        initial_capacity(m, req_n[rmax], box_avg);
+    }
+    NEP_TRY(upload_plan(m, p));
+    NEP_TRY(ensure_plan_workspace(m, p));
+    const int n = p.n;
+    const int* types_d = types;
+    const double* pos_d = pos;
+    double *force_d = force, *virial_d = virial, *site_d = site_energy;
+    if (mem == NEP_HOST) {
+        NEP_TRY(m->types_d.ensure(sizeof(int) * n));
+        NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        types_d = m->types_d.as<int>();
+        pos_d = m->pos_d.as<double>();
+        NEP_TRY(m->force_d.ensure(sizeof(double) * 3 * (size_t)n));
+        force_d = m->force_d.as<double>();
+        virial_d = site_d = nullptr;
+        if (virial) {
+            NEP_TRY(m->virial_d.ensure(sizeof(double) * 9 * (size_t)n));
+            virial_d = m->virial_d.as<double>();
+        }
+        if (site_energy) {
+            NEP_TRY(m->site_d.ensure(sizeof(double) * (size_t)n));
+            site_d = m->site_d.as<double>();
+        }
+    } else if (!force_d) {
+        force_d = m->force_tmp.as<double>();
+    }
+    double* totals = m->totals.as<double>();
+    NEP_TRY(evaluate_plan<real>(m, p, types_d, pos_d, force_d, virial_d, site_d, totals));
+    if (mem == NEP_HOST) {
+        NEP_TRY(ensure_host_totals(m, 10 * (size_t)n_req));
+        if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+        if (virial) NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
+        if (site_energy)
+            NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10 * n_req, cudaMemcpyDeviceToHost, m->cur));
+        NEP_TRY(leave(m, stream));
+        for (int r = 0; r < n_req; ++r) {
+            if (energy) energy[r] = m->h_totals[10 * r];
+            if (virial_total)
+                for (int k = 0; k < 9; ++k) virial_total[9 * r + k] = m->h_totals[10 * r + 1 + k];
+        }
+    } else {
+        // totals [req][10] -> energy[req], virial_total[req][9] on the device
+        if (energy)
+            NEP_CUDA(cudaMemcpy2DAsync(energy, sizeof(double), totals, 10 * sizeof(double), sizeof(double), n_req,
+                                       cudaMemcpyDeviceToDevice, m->cur));
+        if (virial_total)
+            NEP_CUDA(cudaMemcpy2DAsync(virial_total, 9 * sizeof(double), totals + 1, 10 * sizeof(double),
+                                       9 * sizeof(double), n_req, cudaMemcpyDeviceToDevice, m->cur));
+        NEP_TRY(leave(m, stream));
+    }
+    return NEP_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-int nep_version(void) { return (0 << 16) | 1; }
+int nep_version(void) { return (0 << 16) | 2; }
 
 const char* nep_error_string(int code)
 {
@@ -760,6 +1009,34 @@ const char* nep_last_error(void) { return g_last_error.c_str(); }
 int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial, int n_basis_angular, int l_max)
 {
     return l_max == 4 && evaluate_shape_supported<float>(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular);
+}
+
+int nep_destroy(nep_model* m)
+{
+    if (!m) return NEP_OK;
+    Guard guard(m->device);
+    if (m->st) cudaStreamSynchronize(m->st);
+    if (m->async_pending && m->ev_flags) cudaEventSynchronize(m->ev_flags);
+    if (m->plan_pending && m->ev_plan) cudaEventSynchronize(m->ev_plan);
+    m->graph.reset();
+    m->timer.destroy();
+    Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
+                   &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
+                   &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
+                   &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
+                   &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev};
+    for (Buf* b : bufs) b->release();
+    if (m->h_flags) cudaFreeHost(m->h_flags);
+    if (m->h_totals) cudaFreeHost(m->h_totals);
+    if (m->h_async) cudaFreeHost(m->h_async);
+    if (m->h_stage) cudaFreeHost(m->h_stage);
+    if (m->ev_flags) cudaEventDestroy(m->ev_flags);
+    if (m->ev_plan) cudaEventDestroy(m->ev_plan);
+    if (m->ev_in) cudaEventDestroy(m->ev_in);
+    if (m->ev_out) cudaEventDestroy(m->ev_out);
+    if (m->st) cudaStreamDestroy(m->st);
+    delete m;
+    return NEP_OK;
 }
 
 int nep_create(nep_model** out, int n_types, const double* rc_radial, const double* rc_angular, int n_basis_radial,
@@ -856,7 +1133,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     // [24][n_A][block] tile of the centre particles' Phi
     m->tile_offset = (m->real_size * o.n_cut_coef + 15) & ~(size_t)15;
     m->smem_force = m->tile_offset + (precision == NEP_FP32 ? sizeof(float) * 24 * m->nA * kBlock : 0);
-    if (m->smem_desc > 200 * 1024) return cleanup(fail(NEP_ERR_ARG, "model too large for shared-memory staging"));
+    if (m->smem_desc > 200 * 1024 || m->smem_force > 200 * 1024)
+        return cleanup(fail(NEP_ERR_ARG, "model too large for shared-memory staging"));
     // the attribute is per kernel, shared by all handles: allow the largest staging size
     const size_t smem_cap = 200 * 1024;
     cudaError_t e = precision == NEP_FP64
@@ -866,42 +1144,19 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&m->ev_flags, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&m->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&m->ev_plan, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(NEP_ERR_CUDA, "stream/event creation failed"));
-    if (m->counters.ensure(sizeof(unsigned int) * 4) != NEP_OK || m->totals.ensure(sizeof(double) * 10) != NEP_OK ||
-        m->flags.ensure(sizeof(int) * 4) != NEP_OK)
-        return cleanup(NEP_ERR_OOM);
-    if (cudaMemset(m->counters.p, 0, sizeof(unsigned int) * 4) != cudaSuccess ||
-        cudaMemset(m->flags.p, 0, sizeof(int) * 4) != cudaSuccess ||
+    if (m->flags.ensure(sizeof(int) * 4) != NEP_OK) return cleanup(NEP_ERR_OOM);
+    if (cudaMemset(m->flags.p, 0, sizeof(int) * 4) != cudaSuccess ||
         cudaMallocHost((void**)&m->h_flags, sizeof(int) * 4) != cudaSuccess ||
-        cudaMallocHost((void**)&m->h_totals, sizeof(double) * 10) != cudaSuccess ||
-        cudaMallocHost((void**)&m->h_async, sizeof(int) * 4) != cudaSuccess)
+        cudaMallocHost((void**)&m->h_async, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_stage, 16384) != cudaSuccess ||
+        cudaMallocHost((void**)&m->h_totals, sizeof(double) * 10) != cudaSuccess)
         return cleanup(fail(NEP_ERR_CUDA, "workspace initialisation failed"));
+    m->h_stage_cap = 16384;
+    m->h_totals_cap = 10;
     *out = m;
-    return NEP_OK;
-}
-
-int nep_destroy(nep_model* m)
-{
-    if (!m) return NEP_OK;
-    Guard guard(m->device);
-    if (m->st) cudaStreamSynchronize(m->st);
-    m->graph.reset();
-    m->timer.destroy();
-    Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm, &m->rec_s, &m->cell_s, &m->cntR, &m->cntA,
-                   &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
-                   &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
-                   &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
-                   &m->site_d, &m->force_tmp};
-    for (Buf* b : bufs) b->release();
-    if (m->h_flags) cudaFreeHost(m->h_flags);
-    if (m->h_totals) cudaFreeHost(m->h_totals);
-    if (m->h_async) cudaFreeHost(m->h_async);
-    if (m->ev_flags) cudaEventDestroy(m->ev_flags);
-    if (m->ev_in) cudaEventDestroy(m->ev_in);
-    if (m->ev_out) cudaEventDestroy(m->ev_out);
-    if (m->cur) cudaStreamDestroy(m->cur);
-    delete m;
     return NEP_OK;
 }
 
@@ -911,11 +1166,38 @@ int nep_compute(nep_model* m, int n, const int32_t* types, const double* pos, co
 {
     NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
     Guard guard(m->device);
+    NEP_TRY(inspect_async(m, true));
     return m->precision == NEP_FP64
                ? compute_impl<double>(m, n, types, pos, box, pbc, mem, stream, energy_total, virial_total, site_energy,
                                       force, virial)
                : compute_impl<float>(m, n, types, pos, box, pbc, mem, stream, energy_total, virial_total, site_energy,
                                      force, virial);
+}
+
+int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const int32_t* req_n,
+                      const int32_t* req_model, const double* req_box, const int32_t* req_pbc, const int32_t* types,
+                      const double* pos, int mem, void* stream, double* energy, double* virial_total,
+                      double* site_energy, double* force, double* virial)
+{
+    if (!models || n_models < 1 || !models[0]) return fail(NEP_ERR_ARG, "no models");
+    if (n_req < 1 || !req_n || !req_model || !req_box || !req_pbc || !types || !pos)
+        return fail(NEP_ERR_ARG, "bad request arrays");
+    if (mem != NEP_HOST && mem != NEP_DEVICE) return fail(NEP_ERR_ARG, "mem must be NEP_HOST or NEP_DEVICE");
+    nep_model* m = models[0];
+    for (int k = 0; k < n_models; ++k) {
+        const nep_model* o = models[k];
+        if (!o) return fail(NEP_ERR_ARG, "null model in batch");
+        if (o->device != m->device || o->precision != m->precision || o->nR != m->nR || o->nA != m->nA ||
+            o->KR != m->KR || o->KA != m->KA || o->L != m->L)
+            return fail(NEP_ERR_ARG, "batched models must share device, precision and descriptor sizes");
+    }
+    Guard guard(m->device);
+    NEP_TRY(inspect_async(m, true));
+    return m->precision == NEP_FP64
+               ? batch_impl<double>(models, n_models, n_req, req_n, req_model, req_box, req_pbc, types, pos, mem,
+                                    stream, energy, virial_total, site_energy, force, virial)
+               : batch_impl<float>(models, n_models, n_req, req_n, req_model, req_box, req_pbc, types, pos, mem,
+                                   stream, energy, virial_total, site_energy, force, virial);
 }
 
 int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
@@ -960,6 +1242,7 @@ int nep_neighbors(nep_model* m, int n, const int32_t* types, const double* pos, 
     if (kind != 0 && kind != 1) return fail(NEP_ERR_ARG, "kind must be 0 or 1");
     if (capacity < 1 || !count || !j || !shift) return fail(NEP_ERR_ARG, "bad output buffers");
     Guard guard(m->device);
+    NEP_TRY(inspect_async(m, true));
     return m->precision == NEP_FP64 ? neighbors_impl<double>(m, n, types, pos, box, pbc, kind, capacity, count, j, shift)
                                     : neighbors_impl<float>(m, n, types, pos, box, pbc, kind, capacity, count, j, shift);
 }
@@ -1029,15 +1312,17 @@ constexpr int kStaticMNA = 128;          // angular neighbours per particle
 constexpr int kStaticMaxNA = 5;          // n_A of the compiled shapes
 constexpr int kStaticMaxT = 4;           // particle types of the model
 constexpr int kStaticMaxKRP = 12;        // padded K_R
+constexpr int kStaticMaxItems = (kStaticMaxN + kBlock - 1) / kBlock;
+constexpr size_t kStaticTableBytes = 2048;  // one request, its work items, one model
 constexpr int kStaticMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte layout of the scratch for n particles, ncell cells, real of rs bytes.
 struct StaticLayout {
-    size_t cell_of, rec_user, perm, rec_s, cell_s, cntR, cntA, U, e, phi, force;
+    size_t cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, U, e, phi, force;
     size_t nlR, nlA, cell_count, cell_local, block_off, cell_fill, cell_start;
-    size_t partial, counters, totals, flags, end;
+    size_t partial, counters, totals, flags, tables, end;
 };
 
 constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t nA, size_t ekrp)
@@ -1046,6 +1331,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     size_t p = 0;
     L.cell_of = p; p = align256(p + 4 * n);
     L.rec_user = p; p = align256(p + 4 * rs * n);
+    L.perm_tmp = p; p = align256(p + 4 * n);
     L.perm = p; p = align256(p + 4 * n);
     L.rec_s = p; p = align256(p + 4 * rs * n);
     L.cell_s = p; p = align256(p + 4 * n);
@@ -1066,6 +1352,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     L.counters = p; p = align256(p + 16);
     L.totals = p; p = align256(p + 8 * 10);
     L.flags = p; p = align256(p + 16);
+    L.tables = p; p = align256(p + kStaticTableBytes);
     L.end = p;
     return L;
 }
@@ -1106,6 +1393,33 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     NEP_TRY(static_scratch(m->device, &base));
     const StaticLayout L = static_layout(n, g.ncell, sizeof(real), m->nA, (size_t)m->T * m->KRP);
     if (L.end > kStaticScratchBytes) return fail(NEP_ERR_ARG, "static scratch too small for this call");
+    // the request, its work items and the model table, staged through the handle's
+    // pinned buffer (allocated by nep_create) into the scratch
+    ReqInfo rq;
+    rq.g = g;
+    rq.cell_base = 0;
+    rq.begin = 0;
+    rq.n = n;
+    rq.model = 0;
+    rq.item_begin = 0;
+    WorkItem items[kStaticMaxItems];
+    int n_items = 0;
+    for (int b = 0; b < n; b += kBlock) items[n_items++] = WorkItem{0, b, std::min(n, b + kBlock)};
+    rq.item_end = n_items;
+    const ModelDesc<real> md = model_desc<real>(m);
+    const size_t off_items = align16(sizeof(ReqInfo)), off_models = off_items + align16(sizeof(WorkItem) * n_items);
+    if (m->plan_pending) NEP_CUDA(cudaEventSynchronize(m->ev_plan));
+    memcpy(m->h_stage, &rq, sizeof rq);
+    memcpy(m->h_stage + off_items, items, sizeof(WorkItem) * n_items);
+    memcpy(m->h_stage + off_models, &md, sizeof md);
+    unsigned char* tables = base + L.tables;
+    NEP_CUDA(cudaMemcpyAsync(tables, m->h_stage, off_models + sizeof md, cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaEventRecord(m->ev_plan, m->cur));
+    m->plan_pending = true;
+    const ReqInfo* d_rq = (const ReqInfo*)tables;
+    const WorkItem* d_it = (const WorkItem*)(tables + off_items);
+    const ModelDesc<real>* d_md = (const ModelDesc<real>*)(tables + off_models);
+
     int* flags = (int*)(base + L.flags);
     unsigned int* counters = (unsigned int*)(base + L.counters);
     double* totals = (double*)(base + L.totals);
@@ -1114,47 +1428,45 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     NEP_CUDA(cudaMemsetAsync(flags, 0, 16, m->cur));
     NEP_CUDA(cudaMemsetAsync(counters, 0, 16, m->cur));
     cudaError_t e = launch_cell_build<real>(
-        n, pos, types, m->T, g, (int*)(base + L.cell_of), (PosRec<real>*)(base + L.rec_user),
-        (int*)(base + L.cell_count), (int*)(base + L.cell_local), (int*)(base + L.block_off),
-        (int*)(base + L.cell_fill), (int*)(base + L.perm), (int*)(base + L.cell_start), (int*)(base + L.cell_s),
-        (PosRec<real>*)(base + L.rec_s), flags + 2, m->cur);
+        n, n_items, g.ncell, d_it, d_rq, d_md, pos, types, (int*)(base + L.cell_of),
+        (PosRec<real>*)(base + L.rec_user), (int*)(base + L.cell_count), (int*)(base + L.cell_local),
+        (int*)(base + L.block_off), (int*)(base + L.cell_fill), (int*)(base + L.perm_tmp), (int*)(base + L.perm),
+        (int*)(base + L.cell_start), (int*)(base + L.cell_s), (PosRec<real>*)(base + L.rec_s), flags + 2, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
     NeighborArgs<real> na;
     na.n = n;
-    na.T = m->T;
     na.mnR = kStaticMNR;
     na.mnA = kStaticMNA;
-    na.g = g;
+    na.items = d_it;
+    na.reqs = d_rq;
+    na.models = d_md;
     na.cell_start = (int*)(base + L.cell_start);
     na.cell_s = (int*)(base + L.cell_s);
     na.rec = (PosRec<real>*)(base + L.rec_s);
-    na.params = m->params.as<real>();
-    na.off = m->off;
     na.nlR = (uint32_t*)(base + L.nlR);
     na.nlA = (uint32_t*)(base + L.nlA);
     na.cntR = (int*)(base + L.cntR);
     na.cntA = (int*)(base + L.cntA);
     na.maxcnt = flags;
-    e = launch_neighbors<real>(na, m->cur);
+    e = launch_neighbors<real>(na, n_items, 2 * sizeof(real) * m->T * m->T, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     EvalArgs<real> a;
     a.n = n;
-    a.T = m->T;
-    a.H = m->H;
     a.mnR = kStaticMNR;
     a.mnA = kStaticMNA;
-    for (int k = 0; k < 3; ++k) a.len[k] = (real)g.len[k];
+    a.items = d_it;
+    a.reqs = d_rq;
+    a.models = d_md;
     a.rec = na.rec;
     a.nlR = na.nlR;
     a.nlA = na.nlA;
     a.cntR = na.cntR;
     a.cntA = na.cntA;
-    a.params = na.params;
-    a.off = m->off;
     a.U = (real*)(base + L.U);
     a.e = (real*)(base + L.e);
-    a.tile_offset = (int)m->tile_offset;
+    a.e_stride = m->T * m->KRP;
     a.phi = (real*)(base + L.phi);
+    a.tile_offset = (int)m->tile_offset;
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;
@@ -1162,7 +1474,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
     a.totals = totals;
-    e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, m->smem_desc, m->smem_force, m->cur);
+    e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     if (energy_total) NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
     if (virial_total)

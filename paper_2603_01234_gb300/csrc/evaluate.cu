@@ -39,7 +39,14 @@ constexpr int kNLM = 24;
 constexpr int kForceMinBlocks = NEP_FORCE_MIN_BLOCKS;
 constexpr int kDescMinBlocks = NEP_DESC_MIN_BLOCKS;
 
-__device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
+// sin(pi x), cos(pi x) for x = r / r_c in [0, 1].  FP32 uses the hardware
+// approximations (absolute error below 4e-7 on [0, pi]); FP64 the accurate routine.
+__device__ __forceinline__ void sincospi_r(float x, float* s, float* c)
+{
+    const float t = 3.14159265358979f * x;
+    *s = __sinf(t);
+    *c = __cosf(t);
+}
 __device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
 
 // Chebyshev basis f_k(r) of Eq. 7 with the cutoff of Eq. 8, k = 0..K-1, by the
@@ -49,46 +56,48 @@ __device__ __forceinline__ void basis(real r, real inv_rc, real* f)
 {
     real sn, cs;
     sincospi_r(r * inv_rc, &sn, &cs);
-    const real fc = real(0.5) * (real(1) + cs);
+    const real hf = real(0.25) + real(0.25) * cs;  // f_c / 2
     const real s = r * inv_rc - real(1);
     const real x = real(2) * s * s - real(1);
+    const real x2 = x + x;
     real t0 = real(1), t1 = x;
-    const real hf = real(0.5) * fc;
-    f[0] = fc;
-    if (K > 1) f[1] = hf * (x + real(1));
+    f[0] = hf + hf;
+    if (K > 1) f[1] = hf * x + hf;
 #pragma unroll
     for (int k = 2; k < K; ++k) {
-        const real t2 = real(2) * x * t1 - t0;
-        f[k] = hf * (t2 + real(1));
+        const real t2 = x2 * t1 - t0;
+        f[k] = hf * t2 + hf;  // (T_k + 1) f_c / 2
         t0 = t1;
         t1 = t2;
     }
 }
 
-// f_k and df_k/dr.
+// f_k and df_k/dr:  df_k = 1/2 [T_k'(x) x'(r) f_c + (T_k + 1) f_c'],
+// with T'_{k+1} = 2 T_k + 2 x T'_k - T'_{k-1}.
 template <typename real, int K>
 __device__ __forceinline__ void basis_d(real r, real inv_rc, real* f, real* df)
 {
     real sn, cs;
     sincospi_r(r * inv_rc, &sn, &cs);
-    const real fc = real(0.5) * (real(1) + cs);
-    const real dfc = real(-0.5) * real(3.14159265358979323846) * inv_rc * sn;
+    const real hf = real(0.25) + real(0.25) * cs;                           // f_c / 2
+    const real hdf = real(-0.25 * 3.14159265358979323846) * inv_rc * sn;    // f_c' / 2
     const real s = r * inv_rc - real(1);
     const real x = real(2) * s * s - real(1);
-    const real dxdr = real(4) * s * inv_rc;
+    const real hdx = real(4) * s * inv_rc * hf;                             // x'(r) f_c / 2
+    const real x2 = x + x;
     real t0 = real(1), t1 = x, d0 = real(0), d1 = real(1);
-    f[0] = fc;
-    df[0] = dfc;
+    f[0] = hf + hf;
+    df[0] = hdf + hdf;
     if (K > 1) {
-        f[1] = real(0.5) * (x + real(1)) * fc;
-        df[1] = real(0.5) * (dxdr * fc + (x + real(1)) * dfc);
+        f[1] = hf * x + hf;
+        df[1] = hdx + (hdf * x + hdf);
     }
 #pragma unroll
     for (int k = 2; k < K; ++k) {
-        const real t2 = real(2) * x * t1 - t0;
-        const real d2 = real(2) * t1 + real(2) * x * d1 - d0;
-        f[k] = real(0.5) * (t2 + real(1)) * fc;
-        df[k] = real(0.5) * (d2 * dxdr * fc + (t2 + real(1)) * dfc);
+        const real t2 = x2 * t1 - t0;
+        const real d2 = real(2) * t1 + (x2 * d1 - d0);
+        f[k] = hf * t2 + hf;
+        df[k] = d2 * hdx + (hdf * t2 + hdf);
         t0 = t1;
         t1 = t2;
         d0 = d1;
@@ -96,17 +105,45 @@ __device__ __forceinline__ void basis_d(real r, real inv_rc, real* f, real* df)
     }
 }
 
+// Pair vector r_ij from i's and j's records and the entry's cell offset.
 template <typename real>
-__device__ __forceinline__ void pair_vector(const EvalArgs<real>& a, const PosRec<real>& ri, uint32_t e,
-                                            PosRec<real>& rj, real& dx, real& dy, real& dz)
+__device__ __forceinline__ void pair_vec(const real* len, const PosRec<real>& ri, const PosRec<real>& rj, uint32_t e,
+                                         real& dx, real& dy, real& dz)
 {
-    const int j = (int)(e & kJMask);
     const uint32_t code = e >> kJBits;
-    rj = a.rec[j];
-    dx = (rj.x - ri.x) + (real)((int)(code & 7u) - 2) * a.len[0];
-    dy = (rj.y - ri.y) + (real)((int)((code >> 3) & 7u) - 2) * a.len[1];
-    dz = (rj.z - ri.z) + (real)((int)((code >> 6) & 7u) - 2) * a.len[2];
+    dx = (rj.x - ri.x) + (real)((int)(code & 7u) - 2) * len[0];
+    dy = (rj.y - ri.y) + (real)((int)((code >> 3) & 7u) - 2) * len[1];
+    dz = (rj.z - ri.z) + (real)((int)((code >> 6) & 7u) - 2) * len[2];
 }
+
+// Software-pipelined walk over one particle's neighbour list: the entries are
+// loaded two iterations ahead and the neighbour's record one iteration ahead, so
+// the dependent load chain (entry -> record) overlaps the previous pair's math.
+template <typename real>
+struct NbrWalk {
+    const uint32_t* nl;  // &list[0][i]
+    size_t stride;
+    int cnt;
+    const PosRec<real>* rec;
+    uint32_t e0, e1;
+    PosRec<real> r0;
+    __device__ __forceinline__ NbrWalk(const uint32_t* list, int n, int i, int c, const PosRec<real>* recs)
+        : nl(list + i), stride((size_t)n), cnt(c), rec(recs)
+    {
+        e0 = c > 0 ? nl[0] : 0u;
+        e1 = c > 1 ? nl[stride] : 0u;
+        r0 = rec[e0 & kJMask];  // index 0 is valid even for an empty list
+    }
+    // current entry and record, then advance the pipeline (s = current index)
+    __device__ __forceinline__ void next(int s, uint32_t& e, PosRec<real>& rj)
+    {
+        e = e0;
+        rj = r0;
+        e0 = e1;
+        e1 = (s + 2 < cnt) ? nl[(size_t)(s + 2) * stride] : 0u;
+        r0 = rec[e0 & kJMask];
+    }
+};
 
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
@@ -125,10 +162,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
     constexpr int KRP = (KR + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
-    stage_params(a.params, P, a.off.total);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const int T = a.T;
+    const WorkItem it = a.items[blockIdx.x];
+    const ReqInfo& rq = a.reqs[it.req];
+    const ModelDesc<real> md = a.models[rq.model];
+    const ParamLayout off = md.off;
+    stage_params(md.params, P, off.total);
+    const int i = it.begin + threadIdx.x;
+    if (i >= it.end) return;
+    const int T = md.T, H = md.H;
+    const real len[3] = {(real)rq.g.len[0], (real)rq.g.len[1], (real)rq.g.len[2]};
     const PosRec<real> ri = a.rec[i];
     const int ti = ri.t;
     real q[ND];
@@ -137,24 +179,55 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
 
     // ---- radial descriptors (Eq. 3, 6-8) ----
     const int cR = min(a.cntR[i], a.mnR);
-    for (int s = 0; s < cR; ++s) {
-        const uint32_t e = a.nlR[(size_t)s * a.n + i];
-        PosRec<real> rj;
-        real dx, dy, dz;
-        pair_vector(a, ri, e, rj, dx, dy, dz);
-        const real r2 = dx * dx + dy * dy + dz * dz;
-        const real inv_r = rsqrt_r(r2);
-        const real r = r2 * inv_r;
-        const int tp = ti * T + rj.t;
-        real f[KR];
-        basis<real, KR>(r, P[a.off.rcRi + tp], f);
-        const real* c = P + a.off.cR + tp * NR * KR;
+    if (T == 1) {
+        // one pair type: q_n = sum_k c_nk (sum_j f_k(r_ij)), contracted once per bead
+        real fs[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) fs[k] = real(0);
+        const real inv_rc = P[off.rcRi];
+        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
+        for (int s = 0; s < cR; ++s) {
+            uint32_t e;
+            PosRec<real> rj;
+            w.next(s, e, rj);
+            real dx, dy, dz;
+            pair_vec(len, ri, rj, e, dx, dy, dz);
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const real r = r2 * rsqrt_r(r2);
+            real f[KR];
+            basis<real, KR>(r, inv_rc, f);
+#pragma unroll
+            for (int k = 0; k < KR; ++k) fs[k] += f[k];
+        }
+        const real* c = P + off.cR;
 #pragma unroll
         for (int nn = 0; nn < NR; ++nn) {
             real g = real(0);
 #pragma unroll
-            for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * f[k];
-            q[nn] += g;
+            for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * fs[k];
+            q[nn] = g;
+        }
+    } else {
+        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
+        for (int s = 0; s < cR; ++s) {
+            uint32_t e;
+            PosRec<real> rj;
+            w.next(s, e, rj);
+            real dx, dy, dz;
+            pair_vec(len, ri, rj, e, dx, dy, dz);
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const real r = r2 * rsqrt_r(r2);
+            const int tp = ti * T + rj.t;
+            real f[KR];
+            basis<real, KR>(r, P[off.rcRi + tp], f);
+            const real* c = P + off.cR + tp * NR * KR;
+#pragma unroll
+            for (int nn = 0; nn < NR; ++nn) {
+                real g = real(0);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * f[k];
+                q[nn] += g;
+            }
         }
     }
 
@@ -165,18 +238,20 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
 #pragma unroll
         for (int k = 0; k < kNLM; ++k) A[nn][k] = real(0);
     const int cA = min(a.cntA[i], a.mnA);
+    NbrWalk<real> wa(a.nlA, a.n, i, cA, a.rec);
     for (int s = 0; s < cA; ++s) {
-        const uint32_t e = a.nlA[(size_t)s * a.n + i];
+        uint32_t e;
         PosRec<real> rj;
+        wa.next(s, e, rj);
         real dx, dy, dz;
-        pair_vector(a, ri, e, rj, dx, dy, dz);
+        pair_vec(len, ri, rj, e, dx, dy, dz);
         const real r2 = dx * dx + dy * dy + dz * dz;
         const real inv_r = rsqrt_r(r2);
         const real r = r2 * inv_r;
         const int tp = ti * T + rj.t;
         real f[KA];
-        basis<real, KA>(r, P[a.off.rcAi + tp], f);
-        const real* c = P + a.off.cA + tp * NA * KA;
+        basis<real, KA>(r, P[off.rcAi + tp], f);
+        const real* c = P + off.cA + tp * NA * KA;
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
 #pragma unroll
@@ -195,14 +270,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
         for (int k = 0; k < kNLM; ++k) q[NR + (l_of(k) - 1) * NA + nn] += A[nn][k] * A[nn][k];
 
     // ---- network (Eq. 2) and dU/dq ----
-    const real* w0 = P + a.off.w0 + ti * a.H * ND;
-    const real* b0 = P + a.off.b0 + ti * a.H;
-    const real* w1 = P + a.off.w1 + ti * a.H;
-    real U = -P[a.off.b1 + ti];
+    const real* w0 = P + off.w0 + ti * H * ND;
+    const real* b0 = P + off.b0 + ti * H;
+    const real* w1 = P + off.w1 + ti * H;
+    real U = -P[off.b1 + ti];
     real dq[ND];
 #pragma unroll
     for (int v = 0; v < ND; ++v) dq[v] = real(0);
-    for (int mu = 0; mu < a.H; ++mu) {
+    for (int mu = 0; mu < H; ++mu) {
         real x = -b0[mu];
 #pragma unroll
         for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
@@ -214,9 +289,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
     }
     a.U[i] = U;
     // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
-    real* ei = a.e + (size_t)i * T * KRP;
+    real* ei = a.e + (size_t)i * a.e_stride;
     for (int t = 0; t < T; ++t) {
-        const real* c = P + a.off.cR + (ti * T + t) * NR * KR;
+        const real* c = P + off.cR + (ti * T + t) * NR * KR;
 #pragma unroll
         for (int k = 0; k < KRP; ++k) {
             real v = real(0);
@@ -242,9 +317,10 @@ __device__ __forceinline__ real warp_sum(real v)
     return v;
 }
 
-// FP64 block partials of (E, W[9]) and a deterministic last-block total.
-__device__ __forceinline__ void reduce_totals(double (&v)[10], double* partial, unsigned int* counter,
-                                              double* totals)
+// FP64 block partials of (E, W[9]); the last block of a request sums its request's
+// partials in item order (deterministic) into totals[req].
+__device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& it, const ReqInfo& rq,
+                                              double* partial, unsigned int* counter, double* totals)
 {
     __shared__ double red[kBlock / 32][10];
     __shared__ bool last;
@@ -263,17 +339,18 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], double* partial, 
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    const unsigned int n_items = (unsigned int)(rq.item_end - rq.item_begin);
+    if (threadIdx.x == 0) last = (atomicAdd(&counter[it.req], 1u) == n_items - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
     if (threadIdx.x < 10) {
         double s = 0.0;
         const volatile double* p = partial;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)b * 10 + threadIdx.x];
-        totals[threadIdx.x] = s;
+        for (int b = rq.item_begin; b < rq.item_end; ++b) s += p[(size_t)b * 10 + threadIdx.x];
+        totals[(size_t)it.req * 10 + threadIdx.x] = s;
     }
-    if (threadIdx.x == 0) *counter = 0u;
+    if (threadIdx.x == 0) counter[it.req] = 0u;
 }
 
 // 4 consecutive reals (16-byte aligned) into registers
@@ -307,13 +384,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
     real* tile = reinterpret_cast<real*>(smem_raw + a.tile_offset);
-    stage_params(a.params, P, a.off.n_cut_coef);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const WorkItem it = a.items[blockIdx.x];
+    const ReqInfo& rq = a.reqs[it.req];
+    const ModelDesc<real> md = a.models[rq.model];
+    const ParamLayout off = md.off;
+    stage_params(md.params, P, off.n_cut_coef);
+    const int i = it.begin + threadIdx.x;
     double tot[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) tot[k] = 0.0;
-    if (i < a.n) {
-        const int T = a.T;
+    if (i < it.end) {
+        const int T = md.T;
+        const real len[3] = {(real)rq.g.len[0], (real)rq.g.len[1], (real)rq.g.len[2]};
         const PosRec<real> ri = a.rec[i];
         const int ti = ri.t;
         real F[3] = {real(0), real(0), real(0)};
@@ -322,22 +404,35 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
         for (int k = 0; k < 9; ++k) W[k] = real(0);
 
         // ---- radial pairs: f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u ----
-        const real* e_i = a.e + (size_t)i * T * KRP;
+        const real* e_i = a.e + (size_t)i * a.e_stride;
+        real ei1[KRP];  // the one partner type's vector, when the model has one type
+        if (T == 1) loadN<real, KRP>(e_i, ei1);
         const int cR = min(a.cntR[i], a.mnR);
+        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
+        real eji_next[KRP];  // j's radial vector, one pair ahead
+        loadN<real, KRP>(a.e + (size_t)(w.e0 & kJMask) * a.e_stride + ti * KRP, eji_next);
         for (int s = 0; s < cR; ++s) {
-            const uint32_t e = a.nlR[(size_t)s * a.n + i];
-            const int j = (int)(e & kJMask);
+            uint32_t e;
             PosRec<real> rj;
+            w.next(s, e, rj);
+            real eji[KRP];
+#pragma unroll
+            for (int k = 0; k < KRP; ++k) eji[k] = eji_next[k];
+            loadN<real, KRP>(a.e + (size_t)(w.e0 & kJMask) * a.e_stride + ti * KRP, eji_next);
             real dx, dy, dz;
-            pair_vector(a, ri, e, rj, dx, dy, dz);
+            pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real inv_r = rsqrt_r(r2);
             const real r = r2 * inv_r;
             real f[KR], df[KR];
-            basis_d<real, KR>(r, P[a.off.rcRi + ti * T + rj.t], f, df);
-            real eij[KRP], eji[KRP];
-            loadN<real, KRP>(e_i + rj.t * KRP, eij);
-            loadN<real, KRP>(a.e + ((size_t)j * T + ti) * KRP, eji);
+            basis_d<real, KR>(r, P[off.rcRi + ti * T + rj.t], f, df);
+            real eij[KRP];
+            if (T == 1) {
+#pragma unroll
+                for (int k = 0; k < KRP; ++k) eij[k] = ei1[k];
+            } else {
+                loadN<real, KRP>(e_i + rj.t * KRP, eij);
+            }
             real ai = real(0), bj = real(0);
 #pragma unroll
             for (int k = 0; k < KR; ++k) {
@@ -360,26 +455,30 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
 
         // ---- angular pairs ----
         const real* phi_i = a.phi + (size_t)i * kNLM * NA;
-        if (kTile) {
+        if (kTile) {  // column of this thread: [k][nn] at ((k * kBlock + thread) * NA + nn)
 #pragma unroll
-            for (int k = 0; k < kNLM * NA; ++k) tile[k * kBlock + threadIdx.x] = phi_i[k];
+            for (int k = 0; k < kNLM; ++k)
+#pragma unroll
+                for (int nn = 0; nn < NA; ++nn) tile[(k * kBlock + threadIdx.x) * NA + nn] = phi_i[k * NA + nn];
         }
         const int cA = min(a.cntA[i], a.mnA);
+        NbrWalk<real> wa(a.nlA, a.n, i, cA, a.rec);
         for (int s = 0; s < cA; ++s) {
-            const uint32_t e = a.nlA[(size_t)s * a.n + i];
-            const int j = (int)(e & kJMask);
+            uint32_t e;
             PosRec<real> rj;
+            wa.next(s, e, rj);
+            const int j = (int)(e & kJMask);
             real dx, dy, dz;
-            pair_vector(a, ri, e, rj, dx, dy, dz);
+            pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real inv_r = rsqrt_r(r2);
             const real r = r2 * inv_r;
             const int tij = ti * T + rj.t, tji = rj.t * T + ti;
             real f[KA], df[KA];
-            basis_d<real, KA>(r, P[a.off.rcAi + tij], f, df);
+            basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
             real gi[NA], dgi[NA], gj[NA], dgj[NA];
             {
-                const real* c = P + a.off.cA + tij * NA * KA;
+                const real* c = P + off.cA + tij * NA * KA;
 #pragma unroll
                 for (int nn = 0; nn < NA; ++nn) {
                     real s0 = real(0), s1 = real(0);
@@ -399,7 +498,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
                     dgj[nn] = dgi[nn];
                 }
             } else {
-                const real* c = P + a.off.cA + tji * NA * KA;
+                const real* c = P + off.cA + tji * NA * KA;
 #pragma unroll
                 for (int nn = 0; nn < NA; ++nn) {
                     real s0 = real(0), s1 = real(0);
@@ -422,8 +521,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
                 const real lr = real(l_of(k)) * inv_r;
                 real pi_[NA], pj[NA];
                 if (kTile) {
-#pragma unroll
-                    for (int nn = 0; nn < NA; ++nn) pi_[nn] = tile[(k * NA + nn) * kBlock + threadIdx.x];
+                    loadN<real, NA>(tile + (k * kBlock + threadIdx.x) * NA, pi_);
                 } else {
                     loadN<real, NA>(phi_i + k * NA, pi_);
                 }
@@ -467,19 +565,22 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
         }
 
         const int ui = a.perm[i];
+        const int lu = ui - rq.begin;  // index within the request's output blocks
         const real Ui = a.U[i];
+        double* fo = a.force + (size_t)3 * rq.begin + lu;
 #pragma unroll
-        for (int p = 0; p < 3; ++p) a.force[(size_t)p * a.n + ui] = (double)F[p];
+        for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
         if (a.virial) {
+            double* vo = a.virial + (size_t)9 * rq.begin + lu;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) a.virial[(size_t)k * a.n + ui] = (double)W[k];
+            for (int k = 0; k < 9; ++k) vo[(size_t)k * rq.n] = (double)W[k];
         }
         if (a.site) a.site[ui] = (double)Ui;
         tot[0] = (double)Ui;
 #pragma unroll
         for (int k = 0; k < 9; ++k) tot[1 + k] = (double)W[k];
     }
-    reduce_totals(tot, a.partial, a.counter, a.totals);
+    reduce_totals(tot, it, rq, a.partial, a.counter, a.totals);
 }
 
 // ---- shape dispatch -----------------------------------------------------------
@@ -512,10 +613,10 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
 }
 
 template <typename real>
-cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, size_t smem_desc,
+cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid)
 {
-    const int nb = (a.n + kBlock - 1) / kBlock;
+    const int nb = n_items;
 #define NEP_CASE(a_, b_, c_, d_)                                                          \
     if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                   \
         k_descriptor<real, a_, b_, c_, d_><<<nb, kBlock, smem_desc, st>>>(a);             \
@@ -531,7 +632,7 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
 #define NEP_INSTANTIATE(real)                                                                             \
     template bool evaluate_shape_supported<real>(int, int, int, int);                                     \
     template cudaError_t evaluate_set_smem<real>(int, int, int, int, size_t, size_t);                     \
-    template cudaError_t launch_evaluate<real>(int, int, int, int, const EvalArgs<real>&, size_t, size_t, \
+    template cudaError_t launch_evaluate<real>(int, int, int, int, const EvalArgs<real>&, int, size_t, size_t, \
                                                cudaStream_t, cudaEvent_t);
 NEP_INSTANTIATE(float)
 NEP_INSTANTIATE(double)

@@ -1,11 +1,11 @@
 // Cell list and neighbour lists (the neighbour search that precedes Eq. 3-5).
 //
-// Per configuration:
+// Per batch of configurations (requests), each with its own box and cell grid:
 //   k_bin        wrap periodic axes, bin every particle into a cell, store its
 //                cell-relative position (FP32 or FP64) and count cell members
 //   k_scan_*     exclusive scan of the cell counts (two levels)
 //   k_scatter    counting-sort scatter of particle indices into cell order
-//   k_cell_sort  sort each cell's members by caller index (deterministic order)
+//   k_cell_rank  order each cell's members by caller index (deterministic order)
 //                and gather the records into cell order
 //   k_neighbors  one thread per particle scans the (2S+1)^3 surrounding cells and
 //                writes the radial (r < r_c^R) and angular (r < r_c^A) lists
@@ -14,18 +14,23 @@
 namespace nep {
 
 template <typename real>
-__global__ void __launch_bounds__(kBlock) k_bin(int n, const double* __restrict__ pos, const int* __restrict__ types,
-                                                int T, CellGrid g, int* __restrict__ cell_of,
-                                                PosRec<real>* __restrict__ rec, int* __restrict__ cell_count,
-                                                int* __restrict__ err)
+__global__ void __launch_bounds__(kBlock) k_bin(const WorkItem* __restrict__ items, const ReqInfo* __restrict__ reqs,
+                                                const ModelDesc<real>* __restrict__ models,
+                                                const double* __restrict__ pos, const int* __restrict__ types,
+                                                int* __restrict__ cell_of, PosRec<real>* __restrict__ rec,
+                                                int* __restrict__ cell_count, int* __restrict__ err)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const WorkItem it = items[blockIdx.x];
+    const int i = it.begin + threadIdx.x;
+    if (i >= it.end) return;
+    const ReqInfo& q = reqs[it.req];
+    const CellGrid& g = q.g;
+    const int local = i - q.begin;
     int c3[3];
     real xr[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        double x = pos[(size_t)a * n + i];
+        double x = pos[(size_t)3 * q.begin + (size_t)a * q.n + local];
         if (!isfinite(x)) {
             atomicOr(err, 1);
             x = 0.0;
@@ -40,11 +45,11 @@ __global__ void __launch_bounds__(kBlock) k_bin(int n, const double* __restrict_
         xr[a] = (real)(x - (double)c * g.len[a]);
     }
     int t = types[i];
-    if (t < 0 || t >= T) {
+    if (t < 0 || t >= models[q.model].T) {
         atomicOr(err, 2);
         t = 0;
     }
-    const int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+    const int cell = q.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
     cell_of[i] = cell;
     PosRec<real> r;
     r.x = xr[0];
@@ -135,105 +140,111 @@ __global__ void __launch_bounds__(1024) k_scan_top(int nb, int* __restrict__ blo
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_scatter(int n, const int* __restrict__ cell_of,
+// Counting-sort scatter (thread per particle, arbitrary order within a cell) and the
+// cell start offsets (thread per cell).
+__global__ void __launch_bounds__(kBlock) k_scatter(int n, int ncell, const int* __restrict__ cell_of,
                                                     const int* __restrict__ local, const int* __restrict__ block_off,
-                                                    int* __restrict__ fill, int* __restrict__ perm)
+                                                    int* __restrict__ fill, int* __restrict__ perm_tmp,
+                                                    int* __restrict__ cell_start)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cell_of[i];
-    const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
-    perm[slot] = i;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        const int c = cell_of[t];
+        const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
+        perm_tmp[slot] = t;
+    }
+    if (t < ncell) cell_start[t] = local[t] + block_off[t / kScanItems];
+    if (t == ncell) cell_start[ncell] = n;
 }
 
+// Deterministic order within each cell (by caller index): thread per slot, rank =
+// number of the cell's members with a smaller caller index; gathers the records.
 template <typename real>
-__global__ void __launch_bounds__(kBlock) k_cell_sort(int ncell, int n, const int* __restrict__ count,
-                                                      const int* __restrict__ local,
-                                                      const int* __restrict__ block_off, int* __restrict__ perm,
-                                                      int* __restrict__ cell_start, int* __restrict__ cell_s,
-                                                      const PosRec<real>* __restrict__ rec,
+__global__ void __launch_bounds__(kBlock) k_cell_rank(int n, const int* __restrict__ cell_of,
+                                                      const int* __restrict__ cell_start,
+                                                      const int* __restrict__ perm_tmp, int* __restrict__ perm,
+                                                      int* __restrict__ cell_s, const PosRec<real>* __restrict__ rec,
                                                       PosRec<real>* __restrict__ rec_s)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int b = local[c] + block_off[c / kScanItems];
-    const int e = b + count[c];
-    cell_start[c] = b;
-    if (c == ncell - 1) cell_start[ncell] = e;
-    for (int k = b + 1; k < e; ++k) {  // insertion sort by caller index
-        const int v = perm[k];
-        int q = k - 1;
-        while (q >= b && perm[q] > v) {
-            perm[q + 1] = perm[q];
-            --q;
-        }
-        perm[q + 1] = v;
-    }
-    for (int k = b; k < e; ++k) {
-        rec_s[k] = rec[perm[k]];
-        cell_s[k] = c;
-    }
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int v = perm_tmp[k];
+    const int c = cell_of[v];
+    const int b = cell_start[c], e = cell_start[c + 1];
+    int rank = 0;
+    for (int q = b; q < e; ++q) rank += perm_tmp[q] < v;
+    const int dst = b + rank;
+    perm[dst] = v;
+    cell_s[dst] = c;
+    rec_s[dst] = rec[v];
 }
 
 template <typename real>
-cudaError_t launch_cell_build(int n, const double* pos, const int* types, int T, const CellGrid& g,
-                              int* cell_of, PosRec<real>* rec_user, int* cell_count, int* cell_start_local,
-                              int* block_off, int* cell_fill, int* perm, int* cell_start, int* cell_s,
+cudaError_t launch_cell_build(int n, int n_items, int ncell_total, const WorkItem* items, const ReqInfo* reqs,
+                              const ModelDesc<real>* models, const double* pos, const int* types, int* cell_of,
+                              PosRec<real>* rec_user, int* cell_count, int* cell_start_local, int* block_off,
+                              int* cell_fill, int* perm_tmp, int* perm, int* cell_start, int* cell_s,
                               PosRec<real>* rec_sorted, int* err, cudaStream_t st)
 {
-    const int nb_scan = (g.ncell + kScanItems - 1) / kScanItems;
+    const int nb_scan = (ncell_total + kScanItems - 1) / kScanItems;
     if (nb_scan > kScanItems) return cudaErrorInvalidValue;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * g.ncell, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * g.ncell, st)) != cudaSuccess) return e;
-    const int nbp = (n + kBlock - 1) / kBlock;
-    k_bin<real><<<nbp, kBlock, 0, st>>>(n, pos, types, T, g, cell_of, rec_user, cell_count, err);
-    k_scan_local<<<nb_scan, 1024, 0, st>>>(g.ncell, cell_count, cell_start_local, block_off);
+    if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell_total, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell_total, st)) != cudaSuccess) return e;
+    k_bin<real><<<n_items, kBlock, 0, st>>>(items, reqs, models, pos, types, cell_of, rec_user, cell_count, err);
+    k_scan_local<<<nb_scan, 1024, 0, st>>>(ncell_total, cell_count, cell_start_local, block_off);
     k_scan_top<<<1, 1024, 0, st>>>(nb_scan, block_off);
-    k_scatter<<<nbp, kBlock, 0, st>>>(n, cell_of, cell_start_local, block_off, cell_fill, perm);
-    k_cell_sort<real><<<(g.ncell + kBlock - 1) / kBlock, kBlock, 0, st>>>(
-        g.ncell, n, cell_count, cell_start_local, block_off, perm, cell_start, cell_s, rec_user, rec_sorted);
+    const int nt = (n > ncell_total + 1 ? n : ncell_total + 1);
+    k_scatter<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, ncell_total, cell_of, cell_start_local, block_off,
+                                                              cell_fill, perm_tmp, cell_start);
+    k_cell_rank<real><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, cell_of, cell_start, perm_tmp, perm, cell_s,
+                                                                    rec_user, rec_sorted);
     return cudaGetLastError();
 }
 
 // One thread per sorted particle i: scan the cells at offsets [-S, S]^3 from i's
-// cell and keep every (j, offset) with r^2 < r_c^2(t_i, t_j).
+// cell in its request's grid and keep every (j, offset) with r^2 < r_c^2(t_i, t_j).
 template <typename real>
 __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     real* cut = reinterpret_cast<real*>(smem_raw);  // rcR2[T*T], rcA2[T*T]
-    const int TT = a.T * a.T;
+    const WorkItem it = a.items[blockIdx.x];
+    const ReqInfo& q = a.reqs[it.req];
+    const ModelDesc<real> md = a.models[q.model];
+    const int T = md.T, TT = T * T;
     for (int k = threadIdx.x; k < TT; k += blockDim.x) {
-        cut[k] = a.params[a.off.rcR2 + k];
-        cut[TT + k] = a.params[a.off.rcA2 + k];
+        cut[k] = md.params[md.off.rcR2 + k];
+        cut[TT + k] = md.params[md.off.rcA2 + k];
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = it.begin + threadIdx.x;
     int nr = 0, na = 0;
-    if (i < a.n) {
+    if (i < it.end) {
+        const CellGrid& g = q.g;
         const PosRec<real> ri = a.rec[i];
-        const int c = a.cell_s[i];
-        const int cx = c % a.g.nc[0], cy = (c / a.g.nc[0]) % a.g.nc[1], cz = c / (a.g.nc[0] * a.g.nc[1]);
-        const real* cutR = cut + ri.t * a.T;
-        const real* cutA = cut + TT + ri.t * a.T;
-        const real lx = (real)a.g.len[0], ly = (real)a.g.len[1], lz = (real)a.g.len[2];
-        for (int dz = -a.g.S[2]; dz <= a.g.S[2]; ++dz) {
+        const int c = a.cell_s[i] - q.cell_base;
+        const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+        const real* cutR = cut + ri.t * T;
+        const real* cutA = cut + TT + ri.t * T;
+        const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
+        for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
             int z = cz + dz;
-            if (a.g.pbc[2]) z = ((z % a.g.nc[2]) + a.g.nc[2]) % a.g.nc[2];
-            else if (z < 0 || z >= a.g.nc[2]) continue;
-            for (int dy = -a.g.S[1]; dy <= a.g.S[1]; ++dy) {
+            if (g.pbc[2]) z = ((z % g.nc[2]) + g.nc[2]) % g.nc[2];
+            else if (z < 0 || z >= g.nc[2]) continue;
+            for (int dy = -g.S[1]; dy <= g.S[1]; ++dy) {
                 int y = cy + dy;
-                if (a.g.pbc[1]) y = ((y % a.g.nc[1]) + a.g.nc[1]) % a.g.nc[1];
-                else if (y < 0 || y >= a.g.nc[1]) continue;
-                for (int dx = -a.g.S[0]; dx <= a.g.S[0]; ++dx) {
+                if (g.pbc[1]) y = ((y % g.nc[1]) + g.nc[1]) % g.nc[1];
+                else if (y < 0 || y >= g.nc[1]) continue;
+                for (int dx = -g.S[0]; dx <= g.S[0]; ++dx) {
                     int x = cx + dx;
-                    if (a.g.pbc[0]) x = ((x % a.g.nc[0]) + a.g.nc[0]) % a.g.nc[0];
-                    else if (x < 0 || x >= a.g.nc[0]) continue;
-                    const int cell = (z * a.g.nc[1] + y) * a.g.nc[0] + x;
+                    if (g.pbc[0]) x = ((x % g.nc[0]) + g.nc[0]) % g.nc[0];
+                    else if (x < 0 || x >= g.nc[0]) continue;
+                    const int cell = q.cell_base + (z * g.nc[1] + y) * g.nc[0] + x;
                     const real ox = (real)dx * lx - ri.x, oy = (real)dy * ly - ri.y, oz = (real)dz * lz - ri.z;
                     const bool centre = (dx == 0 && dy == 0 && dz == 0);
                     const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+#pragma unroll 4
                     for (int k = kb; k < ke; ++k) {
                         if (centre && k == i) continue;
                         const PosRec<real> rj = a.rec[k];
@@ -268,18 +279,18 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 }
 
 template <typename real>
-cudaError_t launch_neighbors(const NeighborArgs<real>& a, cudaStream_t st)
+cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st)
 {
-    const size_t smem = 2 * sizeof(real) * a.T * a.T;
-    k_neighbors<real><<<(a.n + kBlock - 1) / kBlock, kBlock, smem, st>>>(a);
+    k_neighbors<real><<<n_items, kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-#define NEP_INSTANTIATE(real)                                                                                     \
-    template cudaError_t launch_cell_build<real>(int, const double*, const int*, int, const CellGrid&, int*,      \
-                                                 PosRec<real>*, int*, int*, int*, int*, int*, int*, int*,         \
+#define NEP_INSTANTIATE(real)                                                                                   \
+    template cudaError_t launch_cell_build<real>(int, int, int, const WorkItem*, const ReqInfo*,                \
+                                                 const ModelDesc<real>*, const double*, const int*, int*,         \
+                                                 PosRec<real>*, int*, int*, int*, int*, int*, int*, int*, int*,   \
                                                  PosRec<real>*, int*, cudaStream_t);                              \
-    template cudaError_t launch_neighbors<real>(const NeighborArgs<real>&, cudaStream_t);
+    template cudaError_t launch_neighbors<real>(const NeighborArgs<real>&, int, size_t, cudaStream_t);
 NEP_INSTANTIATE(float)
 NEP_INSTANTIATE(double)
 #undef NEP_INSTANTIATE

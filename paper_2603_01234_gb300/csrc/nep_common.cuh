@@ -1,4 +1,12 @@
 // Internal definitions shared by the CUDA translation units of the NEP library.
+//
+// Every kernel works on a batch of requests (configurations).  The particles of
+// all requests are concatenated; request r owns [begin, begin + n).  Each request
+// has its own box, cell grid (its cells are numbered from cell_base in one global
+// cell numbering) and model.  Work is cut into work items: up to kBlock particles
+// of one request, one thread block per item, so a block stages one model's tables
+// and contributes to one request's FP64 totals.  A single configuration is a
+// batch of one request.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,7 +21,7 @@ constexpr uint32_t kJMask = (1u << kJBits) - 1u;
 constexpr int kMaxN = (1 << kJBits) - 1;
 constexpr int kMaxS = 2;
 constexpr int kMaxTypes = 16;
-constexpr int kBlock = 128;          // threads per block of the per-bead kernels
+constexpr int kBlock = 128;          // threads per block = particles per work item
 constexpr int kScanItems = 4096;     // cells per block of the scan
 
 __host__ __device__ inline uint32_t pack_entry(int j, int dx, int dy, int dz)
@@ -49,15 +57,37 @@ struct ParamLayout {
     int total;                  // all elements
 };
 
+// One model of a batch (device table).
+template <typename real>
+struct ModelDesc {
+    const real* params;
+    ParamLayout off;
+    int T, H;
+};
+
+// One request of a batch (device table).
+struct ReqInfo {
+    CellGrid g;
+    int cell_base;              // first global cell of this request
+    int begin, n;               // particle range in the concatenated arrays
+    int model;                  // index into the model table
+    int item_begin, item_end;   // work items of this request
+};
+
+// One block of work: particles [begin, end) of request `req` (end - begin <= kBlock).
+struct WorkItem {
+    int req, begin, end;
+};
+
 template <typename real>
 struct NeighborArgs {
-    int n, T, mnR, mnA;
-    CellGrid g;
-    const int* cell_start;      // [ncell + 1]
-    const int* cell_s;          // [n] cell of sorted particle
+    int n, mnR, mnA;
+    const WorkItem* items;
+    const ReqInfo* reqs;
+    const ModelDesc<real>* models;
+    const int* cell_start;      // [ncell_total + 1]
+    const int* cell_s;          // [n] global cell of sorted particle
     const PosRec<real>* rec;    // [n] sorted
-    const real* params;         // model tables (cutoff prefix used)
-    ParamLayout off;
     uint32_t* nlR;              // [mnR][n]
     uint32_t* nlA;              // [mnA][n]
     int* cntR;                  // [n]
@@ -67,41 +97,43 @@ struct NeighborArgs {
 
 template <typename real>
 struct EvalArgs {
-    int n, T, H, mnR, mnA;
-    real len[3];                // cell side, for the packed offsets
+    int n, mnR, mnA;
+    const WorkItem* items;
+    const ReqInfo* reqs;
+    const ModelDesc<real>* models;
     const PosRec<real>* rec;    // [n] sorted
     const uint32_t* nlR;
     const uint32_t* nlA;
     const int* cntR;
     const int* cntA;
-    const real* params;
-    ParamLayout off;
     real* U;                    // [n] sorted site energies
-    real* e;                    // [n][T][KRP] radial gradient folded into the basis
+    real* e;                    // [n][e_stride] radial gradient folded into the basis
+    int e_stride;               // Tmax * KRP
     real* phi;                  // [n][24][NA] dU/dA_nlm
     int tile_offset;            // byte offset of the force kernel's Phi tile in dynamic smem
     const int* perm;            // sorted slot -> caller index
-    double* force;              // [3][n] caller order (required)
-    double* virial;             // [9][n] caller order or null
-    double* site;               // [n] caller order or null
-    double* partial;            // [gridDim][10] per-block (E, W[9])
-    unsigned int* counter;      // last-block counter (self-resetting)
-    double* totals;             // [10]: E, W[9]
+    double* force;              // per request [3][n_r] blocks (required)
+    double* virial;             // per request [9][n_r] blocks, or null
+    double* site;               // [n] or null
+    double* partial;            // [items][10] per-block (E, W[9])
+    unsigned int* counter;      // [requests] last-block counters (self-resetting)
+    double* totals;             // [requests][10]: E, W[9]
 };
 
 // ---- host-side launchers (defined in the .cu files) ----
 template <typename real>
-cudaError_t launch_cell_build(int n, const double* pos, const int* types, int T, const CellGrid& g,
-                              int* cell_of, PosRec<real>* rec_user, int* cell_count, int* cell_start_local,
-                              int* block_off, int* cell_fill, int* perm, int* cell_start, int* cell_s,
+cudaError_t launch_cell_build(int n, int n_items, int ncell_total, const WorkItem* items, const ReqInfo* reqs,
+                              const ModelDesc<real>* models, const double* pos, const int* types, int* cell_of,
+                              PosRec<real>* rec_user, int* cell_count, int* cell_start_local, int* block_off,
+                              int* cell_fill, int* perm_tmp, int* perm, int* cell_start, int* cell_s,
                               PosRec<real>* rec_sorted, int* err, cudaStream_t st);
 
 template <typename real>
-cudaError_t launch_neighbors(const NeighborArgs<real>& a, cudaStream_t st);
+cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st);
 
 // Shape-dispatched evaluation; returns cudaErrorInvalidValue for an uncompiled shape.
 template <typename real>
-cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, size_t smem_desc,
+cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr);
 
 template <typename real>
