@@ -41,25 +41,57 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 
 
 N_BEADS = 100_000
+WORKLOAD = "water100k"
+
+# name -> (description, dt in fs)
+WORKLOADS = {
+    "water100k": ("CG water, 1 type, density 0.0334/A^3, periodic cube", 10.0),
+    "water512": ("CG water, 512 beads (8^3 lattice, 3.1 A), periodic cube 24.8 A", 10.0),
+    "monolayer200k": ("4-type distorted hexagonal monolayer, 250x200 cells, periodic x,y, open z", 20.0),
+    "nanowire1M": ("atom-and-bead nanowire: FCC core r=15 A (type 0) in 2 bead sheaths, periodic x", 5.0),
+}
 
 
-def workload():
-    model = inputs.random_model(n_types=1, n_desc_radial=5, n_desc_angular=4, n_basis_radial=8,
-                                n_basis_angular=8, l_max=4, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
-    system = inputs.water_box(N_BEADS, density=0.0334, seed=1001)
-    system.masses = np.array([18.0])
+def workload(name=None):
+    """(model, system, velocities) of a named workload; seeds fixed."""
+    name = name or WORKLOAD
+    if name == "water100k":
+        model = inputs.random_model(n_types=1, n_desc_radial=5, n_desc_angular=4, n_basis_radial=8,
+                                    n_basis_angular=8, l_max=4, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
+        system = inputs.water_box(N_BEADS, density=0.0334, seed=1001)
+        system.masses = np.array([18.0])
+    elif name == "water512":
+        model = inputs.random_model(n_types=1, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
+        system = inputs.water_small(seed=1000)
+    elif name == "monolayer200k":
+        model = inputs.random_model(n_types=4, hidden=50, rc_radial=15.0, rc_angular=11.0, seed=2)
+        system = inputs.monolayer(250, 200, seed=1002)
+    elif name == "nanowire1M":
+        model = inputs.random_model(n_types=3, hidden=40, rc_radial=7.0, rc_angular=5.0, seed=4)
+        system = inputs.nanowire(1_000_000, seed=1003)
+    else:
+        raise ValueError(name)
     vel = inputs.maxwell_boltzmann(system, 300.0, seed=7)
     return model, system, vel
 
 
-def config_dict(system):
-    return {"workload": f"CG water, {system.n} beads, 1 type, density 0.0334/A^3, periodic cube "
-                        f"{system.box[0]:.1f} A",
-            "model": "NEP4-form random weights N(0,0.1): n_R=5, n_A=4, K_R=K_A=8, l_max=4, H=30, r_c 8/5 A",
-            "n_beads": system.n, "dt_fs": DT_FS, "integrator": "velocity-Verlet NVE (FP64)",
+def config_dict(system, name=None):
+    name = name or WORKLOAD
+    m = workload_model_note(name)
+    return {"workload": f"{WORKLOADS[name][0]}; {system.n} particles; box "
+                        f"{system.box[0]:.1f} x {system.box[1]:.1f} x {system.box[2]:.1f} A",
+            "model": m, "n_beads": system.n, "dt_fs": WORKLOADS[name][1],
+            "integrator": "velocity-Verlet NVE (FP64)",
             "precision": "FP32 descriptors/network/forces, FP64 reductions+integration",
-            "l2": "flushed between timed steps (256 MiB write); working set < L2",
-            "data": "synthetic (seeded jittered lattice, Maxwell-Boltzmann 300 K)"}
+            "l2": "flushed between timed steps (256 MiB write)",
+            "data": "synthetic (seeded lattice, Maxwell-Boltzmann 300 K)"}
+
+
+def workload_model_note(name):
+    return {"water100k": "NEP4-form random weights N(0,0.1): n_R=5, n_A=4, K_R=K_A=8, l_max=4, H=30, r_c 8/5 A",
+            "water512": "as water100k",
+            "monolayer200k": "4 types, H=50, r_c 15/11 A, n_R=5, n_A=4, K=8, l_max=4",
+            "nanowire1M": "3 types, H=40, r_c 7/5 A, n_R=5, n_A=4, K=8, l_max=4"}[name]
 
 
 # ---- algorithmic work per kernel (FMA = 2 flop; sin/cos, rsqrt, tanh, div = 1) ----
@@ -228,6 +260,12 @@ def run_ours(args):
     sp = stream.cuda_stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
+    pos0, vel0_d = pos.clone(), vel.clone()  # every leg starts from this state
+
+    def restore():
+        pos.copy_(pos0)
+        vel.copy_(vel0_d)
+
     def step(k=1, fv=1, sample=0, thermo=None):
         binding.nep_md_step(m.h, types, system.masses, system.box, system.pbc, pos, vel, force, fv, k, DT_FS,
                             sample, thermo, stream=sp)
@@ -273,8 +311,12 @@ def run_ours(args):
     # steady state: the same steps back to back through the graph-captured loop
     steady = None
     if not args.quick:
-        k2 = max(2 * args.steps, 20)
-        step(k=k2)
+        k2 = max(args.steps, 20)
+        restore()
+        step(k=0, fv=0)
+        step(k=k2)  # captures the chunk graph
+        restore()
+        step(k=0, fv=0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -289,6 +331,9 @@ def run_ours(args):
     e2e = None
     if not args.quick:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        restore()
+        step(k=0, fv=0)
+        torch.cuda.synchronize()
         h_types, h_pos = pin(system.types), pin(pos.cpu().numpy())
         h_vel, h_force = pin(vel.cpu().numpy()), pin(force.cpu().numpy())
         thermo = pin(np.zeros((1, 12)))
@@ -309,7 +354,7 @@ def run_ours(args):
     plain = None
     if not args.quick:
         m64 = binding.Model(model, "fp64", device=local)
-        pos64, vel64 = pos.clone(), vel.clone()
+        pos64, vel64 = pos0.clone(), vel0_d.clone()
         f64 = torch.zeros_like(force)
         binding.nep_md_step(m64.h, types, system.masses, system.box, system.pbc, pos64, vel64, f64, 0, 0, DT_FS,
                             0, None, stream=sp)
@@ -333,6 +378,9 @@ def run_ours(args):
         m64.close()
 
     m.close()
+    serve = None
+    if not args.quick and not args.no_serve and rank == 0:
+        serve = serving_leg(local)
     if rank != 0:
         return 0
 
@@ -355,7 +403,9 @@ def run_ours(args):
         cpu = {"value": n * st / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{st} full FP64 velocity-Verlet step of all {n} beads on the host cores"}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    metric = METRIC if WORKLOAD == "water100k" and N_BEADS == 100_000 else \
+        f"bead-steps/s ({WORKLOAD}, {n} particles, MD step)"
+    line = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(system),
@@ -364,8 +414,95 @@ def run_ours(args):
             "stages_ms_per_step": {k: v / max(1, tsteps) for k, v in stages.items()},
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
-            "steady_state_graph": steady, "plain_fp64": plain}
+            "steady_state_graph": steady, "plain_fp64": plain, "serving": serve}
     print(json.dumps(line))
+    return 0
+
+
+def serving_leg(device, n_requests=4096, fractions=(0.25, 0.5, 0.75, 0.9)):
+    """Served stream: n_requests energy/force/virial requests, bead counts
+    log-uniform in [64, 4096], half water-like cubes (model 0), half four-type
+    monolayer patches (model 1); host buffers in and out.  Saturation throughput
+    (all requests queued at t = 0) and p50/p99 latency under Poisson arrivals at
+    fractions of each form's own saturation rate, for the batched server (2 lanes)
+    and for one launch sequence per request."""
+    from paper_2603_01234_gb300 import serving
+
+    m_water = inputs.random_model(n_types=1, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
+    m_mono = inputs.random_model(n_types=4, hidden=50, rc_radial=15.0, rc_angular=11.0, seed=2)
+    stream = inputs.request_stream(n_requests=n_requests, seed=1004)
+    out = {"requests": n_requests, "particles": int(sum(s.n for _, s in stream)),
+           "workload": "log-uniform 64-4096 beads; water cubes (1 type, H=30, r_c 8/5) and 4-type monolayer "
+                       "patches (H=50, r_c 15/11), 50/50; host buffers"}
+    forms = {"batched": dict(lanes=2, lane_bytes=2 << 30, max_requests=4096),
+             "one_launch_per_request": dict(lanes=1, lane_bytes=2 << 30, max_requests=1)}
+    sat = {}
+    for name, kw in forms.items():
+        srv = serving.Server([m_water, m_mono], "fp32", device=device, keep_results=False, **kw)
+        warm = [serving.Request(k, mi, s) for k, (mi, s) in enumerate(stream[:64])]
+        srv.serve(warm, np.zeros(len(warm)))
+        reqs = [serving.Request(k, mi, s) for k, (mi, s) in enumerate(stream)]
+        st = srv.serve(reqs, np.zeros(len(reqs)))
+        sat[name] = st
+        out[name] = {"saturation": {"particles_per_s": st.throughput, "requests_per_s": st.n_requests / st.wall_s,
+                                    "batches": st.batches, "mean_requests_per_batch": st.mean_batch_requests,
+                                    "p50_ms": 1e3 * st.pct(50), "p99_ms": 1e3 * st.pct(99)},
+                     "poisson": []}
+        srv.close()
+    for name, kw in forms.items():
+        srv = serving.Server([m_water, m_mono], "fp32", device=device, keep_results=False, **kw)
+        rate_sat = sat[name].n_requests / sat[name].wall_s  # each form at fractions of its own saturation
+        for f in fractions:
+            rate = f * rate_sat
+            reqs = [serving.Request(k, mi, s) for k, (mi, s) in enumerate(stream)]
+            st = srv.serve(reqs, serving.poisson_arrivals(len(reqs), rate, seed=7))
+            out[name]["poisson"].append({"rate_req_per_s": rate, "fraction_of_own_saturation": f,
+                                         "p50_ms": 1e3 * st.pct(50), "p99_ms": 1e3 * st.pct(99),
+                                         "particles_per_s": st.throughput,
+                                         "mean_requests_per_batch": st.mean_batch_requests})
+        srv.close()
+    return out
+
+
+def run_drift(args, n_steps=1000, every=10):
+    """NVE energy drift of the workload in the FP32 and FP64 forms: n_steps
+    velocity-Verlet steps from 300 K, thermo row every `every` steps; the drift is
+    the slope of a linear fit of E_pot + E_kin against time, per ns and per bead."""
+    import torch
+
+    from paper_2603_01234_gb300 import binding
+    binding.load(build_if_missing=True)
+    dev = torch.device("cuda", 0)
+    model, system, vel0 = workload()
+    out = {"metric": "NVE energy drift", "workload": WORKLOAD, "n": system.n, "dt_fs": DT_FS, "steps": n_steps,
+           "forms": {}}
+    for precision in ("fp32", "fp64"):
+        m = binding.Model(model, precision)
+        types = torch.from_numpy(system.types).to(dev)
+        pos = torch.from_numpy(system.pos.copy()).to(dev)
+        vel = torch.from_numpy(vel0.copy()).to(dev)
+        force = torch.zeros(3, system.n, dtype=torch.float64, device=dev)
+        th = np.zeros((n_steps // every, 12))
+        st = torch.cuda.current_stream(dev).cuda_stream
+        t0 = time.perf_counter()
+        binding.nep_md_step(m.h, types, system.masses, system.box, system.pbc, pos, vel, force, 0, n_steps, DT_FS,
+                            every, th, stream=st)
+        binding.nep_sync(m.h)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        t_ns = th[:, 0] * DT_FS * 1e-6
+        etot = th[:, 1] + th[:, 2]
+        slope, icpt = np.polyfit(t_ns, etot, 1)
+        resid = etot - (slope * t_ns + icpt)
+        temp = 2.0 * th[:, 2] / ((3 * system.n - 3) * inputs.KB_EV)
+        out["forms"][precision] = {
+            "drift_eV_per_ns_per_bead": slope / system.n, "etot_first": etot[0], "etot_last": etot[-1],
+            "etot_fluct_rms_eV_per_bead": float(np.sqrt(np.mean(resid ** 2))) / system.n,
+            "epot_change_eV_per_bead": (th[-1, 1] - th[0, 1]) / system.n,
+            "temperature_first_K": temp[0], "temperature_last_K": temp[-1],
+            "bead_steps_per_s_wall": system.n * n_steps / wall}
+        m.close()
+    print(json.dumps(out))
     return 0
 
 
@@ -377,14 +514,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the steady-state, e2e and FP64 legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--workload", default="water100k", choices=sorted(WORKLOADS),
+                    help="the metric is quoted on water100k; the others are further configurations")
+    ap.add_argument("--drift", action="store_true", help="NVE energy-drift run (1000 steps, FP32 and FP64)")
     ap.add_argument("--n-beads", type=int, default=N_BEADS,
                     help="size of the water box (profiling captures only; the metric is quoted at 100000)")
     args = ap.parse_args()
     globals()["N_BEADS"] = args.n_beads
+    globals()["WORKLOAD"] = args.workload
+    globals()["DT_FS"] = WORKLOADS[args.workload][1]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.drift:
+        return run_drift(args)
     return run_ours(args)
 
 

@@ -687,7 +687,7 @@ int inspect_async(nep_model* m, bool wait)
     }
     m->async_pending = false;
     const int needR = m->h_async[0], needA = m->h_async[1], err = m->h_async[2];
-    bool grow_now = needR * 10 > m->mnR * 9 || needA * 10 > m->mnA * 9;
+    bool grow_now = needR * 5 > m->mnR * 4 || needA * 5 > m->mnA * 4;
     if (err || grow_now) {
         // a later call on this stream runs after the current work; reset the words there
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->async_stream));
@@ -695,8 +695,8 @@ int inspect_async(nep_model* m, bool wait)
     if (err) return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
     if (grow_now) {
         const bool overflow = needR > m->mnR || needA > m->mnA;
-        m->mnR = std::max(m->mnR, ((int)(needR * 1.3) + 8 + 7) & ~7);
-        m->mnA = std::max(m->mnA, ((int)(needA * 1.3) + 8 + 7) & ~7);
+        m->mnR = std::max(m->mnR, ((int)(needR * 1.5) + 8 + 7) & ~7);
+        m->mnA = std::max(m->mnA, ((int)(needA * 1.5) + 8 + 7) & ~7);
         m->n_lists = 0;
         m->graph.reset();
         if (overflow) return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "a neighbour list outgrew its capacity during MD");
@@ -755,8 +755,8 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         NEP_TRY(run_neighbors<real>(m, p));
         if (new_shape) {
             NEP_TRY(check_lists<real>(m, p));
-            const int wantR = ((int)(m->h_flags[0] * 1.3) + 8 + 7) & ~7;
-            const int wantA = ((int)(m->h_flags[1] * 1.3) + 8 + 7) & ~7;
+            const int wantR = ((int)(m->h_flags[0] * 1.5) + 8 + 7) & ~7;
+            const int wantA = ((int)(m->h_flags[1] * 1.5) + 8 + 7) & ~7;
             if (wantR > m->mnR || wantA > m->mnA) {
                 m->mnR = std::max(m->mnR, wantR);
                 m->mnA = std::max(m->mnA, wantA);
@@ -775,10 +775,13 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     if (n_samples > 0) NEP_CUDA(cudaMemsetAsync(m->sample_index.p, 0, sizeof(int), m->cur));
 
     // the steps run in chunks; one chunk is captured once as a CUDA graph (cached
-    // by its arguments) and replayed
+    // by its arguments) and replayed.  After each chunk the status words are
+    // copied to pinned memory and inspected one chunk later (so the GPU never
+    // waits for the host); counts above 80% of capacity grow the lists and the
+    // graph is captured again before the next chunk.
     const int chunk = sample_every > 0 ? sample_every : std::max(1, std::min(n_steps, 50));
     int done = 0;
-    if (n_steps >= chunk && !m->timer.on) {  // stage timing runs the steps eagerly
+    auto capture = [&]() -> int {
         std::vector<unsigned char> key;
         auto put = [&](const void* q, size_t sz) {
             const unsigned char* b = (const unsigned char*)q;
@@ -796,26 +799,63 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&m->mnR, sizeof m->mnR);
         put(&m->mnA, sizeof m->mnA);
         put(inv_m.data(), sizeof(double) * m->T);
-        if (!m->graph.exec || m->graph.key != key) {
-            m->graph.reset();
-            NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
-            int rc = NEP_OK;
-            for (int s = 0; s < chunk && rc == NEP_OK; ++s)
-                rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                            sample_every > 0 && s == chunk - 1, sample_every);
-            cudaGraph_t graph = nullptr;
-            cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
-            if (rc != NEP_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return rc;
-            }
-            if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-            ec = cudaGraphInstantiate(&m->graph.exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
-            m->graph.key = key;
+        if (m->graph.exec && m->graph.key == key) return NEP_OK;
+        m->graph.reset();
+        NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
+        int rc = NEP_OK;
+        for (int s = 0; s < chunk && rc == NEP_OK; ++s)
+            rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
+                                        sample_every > 0 && s == chunk - 1, sample_every);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
+        if (rc != NEP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
         }
-        for (; done + chunk <= n_steps; done += chunk) NEP_CUDA(cudaGraphLaunch(m->graph.exec, m->cur));
+        if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&m->graph.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+        m->graph.key = key;
+        return NEP_OK;
+    };
+    if (n_steps >= chunk && !m->timer.on) {  // stage timing runs the steps eagerly
+        NEP_TRY(capture());
+        const bool check = n_steps >= 2 * chunk;
+        bool pending = false;
+        for (; done + chunk <= n_steps; done += chunk) {
+            NEP_CUDA(cudaGraphLaunch(m->graph.exec, m->cur));
+            if (!check) continue;
+            if (pending) {  // the previous chunk's status
+                NEP_CUDA(cudaEventSynchronize(m->ev_flags));
+                const int needR = m->h_async[0], needA = m->h_async[1];
+                if (m->h_async[2]) {
+                    NEP_CUDA(cudaStreamSynchronize(m->cur));
+                    return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
+                }
+                if (needR > m->mnR || needA > m->mnA) {
+                    NEP_CUDA(cudaStreamSynchronize(m->cur));
+                    NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+                    m->mnR = std::max(m->mnR, ((int)(needR * 1.5) + 8 + 7) & ~7);
+                    m->mnA = std::max(m->mnA, ((int)(needA * 1.5) + 8 + 7) & ~7);
+                    m->n_lists = 0;
+                    m->graph.reset();
+                    return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "a neighbour list outgrew its capacity during MD");
+                }
+                if (needR * 5 > m->mnR * 4 || needA * 5 > m->mnA * 4) {
+                    // grow before the lists overflow: finish the chunk in flight, then
+                    // resize and capture again
+                    NEP_CUDA(cudaStreamSynchronize(m->cur));
+                    m->mnR = std::max(m->mnR, ((int)(needR * 1.5) + 8 + 7) & ~7);
+                    m->mnA = std::max(m->mnA, ((int)(needA * 1.5) + 8 + 7) & ~7);
+                    NEP_TRY(ensure_lists(m, n));
+                    NEP_TRY(capture());
+                }
+            }
+            NEP_CUDA(cudaMemcpyAsync(m->h_async, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
+            NEP_CUDA(cudaEventRecord(m->ev_flags, m->cur));
+            pending = true;
+        }
     }
     for (; done < n_steps; ++done)
         NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
