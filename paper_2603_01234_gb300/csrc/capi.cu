@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/nep.h"
+#include "nep.h"
 #include "nep_common.cuh"
 
 using namespace nep;
@@ -154,7 +154,6 @@ struct Plan {
     int n = 0, ncell = 0, n_models = 0;
     int Tmax = 1;
     size_t smem_desc = 0, smem_force = 0, smem_nbr = 0;
-    size_t tile_offset = 0;             // force kernel's Phi tile: after the largest staged prefix
     std::vector<unsigned char> key;     // identity of the uploaded tables
     Buf dev;                            // [reqs | items | models] on the device
     size_t off_items = 0, off_models = 0;
@@ -171,7 +170,7 @@ struct nep_model {
     ParamLayout off{};
     Buf params;
     size_t real_size = 4;
-    size_t smem_desc = 0, smem_force = 0, tile_offset = 0;
+    size_t smem_desc = 0, smem_force = 0;
     int mnR = 0, mnA = 0;  // neighbour capacities
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
@@ -284,18 +283,15 @@ void set_models(Plan& p, nep_model* const* models, int n_models)
     p.n_models = n_models;
     p.models.resize(sizeof(ModelDesc<real>) * n_models);
     p.Tmax = 1;
-    p.smem_desc = p.smem_force = p.smem_nbr = p.tile_offset = 0;
-    size_t tile_bytes = 0;
+    p.smem_desc = p.smem_force = p.smem_nbr = 0;
     for (int k = 0; k < n_models; ++k) {
         ModelDesc<real> d = model_desc<real>(models[k]);
         memcpy(p.models.data() + k * sizeof d, &d, sizeof d);
         p.Tmax = std::max(p.Tmax, models[k]->T);
         p.smem_desc = std::max(p.smem_desc, models[k]->smem_desc);
-        p.tile_offset = std::max(p.tile_offset, models[k]->tile_offset);
-        tile_bytes = std::max(tile_bytes, models[k]->smem_force - models[k]->tile_offset);
+        p.smem_force = std::max(p.smem_force, models[k]->smem_force);
         p.smem_nbr = std::max(p.smem_nbr, 2 * sizeof(real) * models[k]->T * models[k]->T);
     }
-    p.smem_force = p.tile_offset + tile_bytes;
 }
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -483,7 +479,6 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.e = m->e.as<real>();
     a.e_stride = p.Tmax * m->KRP;
     a.phi = m->phi.as<real>();
-    a.tile_offset = (int)p.tile_offset;
     a.perm = m->perm.as<int>();
     a.force = force;
     a.virial = virial;
@@ -1169,10 +1164,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
     }
     m->smem_desc = m->real_size * o.total;
-    // the force kernel stages the cutoff + coefficient prefix, then (FP32) a
-    // [24][n_A][block] tile of the centre particles' Phi
-    m->tile_offset = (m->real_size * o.n_cut_coef + 15) & ~(size_t)15;
-    m->smem_force = m->tile_offset + (precision == NEP_FP32 ? sizeof(float) * 24 * m->nA * kBlock : 0);
+    // the force kernel stages the cutoff + coefficient prefix only
+    m->smem_force = m->real_size * o.n_cut_coef;
     if (m->smem_desc > 200 * 1024 || m->smem_force > 200 * 1024)
         return cleanup(fail(NEP_ERR_ARG, "model too large for shared-memory staging"));
     // the attribute is per kernel, shared by all handles: allow the largest staging size
@@ -1506,7 +1499,6 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.e = (real*)(base + L.e);
     a.e_stride = m->T * m->KRP;
     a.phi = (real*)(base + L.phi);
-    a.tile_offset = (int)m->tile_offset;
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;

@@ -31,7 +31,7 @@ __host__ __device__ constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : 
 constexpr int kNLM = 24;
 // resident blocks per SM the FP32 kernels are compiled for (caps registers per thread)
 #ifndef NEP_FORCE_MIN_BLOCKS
-#define NEP_FORCE_MIN_BLOCKS 3
+#define NEP_FORCE_MIN_BLOCKS 2
 #endif
 #ifndef NEP_DESC_MIN_BLOCKS
 #define NEP_DESC_MIN_BLOCKS 3
@@ -145,6 +145,31 @@ struct NbrWalk {
     }
 };
 
+// Walk over a column-major neighbour list whose entries are loaded 4 to 8 pairs
+// ahead of use (the list is streamed from L2; a short loop body cannot hide that
+// latency with a shallower prefetch).  body(entry) is called for every entry in order.
+template <typename Body>
+__device__ __forceinline__ void walk4(const uint32_t* nl, size_t stride, int cnt, Body&& body)
+{
+    auto ld = [&](int s) { return s < cnt ? nl[(size_t)s * stride] : 0u; };
+    uint32_t q0 = ld(0), q1 = ld(1), q2 = ld(2), q3 = ld(3);
+    int s = 0;
+    for (; s + 4 <= cnt; s += 4) {
+        const uint32_t a0 = q0, a1 = q1, a2 = q2, a3 = q3;
+        q0 = ld(s + 4);
+        q1 = ld(s + 5);
+        q2 = ld(s + 6);
+        q3 = ld(s + 7);
+        body(a0);
+        body(a1);
+        body(a2);
+        body(a3);
+    }
+    if (s < cnt) body(q0);
+    if (s + 1 < cnt) body(q1);
+    if (s + 2 < cnt) body(q2);
+}
+
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
@@ -185,11 +210,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
 #pragma unroll
         for (int k = 0; k < KR; ++k) fs[k] = real(0);
         const real inv_rc = P[off.rcRi];
-        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
-        for (int s = 0; s < cR; ++s) {
-            uint32_t e;
-            PosRec<real> rj;
-            w.next(s, e, rj);
+        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
+            const PosRec<real> rj = a.rec[e & kJMask];
             real dx, dy, dz;
             pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
@@ -198,7 +220,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
             basis<real, KR>(r, inv_rc, f);
 #pragma unroll
             for (int k = 0; k < KR; ++k) fs[k] += f[k];
-        }
+        });
         const real* c = P + off.cR;
 #pragma unroll
         for (int nn = 0; nn < NR; ++nn) {
@@ -208,11 +230,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
             q[nn] = g;
         }
     } else {
-        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
-        for (int s = 0; s < cR; ++s) {
-            uint32_t e;
-            PosRec<real> rj;
-            w.next(s, e, rj);
+        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
+            const PosRec<real> rj = a.rec[e & kJMask];
             real dx, dy, dz;
             pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
@@ -228,7 +247,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1
                 for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * f[k];
                 q[nn] += g;
             }
-        }
+        });
     }
 
     // ---- angular moments A_nlm (Eq. 5) ----
@@ -378,12 +397,10 @@ template <typename real, int NR, int NA, int KR, int KA>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 1) k_force(EvalArgs<real> a)
 {
     constexpr int KRP = (KR + 3) & ~3;
-    // FP32: i's Phi lives in a shared-memory column [24][NA][kBlock] (conflict-free);
-    // FP64 reads it from global memory (L1).
-    constexpr bool kTile = sizeof(real) == 4;
+    // i's Phi is read through L1 (a shared-memory copy would take L1 capacity that
+    // the neighbours' records and gradients need more)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
-    real* tile = reinterpret_cast<real*>(smem_raw + a.tile_offset);
     const WorkItem it = a.items[blockIdx.x];
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
@@ -408,17 +425,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
         real ei1[KRP];  // the one partner type's vector, when the model has one type
         if (T == 1) loadN<real, KRP>(e_i, ei1);
         const int cR = min(a.cntR[i], a.mnR);
-        NbrWalk<real> w(a.nlR, a.n, i, cR, a.rec);
-        real eji_next[KRP];  // j's radial vector, one pair ahead
-        loadN<real, KRP>(a.e + (size_t)(w.e0 & kJMask) * a.e_stride + ti * KRP, eji_next);
-        for (int s = 0; s < cR; ++s) {
-            uint32_t e;
-            PosRec<real> rj;
-            w.next(s, e, rj);
+        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
+            const int j = (int)(e & kJMask);
+            const PosRec<real> rj = a.rec[j];
             real eji[KRP];
-#pragma unroll
-            for (int k = 0; k < KRP; ++k) eji[k] = eji_next[k];
-            loadN<real, KRP>(a.e + (size_t)(w.e0 & kJMask) * a.e_stride + ti * KRP, eji_next);
+            loadN<real, KRP>(a.e + (size_t)j * a.e_stride + ti * KRP, eji);
             real dx, dy, dz;
             pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
@@ -451,16 +462,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
 #pragma unroll
                 for (int q = 0; q < 3; ++q) W[3 * p + q] -= bd * u[q];
             }
-        }
+        });
 
         // ---- angular pairs ----
         const real* phi_i = a.phi + (size_t)i * kNLM * NA;
-        if (kTile) {  // column of this thread: [k][nn] at ((k * kBlock + thread) * NA + nn)
-#pragma unroll
-            for (int k = 0; k < kNLM; ++k)
-#pragma unroll
-                for (int nn = 0; nn < NA; ++nn) tile[(k * kBlock + threadIdx.x) * NA + nn] = phi_i[k * NA + nn];
-        }
         const int cA = min(a.cntA[i], a.mnA);
         NbrWalk<real> wa(a.nlA, a.n, i, cA, a.rec);
         for (int s = 0; s < cA; ++s) {
@@ -520,11 +525,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 
             for (int k = 0; k < kNLM; ++k) {
                 const real lr = real(l_of(k)) * inv_r;
                 real pi_[NA], pj[NA];
-                if (kTile) {
-                    loadN<real, NA>(tile + (k * kBlock + threadIdx.x) * NA, pi_);
-                } else {
-                    loadN<real, NA>(phi_i + k * NA, pi_);
-                }
+                loadN<real, NA>(phi_i + k * NA, pi_);
                 loadN<real, NA>(phi_j + k * NA, pj);
                 real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
 #pragma unroll

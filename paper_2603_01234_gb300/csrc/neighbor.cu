@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
         const real* cutR = cut + ri.t * T;
         const real* cutA = cut + TT + ri.t * T;
+        const real cR1 = cutR[0], cA1 = cutA[0];  // the one pair type of a one-type model
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
         for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
             int z = cz + dz;
@@ -241,23 +242,31 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
                     if (g.pbc[0]) x = ((x % g.nc[0]) + g.nc[0]) % g.nc[0];
                     else if (x < 0 || x >= g.nc[0]) continue;
                     const int cell = q.cell_base + (z * g.nc[1] + y) * g.nc[0] + x;
-                    const real ox = (real)dx * lx - ri.x, oy = (real)dy * ly - ri.y, oz = (real)dz * lz - ri.z;
-                    const bool centre = (dx == 0 && dy == 0 && dz == 0);
+                    const real ox = (real)dx * lx, oy = (real)dy * ly, oz = (real)dz * lz;
+                    const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
                     const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+                    // the centre cell skips i itself: two ranges instead of a test per candidate
+                    const bool centre = (dx == 0 && dy == 0 && dz == 0);
+                    const int split = centre ? i : ke;
+                    for (int part = 0; part < 2; ++part) {
+                        const int k0 = part == 0 ? kb : split + 1;
+                        const int k1 = part == 0 ? min(split, ke) : ke;
 #pragma unroll 4
-                    for (int k = kb; k < ke; ++k) {
-                        if (centre && k == i) continue;
-                        const PosRec<real> rj = a.rec[k];
-                        const real ddx = rj.x + ox, ddy = rj.y + oy, ddz = rj.z + oz;
-                        const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        const uint32_t ent = pack_entry(k, dx, dy, dz);
-                        if (r2 < cutR[rj.t]) {
-                            if (nr < a.mnR) a.nlR[(size_t)nr * a.n + i] = ent;
-                            ++nr;
-                        }
-                        if (r2 < cutA[rj.t]) {
-                            if (na < a.mnA) a.nlA[(size_t)na * a.n + i] = ent;
-                            ++na;
+                        for (int k = k0; k < k1; ++k) {
+                            const PosRec<real> rj = a.rec[k];
+                            const real ddx = (rj.x + ox) - ri.x, ddy = (rj.y + oy) - ri.y, ddz = (rj.z + oz) - ri.z;
+                            const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            const real cR2 = T == 1 ? cR1 : cutR[rj.t];
+                            const real cA2 = T == 1 ? cA1 : cutA[rj.t];
+                            const uint32_t ent = (uint32_t)k | code;
+                            if (r2 < cR2) {
+                                if (nr < a.mnR) a.nlR[(size_t)nr * a.n + i] = ent;
+                                ++nr;
+                            }
+                            if (r2 < cA2) {
+                                if (na < a.mnA) a.nlA[(size_t)na * a.n + i] = ent;
+                                ++na;
+                            }
                         }
                     }
                 }

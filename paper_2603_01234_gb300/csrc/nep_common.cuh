@@ -110,7 +110,6 @@ struct EvalArgs {
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
     real* phi;                  // [n][24][NA] dU/dA_nlm
-    int tile_offset;            // byte offset of the force kernel's Phi tile in dynamic smem
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null
