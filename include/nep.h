@@ -183,6 +183,25 @@ int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses,
                 const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid,
                 int n_steps, double dt_fs, int sample_every, double* thermo, int mem, void* stream);
 
+/*
+ * n_steps velocity-Verlet steps in the canonical ensemble (the NVT runs of the
+ * paper's benchmark, Sec. III.D): nep_md_step followed, after every step, by
+ * stochastic velocity rescaling (Bussi, Donadio, Parrinello, J. Chem. Phys. 126,
+ * 014101, 2007).  With K the kinetic energy, N_f = 3 n - 3, Kbar = N_f k_B T / 2,
+ * c = exp(-dt / tau) and the step's random numbers R1 ~ N(0, 1) and
+ * S ~ chi^2(N_f - 1):
+ *   K' = c K + (1 - c) (Kbar / N_f) (R1^2 + S) + 2 R1 sqrt(c (1 - c) K Kbar / N_f),
+ * and every velocity is multiplied by sqrt(K' / K) (FP64).
+ *   temperature_K, tau_fs   target temperature and coupling time
+ *   noise                   host [n_steps][2]: (R1, S) of each step; the caller
+ *                           draws them, so runs are reproducible
+ * Every other argument and rule as in nep_md_step.
+ */
+int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                    const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+                    double dt_fs, double temperature_K, double tau_fs, const double* noise, int sample_every,
+                    double* thermo, int mem, void* stream);
+
 /* Wait for the handle's asynchronous MD work and return its deferred status. */
 int nep_sync(nep_model* m);
 

@@ -705,8 +705,13 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
 }
 
 /*
- * Velocity-Verlet NVE (the integrator of the MD step):
+ * Velocity-Verlet (the integrator of the MD step):
  *   v += dt/2 F/m;  r += dt v;  wrap periodic axes;  F = F(r);  v += dt/2 F/m.
+ * With noise != NULL every step ends with stochastic velocity rescaling (Bussi,
+ * Donadio and Parrinello 2007): the kinetic energy K is resampled as
+ *   K' = c K + (1 - c) (Kbar / N_f) (R1^2 + S) + 2 R1 sqrt(c (1 - c) K Kbar / N_f)
+ * with c = exp(-dt / tau), N_f = 3n - 3, Kbar = N_f k_B T / 2 and the step's
+ * noise (R1, S), and all velocities are scaled by sqrt(K' / K).
  * pos, vel, force: SoA [3][n], in/out; force must hold F(pos) on entry.
  * masses: per type (amu).  thermo (optional) [n_steps][2]: potential energy and
  * kinetic energy after each step.
@@ -715,7 +720,8 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
               const double *rcR, const double *rcA, const double *cR, const double *cA,
               const double *w0, const double *b0, const double *w1, const double *b1,
               int n, const int *types, double *pos, double *vel, double *force, const double *masses,
-              const double box[3], const int pbc[3], int use_cells, int n_steps, double dt, double *thermo)
+              const double box[3], const int pbc[3], int use_cells, int n_steps, double dt, double *thermo,
+              double temperature, double tau, const double *noise)
 {
     double *U = (double *)malloc((size_t)n * sizeof(double) + 8);
     double *W = (double *)malloc((size_t)9 * n * sizeof(double) + 8);
@@ -741,6 +747,15 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
                 vel[(size_t)k * n + i] += 0.5 * dt * force[(size_t)k * n + i] * im;
                 ke += 0.5 * mi * vel[(size_t)k * n + i] * vel[(size_t)k * n + i];
             }
+        }
+        if (noise) {
+            double K = ke / ORACLE_ACC;  /* eV */
+            double nf = 3.0 * n - 3.0, c = exp(-dt / tau), kbar = 0.5 * nf * 8.617333262e-5 * temperature;
+            double r1 = noise[2 * step], chi = noise[2 * step + 1];
+            double Kn = c * K + (1.0 - c) * kbar / nf * (r1 * r1 + chi) + 2.0 * r1 * sqrt(c * (1.0 - c) * K * kbar / nf);
+            double alpha = (K > 0.0 && Kn > 0.0) ? sqrt(Kn / K) : (K > 0.0 ? 0.0 : 1.0);
+            for (size_t k = 0; k < (size_t)3 * n; ++k) vel[k] *= alpha;
+            ke *= alpha * alpha;
         }
         if (thermo) {
             thermo[2 * step] = e;

@@ -49,7 +49,7 @@ def lib():
         _lib.oracle_neighbors.restype = C.c_long
         _lib.oracle_compute.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, i, p, i, i, p, p, p, p, p, p]
         _lib.oracle_compute.restype = i
-        _lib.oracle_md.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p]
+        _lib.oracle_md.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p, d, d, p]
         _lib.oracle_md.restype = i
     return _lib
 
@@ -183,8 +183,9 @@ def compute(model, system, sample=None, use_cells=None, want_q=False, q_route=0)
     return OracleResult(e.value if sample is None else np.nan, wt, U, F, W, q)
 
 
-def md(model, system, pos, vel, force, n_steps, dt, use_cells=None):
-    """Velocity-Verlet NVE for n_steps; pos/vel/force are updated copies.
+def md(model, system, pos, vel, force, n_steps, dt, use_cells=None, temperature=0.0, tau=1.0, noise=None):
+    """Velocity-Verlet for n_steps (NVE, or NVT with stochastic velocity rescaling
+    when noise [n_steps][2] is given); pos/vel/force are updated copies.
     Returns (pos, vel, force, thermo[n_steps][2] = (E_pot, E_kin))."""
     L = lib()
     n = system.n
@@ -196,8 +197,10 @@ def md(model, system, pos, vel, force, n_steps, dt, use_cells=None):
     box, pbc = _f64(system.box), _i32(system.pbc)
     masses = _f64(system.masses)
     thermo = np.zeros((n_steps, 2))
+    nz = _f64(noise) if noise is not None else None
     rc = L.oracle_md(*ints, *[_ptr(a) for a in arrs], n, _ptr(types), _ptr(pos), _ptr(vel), _ptr(force),
-                     _ptr(masses), _ptr(box), _ptr(pbc), int(use_cells), int(n_steps), float(dt), _ptr(thermo))
+                     _ptr(masses), _ptr(box), _ptr(pbc), int(use_cells), int(n_steps), float(dt), _ptr(thermo),
+                     float(temperature), float(tau), _ptr(nz))
     if rc != 0:
         raise RuntimeError("oracle_md failed")
     return pos, vel, force, thermo

@@ -33,7 +33,7 @@ NEP_DEVICE = 1
 EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "nep_supported_shape",
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
             "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
-            "nep_compute_static", "nep_compute_batch"]
+            "nep_compute_static", "nep_compute_batch", "nep_md_step_nvt"]
 
 _lib = None
 
@@ -96,6 +96,8 @@ def load(build_if_missing: bool = False):
     lib.nep_compute_static.restype = i
     lib.nep_compute_batch.argtypes = [p, i, i, p, p, p, p, p, p, i, p, p, p, p, p, p]
     lib.nep_compute_batch.restype = i
+    lib.nep_md_step_nvt.argtypes = [p, i, p, p, p, p, p, p, p, i, i, d, d, d, p, i, p, i, p]
+    lib.nep_md_step_nvt.restype = i
     _lib = lib
     return lib
 
@@ -243,6 +245,29 @@ def nep_get_timing(h):
     steps = C.c_longlong()
     _check(load().nep_get_timing(h, _ptr(ms), C.byref(steps)), "nep_get_timing")
     return dict(zip(STAGES, ms.tolist())), steps.value
+
+
+def nep_md_step_nvt(h, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs, temperature_K,
+                    tau_fs, noise, sample_every=0, thermo=None, stream=None):
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    n = int(types.shape[0])
+    masses = _host(masses, np.float64)
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    noise = _host(noise, np.float64)
+    _check(load().nep_md_step_nvt(h, n, _ptr(types), _ptr(masses), _ptr(box), _ptr(pbc), _ptr(pos), _ptr(vel),
+                                  _ptr(force), int(forces_valid), int(n_steps), float(dt_fs), float(temperature_K),
+                                  float(tau_fs), _ptr(noise), int(sample_every), _ptr(thermo), mem,
+                                  _stream_of(pos, stream)), "nep_md_step_nvt")
+
+
+def bussi_noise(n_steps, n_particles, seed):
+    """Random numbers of the thermostat: [n_steps][2] = (R1 ~ N(0,1), chi^2(3n - 4))."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((n_steps, 2))
+    out[:, 0] = rng.standard_normal(n_steps)
+    out[:, 1] = rng.chisquare(3 * n_particles - 4, size=n_steps)
+    return out
 
 
 def nep_sync(h):

@@ -187,6 +187,7 @@ struct nep_model {
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
+    Buf noise_d, bussi;  // thermostat: random numbers of the call; [step, alpha] words
     int* h_flags = nullptr;        // pinned: maxcnt[2], err
     double* h_totals = nullptr;    // pinned [10 * requests]
     size_t h_totals_cap = 0;
@@ -631,11 +632,17 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
     return NEP_OK;
 }
 
+// Stochastic-velocity-rescaling thermostat of an MD call (inactive when noise is null).
+struct Thermostat {
+    const double* noise = nullptr;  // device [n_steps][2]
+    double c = 1.0, kbar = 0.0, n_f = 1.0;
+};
+
 // One MD step's launches (used eagerly and under stream capture).
 template <typename real>
 int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_m_acc, const double* mass,
                      const CellGrid& g, double* pos, double* vel, double* force, double dt, bool sample,
-                     int step_stride)
+                     int step_stride, const Thermostat& th)
 {
     const Plan& p = m->plan;
     cudaEvent_t* ev = nullptr;
@@ -658,6 +665,11 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
     if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
     e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
+    if (th.noise) {
+        e = launch_bussi(n, types_d, mass, m->T, vel, m->partial2.as<double>(), m->counters.as<unsigned int>(),
+                         th.noise, m->bussi.as<int>(), th.c, th.kbar, th.n_f, m->bussi.as<double>() + 1, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("thermostat: ") + cudaGetErrorString(e));
+    }
     if (sample) {
         e = launch_sample(n, types_d, mass, m->T, vel, m->totals.as<double>(), m->partial2.as<double>(),
                           m->counters.as<unsigned int>() + 1, m->thermo.as<double>(), m->sample_index.as<int>(),
@@ -702,7 +714,8 @@ int inspect_async(nep_model* m, bool wait)
 template <typename real>
 int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
             const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
-            double dt, int sample_every, double* thermo, int mem, void* stream)
+            double dt, int sample_every, double* thermo, int mem, void* stream, double temp_K = 0.0,
+            double tau_fs = 0.0, const double* noise = nullptr)
 {
     CellGrid g;
     NEP_TRY(make_grid(m, box, pbc, g));
@@ -764,6 +777,19 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         }
         if (!forces_valid) NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>()));
     }
+    Thermostat th;
+    if (noise) {
+        NEP_TRY(m->noise_d.ensure(sizeof(double) * 2 * std::max(1, n_steps)));
+        NEP_TRY(m->bussi.ensure(sizeof(double) * 2));
+        if (n_steps > 0)
+            NEP_CUDA(cudaMemcpyAsync(m->noise_d.p, noise, sizeof(double) * 2 * n_steps, cudaMemcpyHostToDevice,
+                                     m->cur));
+        NEP_CUDA(cudaMemsetAsync(m->bussi.p, 0, sizeof(int), m->cur));  // step index of the call
+        th.noise = m->noise_d.as<double>();
+        th.c = exp(-dt / tau_fs);
+        th.n_f = 3.0 * n - 3.0;
+        th.kbar = 0.5 * th.n_f * 8.617333262e-5 * temp_K;
+    }
     const int n_samples = sample_every > 0 ? n_steps / sample_every : 0;
     NEP_TRY(m->thermo.ensure(sizeof(double) * 12 * std::max(1, n_samples)));
     NEP_TRY(m->sample_index.ensure(sizeof(int)));
@@ -794,13 +820,16 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&m->mnR, sizeof m->mnR);
         put(&m->mnA, sizeof m->mnA);
         put(inv_m.data(), sizeof(double) * m->T);
+        put(&th, sizeof th);
+        const void* tptr[] = {m->bussi.p};
+        put(tptr, sizeof tptr);
         if (m->graph.exec && m->graph.key == key) return NEP_OK;
         m->graph.reset();
         NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
         int rc = NEP_OK;
         for (int s = 0; s < chunk && rc == NEP_OK; ++s)
             rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                        sample_every > 0 && s == chunk - 1, sample_every);
+                                        sample_every > 0 && s == chunk - 1, sample_every, th);
         cudaGraph_t graph = nullptr;
         cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
         if (rc != NEP_OK) {
@@ -854,7 +883,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     }
     for (; done < n_steps; ++done)
         NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every));
+                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every, th));
     NEP_CUDA(cudaMemcpyAsync(m->h_async, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
     NEP_CUDA(cudaEventRecord(m->ev_flags, m->cur));
     m->async_pending = true;
@@ -1059,7 +1088,7 @@ int nep_destroy(nep_model* m)
                    &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
                    &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
-                   &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev};
+                   &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev, &m->noise_d, &m->bussi};
     for (Buf* b : bufs) b->release();
     if (m->h_flags) cudaFreeHost(m->h_flags);
     if (m->h_totals) cudaFreeHost(m->h_totals);
@@ -1245,6 +1274,24 @@ int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses,
                                  sample_every, thermo, mem, stream)
                : md_impl<float>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
                                 sample_every, thermo, mem, stream);
+}
+
+int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                    const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+                    double dt_fs, double temperature_K, double tau_fs, const double* noise, int sample_every,
+                    double* thermo, int mem, void* stream)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
+    if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return fail(NEP_ERR_ARG, "dt must be positive");
+    if (!(temperature_K >= 0.0) || !(tau_fs > 0.0)) return fail(NEP_ERR_ARG, "need temperature >= 0 and tau > 0");
+    if (!noise && n_steps > 0) return fail(NEP_ERR_ARG, "noise is NULL");
+    if (n < 2) return fail(NEP_ERR_ARG, "the thermostat needs n >= 2");
+    Guard guard(m->device);
+    return m->precision == NEP_FP64
+               ? md_impl<double>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                 sample_every, thermo, mem, stream, temperature_K, tau_fs, noise)
+               : md_impl<float>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                sample_every, thermo, mem, stream, temperature_K, tau_fs, noise);
 }
 
 int nep_sync(nep_model* m)

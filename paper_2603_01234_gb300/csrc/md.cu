@@ -4,6 +4,9 @@
 //   k_kick         v += dt/2 F/m
 //   k_sample       E_kin = sum 1/2 m v^2 (FP64, deterministic last-block total) and
 //                  one thermo row (step, E_pot, E_kin, W[9])
+//   k_bussi_ke     E_kin and the stochastic-velocity-rescaling factor (Bussi,
+//                  Donadio, Parrinello 2007) from the step's two random numbers
+//   k_scale_vel    v *= alpha
 #include "nep_common.cuh"
 
 namespace nep {
@@ -95,6 +98,68 @@ __global__ void __launch_bounds__(kBlock) k_sample(int n, const int* __restrict_
     *counter = 0u;
 }
 
+// Stochastic velocity rescaling: with c = exp(-dt/tau), Kbar = N_f k_B T / 2 and the
+// step's random numbers R1 ~ N(0,1), S ~ chi^2(N_f - 1),
+//   K' = c K + (1 - c) Kbar / N_f (R1^2 + S) + 2 R1 sqrt(c (1 - c) K Kbar / N_f),
+// and velocities are scaled by alpha = sqrt(K' / K).  The last block computes
+// alpha (FP64) into *alpha and advances *step.
+__global__ void __launch_bounds__(kBlock) k_bussi_ke(int n, const int* __restrict__ types, TypeTable mass,
+                                                     const double* __restrict__ vel, double* __restrict__ partial,
+                                                     unsigned int* __restrict__ counter, const double* __restrict__ noise,
+                                                     int* __restrict__ step, double c, double kbar, double n_f,
+                                                     double* __restrict__ alpha)
+{
+    __shared__ double red[kBlock / 32];
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double ke = 0.0;
+    if (i < n) {
+        const double m = mass.v[types[i]];
+        for (int a = 0; a < 3; ++a) {
+            const double v = vel[(size_t)a * n + i];
+            ke += 0.5 * m * v * v;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ke;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += red[w];
+        partial[blockIdx.x] = s;
+        __threadfence();
+        last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const volatile double* p = partial;
+    double K = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) K += p[b];
+    K /= kAcc;  // eV
+    const int k = *step;
+    const double r1 = noise[2 * k], chi = noise[2 * k + 1];
+    double a2 = 1.0;
+    if (K > 0.0) {
+        const double Kn = c * K + (1.0 - c) * kbar / n_f * (r1 * r1 + chi) + 2.0 * r1 * sqrt(c * (1.0 - c) * K * kbar / n_f);
+        a2 = Kn > 0.0 ? Kn / K : 0.0;
+    }
+    *alpha = sqrt(a2);
+    *step = k + 1;
+    *counter = 0u;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scale_vel(int n, double* __restrict__ vel, const double* __restrict__ alpha)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = *alpha;
+    vel[i] *= a;
+    vel[(size_t)n + i] *= a;
+    vel[(size_t)2 * n + i] *= a;
+}
+
 __global__ void k_scale(int n, double* __restrict__ pos, double sx, double sy, double sz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,6 +200,18 @@ cudaError_t launch_sample(int n, const int* types, const double* mass, int T, co
     if (T > kMdMaxTypes) return cudaErrorInvalidValue;
     k_sample<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(mass, T), vel, totals, partial,
                                                            counter, thermo, sample_index, step_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bussi(int n, const int* types, const double* mass, int T, double* vel, double* partial,
+                         unsigned int* counter, const double* noise, int* step, double c, double kbar, double n_f,
+                         double* alpha, cudaStream_t st)
+{
+    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
+    const int nb = (n + kBlock - 1) / kBlock;
+    k_bussi_ke<<<nb, kBlock, 0, st>>>(n, types, make_table(mass, T), vel, partial, counter, noise, step, c, kbar, n_f,
+                                      alpha);
+    k_scale_vel<<<nb, kBlock, 0, st>>>(n, vel, alpha);
     return cudaGetLastError();
 }
 

@@ -149,5 +149,9 @@ cudaError_t launch_sample(int n, const int* types, const double* mass, int T, co
                           const double* totals, double* partial, unsigned int* counter, double* thermo,
                           int* sample_index, int step_stride, cudaStream_t st);
 cudaError_t launch_scale(int n, double* pos, double sx, double sy, double sz, cudaStream_t st);
+// Bussi stochastic velocity rescaling after a step (noise[2*step]: R1, chi^2(N_f - 1)).
+cudaError_t launch_bussi(int n, const int* types, const double* mass, int T, double* vel, double* partial,
+                         unsigned int* counter, const double* noise, int* step, double c, double kbar, double n_f,
+                         double* alpha, cudaStream_t st);
 
 }  // namespace nep

@@ -106,3 +106,35 @@ def test_box_rescale_positions(nep_lib):
     binding.nep_scale_positions(m.h, pos, [1.001, 1.0, 1.0])
     np.testing.assert_allclose(pos[0], s.pos[0] * 1.001)
     m.close()
+
+
+def test_fp64_nvt_trajectory_matches_oracle(nep_lib):
+    model = water_model()
+    s, v = state(n=200, seed=13)
+    steps, dt, T, tau = 20, 2.0, 350.0, 20.0
+    noise = binding.bussi_noise(steps, s.n, seed=14)
+    f0 = oracle.compute(model, s).force
+    p_ref, v_ref, f_ref, th_ref = oracle.md(model, s, s.pos, v, f0, steps, dt, temperature=T, tau=tau, noise=noise)
+    m = binding.Model(model, "fp64")
+    pos, vel, force = s.pos.copy(), v.copy(), np.zeros_like(s.pos)
+    thermo = np.zeros((steps, 12))
+    binding.nep_md_step_nvt(m.h, s.types, s.masses, s.box, s.pbc, pos, vel, force, 0, steps, dt, T, tau, noise, 1,
+                            thermo)
+    np.testing.assert_allclose(pos, p_ref, atol=1e-9)
+    np.testing.assert_allclose(vel, v_ref, atol=1e-11)
+    np.testing.assert_allclose(thermo[:, 2], th_ref[:, 1], rtol=1e-10, atol=1e-12)
+    m.close()
+
+
+def test_fp32_nvt_holds_temperature(nep_lib):
+    model = water_model()
+    s, v = state(n=1000, seed=15, T=100.0)
+    steps, dt, T, tau = 2000, 5.0, 300.0, 100.0
+    noise = binding.bussi_noise(steps, s.n, seed=16)
+    m = binding.Model(model, "fp32")
+    pos, vel, force = s.pos.copy(), v.copy(), np.zeros_like(s.pos)
+    th = np.zeros((steps // 10, 12))
+    binding.nep_md_step_nvt(m.h, s.types, s.masses, s.box, s.pbc, pos, vel, force, 0, steps, dt, T, tau, noise, 10, th)
+    temp = 2.0 * th[:, 2] / ((3 * s.n - 3) * inputs.KB_EV)
+    assert abs(temp[len(temp) // 2:].mean() - T) < 0.03 * T, temp[-5:]
+    m.close()

@@ -273,3 +273,24 @@ def test_md_energy_conservation_second_order():
         spread.append(etot.max() - etot.min())
     assert spread[1] < spread[0] / 3.0
     assert spread[0] < 1e-2
+
+
+# Stochastic velocity rescaling: for an ideal gas (no forces) the resampled kinetic
+# energy follows the canonical Gamma distribution, mean N_f kT/2, variance N_f (kT)^2/2.
+def test_bussi_thermostat_canonical_kinetic_energy():
+    m = small_model(seed=26, rcR=2.0, rcA=1.5)
+    m.w1[:] = 0.0  # U_i = -b1: no forces
+    s = inputs.random_periodic(12, [40.0, 40.0, 40.0], seed=27, min_dist=3.0)
+    s.masses = np.array([18.0])
+    v = inputs.maxwell_boltzmann(s, 50.0, seed=28)
+    steps, T, tau = 30000, 300.0, 50.0
+    rng = np.random.default_rng(29)
+    nf = 3 * s.n - 3
+    noise = np.stack([rng.standard_normal(steps), rng.chisquare(nf - 1, size=steps)], axis=1)
+    f0 = np.zeros_like(s.pos)
+    _, _, f, th = oracle.md(m, s, s.pos, v, f0, steps, 5.0, temperature=T, tau=tau, noise=noise)
+    assert np.abs(f).max() == 0.0
+    K = th[2000:, 1]
+    kT = inputs.KB_EV * T
+    assert K.mean() == pytest.approx(nf * kT / 2, rel=0.05)
+    assert K.var() == pytest.approx(nf * kT * kT / 2, rel=0.2)
