@@ -202,6 +202,33 @@ int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* mas
                     double dt_fs, double temperature_K, double tau_fs, const double* noise, int sample_every,
                     double* thermo, int mem, void* stream);
 
+/*
+ * Coarse-grained mapping of an atomistic configuration onto beads (Sec. II.B-C):
+ *   R_I = sum_{i in I} (m_i / M_I) r_i                 bead position (Eq. 9)
+ *   F_I = sum_{i in I} f_i                             bead force    (Eq. 12)
+ *   W_I = sum_{i in I} W_i                             bead virial   (Eq. 14)
+ * Groups are CSR: bead I owns atoms group_atoms[group_start[I] .. group_start[I+1]).
+ * On periodic axes every atom is taken at its image nearest to the group's first
+ * atom (groups must be smaller than half the box) and R_I is wrapped to [0, L).
+ *   atom_mass[n_aa], atom_pos[3][n_aa]; atom_force[3][n_aa], atom_virial[9][n_aa]
+ *   may be NULL (then the matching bead output is left alone)
+ *   accumulate   0: overwrite bead_force / bead_virial; 1: add to them (the
+ *                constrained time averages of Eq. 12 and Eq. 14 are such sums
+ *                divided by the number of frames)
+ *   bead_pos[3][n_cg], bead_force[3][n_cg], bead_virial[9][n_cg]   outputs or NULL
+ * mem / stream as in nep_compute; the handle supplies device and workspace.
+ */
+int nep_cg_map(nep_model* m, int n_cg, const int32_t* group_start, const int32_t* group_atoms, int n_aa,
+               const double* atom_mass, const double* atom_pos, const double* atom_force,
+               const double* atom_virial, const double box[3], const int32_t pbc[3], int accumulate, int mem,
+               void* stream, double* bead_pos, double* bead_force, double* bead_virial);
+
+/*
+ * Virial correction of a coarse-grained training target (Eq. 17):
+ *   W -> W + (N_AA - N_CG) k_B T I,   virial[9] row-major, eV.  Host function.
+ */
+int nep_virial_correction(double* virial, int n_atoms, int n_beads, double temperature_K);
+
 /* Wait for the handle's asynchronous MD work and return its deferred status. */
 int nep_sync(nep_model* m);
 
@@ -267,6 +294,24 @@ int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
 int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
                        const int32_t pbc[3], void* stream, double* energy_total, double* virial_total,
                        double* site_energy, double* force, double* virial);
+
+/*
+ * Autotuner.  The FP32 descriptor and force kernels are compiled in variants
+ * that keep 2 or 3 thread blocks resident per SM (a register budget per
+ * thread).  nep_autotune evaluates the configuration with every variant pair,
+ * times them with CUDA events and keeps the fastest on the handle; the first
+ * nep_md_step of a new configuration shape (n and cell grid) does the same
+ * unless disabled.  All variants give identical results.  Inputs as in
+ * nep_compute; the chosen variants are returned (may be NULL).
+ */
+int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force);
+
+/* Set the variants (2 or 3) and whether MD calls tune automatically (1/0). */
+int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force);
+
+/* The variants in use. */
+int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force);
 
 /* Current neighbour-list capacities (entries per particle). */
 int nep_get_capacity(nep_model* m, int* radial, int* angular);

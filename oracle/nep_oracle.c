@@ -765,3 +765,46 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
     free(U); free(W);
     return 0;
 }
+
+/*
+ * Coarse-grained mapping (Sec. II.B-C): bead position as the mass-weighted centre
+ * of its atoms (Eq. 9), bead force and virial as sums over its atoms (Eq. 12,
+ * Eq. 14).  Groups in CSR form (start[n_cg + 1], atoms[]).  On periodic axes each
+ * atom is taken at its image nearest to the group's first atom; the centre is
+ * wrapped into [0, L).  force / virial / outputs may be NULL.
+ */
+void oracle_cg_map(int n_cg, const int *start, const int *atoms, int n_aa, const double *mass, const double *pos,
+                   const double *force, const double *virial, const double box[3], const int pbc[3],
+                   double *bpos, double *bforce, double *bvirial)
+{
+    for (int I = 0; I < n_cg; ++I) {
+        int a0 = atoms[start[I]];
+        double msum = 0.0, c[3] = {0, 0, 0};
+        for (int q = start[I]; q < start[I + 1]; ++q) {
+            int i = atoms[q];
+            msum += mass[i];
+            for (int a = 0; a < 3; ++a) {
+                double d = pos[(size_t)a * n_aa + i] - pos[(size_t)a * n_aa + a0];
+                if (pbc[a]) d -= box[a] * round(d / box[a]);
+                c[a] += mass[i] * (pos[(size_t)a * n_aa + a0] + d);
+            }
+        }
+        if (bpos)
+            for (int a = 0; a < 3; ++a) {
+                double x = c[a] / msum;
+                bpos[(size_t)a * n_cg + I] = pbc[a] ? wrap1(x, box[a]) : x;
+            }
+        if (bforce && force)
+            for (int a = 0; a < 3; ++a) {
+                double s = 0.0;
+                for (int q = start[I]; q < start[I + 1]; ++q) s += force[(size_t)a * n_aa + atoms[q]];
+                bforce[(size_t)a * n_cg + I] = s;
+            }
+        if (bvirial && virial)
+            for (int k = 0; k < 9; ++k) {
+                double s = 0.0;
+                for (int q = start[I]; q < start[I + 1]; ++q) s += virial[(size_t)k * n_aa + atoms[q]];
+                bvirial[(size_t)k * n_cg + I] = s;
+            }
+    }
+}

@@ -218,5 +218,24 @@ def wrap(system):
     return pos
 
 
-__all__ = ["fc", "dfc", "fk", "dfk", "chebyshev", "dchebyshev", "gn", "dgn", "legendre", "dlegendre",
+__all__ = ["cg_map", "fc", "dfc", "fk", "dfk", "chebyshev", "dchebyshev", "gn", "dgn", "legendre", "dlegendre",
            "assoc_legendre", "ylm", "neighbors", "compute", "md", "wrap", "OracleResult", "lib"]
+
+
+def cg_map(group_start, group_atoms, mass, pos, box, pbc, force=None, virial=None):
+    """Bead positions [3][n_cg], forces [3][n_cg] (or None), virials [9][n_cg] (or None)
+    of CSR atom groups (Eq. 9, 12, 14)."""
+    L = lib()
+    L.oracle_cg_map.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int] + [C.c_void_p] * 9
+    L.oracle_cg_map.restype = None
+    st, at = _i32(group_start), _i32(group_atoms)
+    n_cg, n_aa = st.size - 1, int(np.asarray(mass).size)
+    m, p = _f64(mass), _f64(pos)
+    f = _f64(force) if force is not None else None
+    w = _f64(virial) if virial is not None else None
+    bp = np.zeros((3, n_cg))
+    bf = np.zeros((3, n_cg)) if f is not None else None
+    bw = np.zeros((9, n_cg)) if w is not None else None
+    L.oracle_cg_map(n_cg, _ptr(st), _ptr(at), n_aa, _ptr(m), _ptr(p), _ptr(f), _ptr(w), _ptr(_f64(box)),
+                    _ptr(_i32(pbc)), _ptr(bp), _ptr(bf), _ptr(bw))
+    return bp, bf, bw

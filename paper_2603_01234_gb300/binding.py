@@ -33,7 +33,8 @@ NEP_DEVICE = 1
 EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "nep_supported_shape",
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
             "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
-            "nep_compute_static", "nep_compute_batch", "nep_md_step_nvt"]
+            "nep_compute_static", "nep_compute_batch", "nep_md_step_nvt", "nep_cg_map",
+            "nep_virial_correction", "nep_autotune", "nep_set_tuning", "nep_get_tuning"]
 
 _lib = None
 
@@ -98,6 +99,16 @@ def load(build_if_missing: bool = False):
     lib.nep_compute_batch.restype = i
     lib.nep_md_step_nvt.argtypes = [p, i, p, p, p, p, p, p, p, i, i, d, d, d, p, i, p, i, p]
     lib.nep_md_step_nvt.restype = i
+    lib.nep_cg_map.argtypes = [p, i, p, p, i, p, p, p, p, p, p, i, i, p, p, p, p]
+    lib.nep_cg_map.restype = i
+    lib.nep_virial_correction.argtypes = [p, i, i, d]
+    lib.nep_virial_correction.restype = i
+    lib.nep_autotune.argtypes = [p, i, p, p, p, p, i, p, C.POINTER(i), C.POINTER(i)]
+    lib.nep_autotune.restype = i
+    lib.nep_set_tuning.argtypes = [p, i, i, i]
+    lib.nep_set_tuning.restype = i
+    lib.nep_get_tuning.argtypes = [p, C.POINTER(i), C.POINTER(i)]
+    lib.nep_get_tuning.restype = i
     _lib = lib
     return lib
 
@@ -268,6 +279,61 @@ def bussi_noise(n_steps, n_particles, seed):
     out[:, 0] = rng.standard_normal(n_steps)
     out[:, 1] = rng.chisquare(3 * n_particles - 4, size=n_steps)
     return out
+
+
+def nep_cg_map(h, group_start, group_atoms, atom_mass, atom_pos, box, pbc, atom_force=None, atom_virial=None,
+               accumulate=False, bead_pos=None, bead_force=None, bead_virial=None, stream=None):
+    """Bead positions / forces / virials of CSR atom groups (Eq. 9, 12, 14).  Host
+    numpy arrays or device torch tensors; returns the outputs it was given or made."""
+    dev = _is_torch(atom_pos) and atom_pos.is_cuda
+    mem = NEP_DEVICE if dev else NEP_HOST
+    n_cg = int(group_start.shape[0]) - 1
+    n_aa = int(atom_mass.shape[0])
+    if not dev:
+        group_start, group_atoms = _host(group_start, np.int32), _host(group_atoms, np.int32)
+        atom_mass, atom_pos = _host(atom_mass, np.float64), _host(atom_pos, np.float64)
+        atom_force = None if atom_force is None else _host(atom_force, np.float64)
+        atom_virial = None if atom_virial is None else _host(atom_virial, np.float64)
+        if bead_pos is None:
+            bead_pos = np.zeros((3, n_cg))
+        if bead_force is None and atom_force is not None:
+            bead_force = np.zeros((3, n_cg))
+        if bead_virial is None and atom_virial is not None:
+            bead_virial = np.zeros((9, n_cg))
+    _check(load().nep_cg_map(h, n_cg, _ptr(group_start), _ptr(group_atoms), n_aa, _ptr(atom_mass), _ptr(atom_pos),
+                             _ptr(atom_force), _ptr(atom_virial), _ptr(_host(box, np.float64)),
+                             _ptr(_host(pbc, np.int32)), int(accumulate), mem, _stream_of(atom_pos, stream),
+                             _ptr(bead_pos), _ptr(bead_force), _ptr(bead_virial)), "nep_cg_map")
+    return bead_pos, bead_force, bead_virial
+
+
+def nep_virial_correction(virial, n_atoms, n_beads, temperature_K):
+    v = _host(virial, np.float64).copy()
+    _check(load().nep_virial_correction(_ptr(v), int(n_atoms), int(n_beads), float(temperature_K)),
+           "nep_virial_correction")
+    return v
+
+
+def nep_autotune(h, types, pos, box, pbc, stream=None):
+    """Tune the kernel variants on this configuration; returns (mb_desc, mb_force)."""
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    if mem == NEP_HOST:
+        types, pos = _host(types, np.int32), _host(pos, np.float64)
+    a, b = C.c_int(), C.c_int()
+    _check(load().nep_autotune(h, int(types.shape[0]), _ptr(types), _ptr(pos), _ptr(_host(box, np.float64)),
+                               _ptr(_host(pbc, np.int32)), mem, _stream_of(pos, stream), C.byref(a), C.byref(b)),
+           "nep_autotune")
+    return a.value, b.value
+
+
+def nep_set_tuning(h, autotune, mb_desc, mb_force):
+    _check(load().nep_set_tuning(h, int(autotune), int(mb_desc), int(mb_force)), "nep_set_tuning")
+
+
+def nep_get_tuning(h):
+    a, b = C.c_int(), C.c_int()
+    _check(load().nep_get_tuning(h, C.byref(a), C.byref(b)), "nep_get_tuning")
+    return a.value, b.value
 
 
 def nep_sync(h):

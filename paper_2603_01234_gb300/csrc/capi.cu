@@ -172,6 +172,8 @@ struct nep_model {
     size_t real_size = 4;
     size_t smem_desc = 0, smem_force = 0;
     int mnR = 0, mnA = 0;  // neighbour capacities
+    int mb_desc = 3, mb_force = 2;  // register-cap variants of the FP32 evaluation kernels
+    bool autotune = true;           // tune the variants on the first MD call of a configuration shape
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_flags = nullptr, ev_plan = nullptr;
@@ -488,7 +490,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.counter = m->counters.as<unsigned int>() + 2;
     a.totals = totals;
     cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, (int)p.items.size(), p.smem_desc,
-                                          p.smem_force, m->cur, mid);
+                                          p.smem_force, m->cur, mid, m->mb_desc, m->mb_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
@@ -632,6 +634,45 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
     return NEP_OK;
 }
 
+// Autotuner: time every register-cap variant pair of the evaluation kernels on the
+// plan's configuration (lists already built) and keep the fastest.  The variants
+// compute the same arithmetic, so the choice does not change results.
+template <typename real>
+int autotune_plan(nep_model* m, const Plan& p, double* force_d)
+{
+    if (m->precision != NEP_FP32) return NEP_OK;  // one FP64 variant only
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NEP_CUDA(cudaEventCreate(&e0));
+    NEP_CUDA(cudaEventCreate(&e1));
+    const int cand[4][2] = {{3, 2}, {2, 2}, {3, 3}, {2, 3}};
+    float best = 1e30f;
+    int bd = m->mb_desc, bf = m->mb_force;
+    int rc = NEP_OK;
+    for (int c = 0; c < 4 && rc == NEP_OK; ++c) {
+        m->mb_desc = cand[c][0];
+        m->mb_force = cand[c][1];
+        rc = run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>());  // warm-up
+        if (rc != NEP_OK) break;
+        cudaEventRecord(e0, m->cur);
+        for (int r = 0; r < 3 && rc == NEP_OK; ++r)
+            rc = run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>());
+        cudaEventRecord(e1, m->cur);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bd = cand[c][0];
+            bf = cand[c][1];
+        }
+    }
+    m->mb_desc = bd;
+    m->mb_force = bf;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 // Stochastic-velocity-rescaling thermostat of an MD call (inactive when noise is null).
 struct Thermostat {
     const double* noise = nullptr;  // device [n_steps][2]
@@ -773,6 +814,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
             }
             m->md_n = n;
             m->md_grid = g;
+            if (m->autotune) NEP_TRY(autotune_plan<real>(m, p, m->force_tmp.as<double>()));
             NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
         }
         if (!forces_valid) NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>()));
@@ -821,6 +863,8 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&m->mnA, sizeof m->mnA);
         put(inv_m.data(), sizeof(double) * m->T);
         put(&th, sizeof th);
+        put(&m->mb_desc, sizeof m->mb_desc);
+        put(&m->mb_force, sizeof m->mb_force);
         const void* tptr[] = {m->bussi.p};
         put(tptr, sizeof tptr);
         if (m->graph.exec && m->graph.key == key) return NEP_OK;
@@ -1294,6 +1338,141 @@ int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* mas
                                 sample_every, thermo, mem, stream, temperature_K, tau_fs, noise);
 }
 
+int nep_cg_map(nep_model* m, int n_cg, const int32_t* group_start, const int32_t* group_atoms, int n_aa,
+               const double* atom_mass, const double* atom_pos, const double* atom_force, const double* atom_virial,
+               const double box[3], const int32_t pbc[3], int accumulate, int mem, void* stream, double* bead_pos,
+               double* bead_force, double* bead_virial)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if (n_cg < 1 || n_aa < 1 || !group_start || !group_atoms || !atom_mass || !atom_pos || !box || !pbc)
+        return fail(NEP_ERR_ARG, "bad mapping arguments");
+    if (mem != NEP_HOST && mem != NEP_DEVICE) return fail(NEP_ERR_ARG, "mem must be NEP_HOST or NEP_DEVICE");
+    CellGrid g{};
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0)) return fail(NEP_ERR_ARG, "box lengths must be positive");
+        g.box[a] = box[a];
+        g.pbc[a] = pbc[a] ? 1 : 0;
+    }
+    Guard guard(m->device);
+    NEP_TRY(inspect_async(m, true));
+    NEP_TRY(enter(m, stream));
+    if (mem == NEP_DEVICE) {
+        cudaError_t e = launch_cg_map(n_cg, n_aa, group_start, group_atoms, atom_mass, atom_pos, atom_force,
+                                      atom_virial, g, accumulate, bead_pos, bead_force, bead_virial, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cg map: ") + cudaGetErrorString(e));
+        return leave(m, stream);
+    }
+    // host memory: stage through one device buffer
+    const int n_members = group_start[n_cg];
+    if (n_members < 0 || n_members > n_aa) return fail(NEP_ERR_ARG, "group_start[n_cg] out of range");
+    const size_t b_int = sizeof(int) * ((size_t)n_cg + 1 + n_members);
+    const size_t b_aa = sizeof(double) * (size_t)n_aa * (1 + 3 + (atom_force ? 3 : 0) + (atom_virial ? 9 : 0));
+    const size_t b_cg = sizeof(double) * (size_t)n_cg * (3 + 3 + 9);
+    NEP_TRY(m->force_tmp.ensure(b_int + b_aa + b_cg + 64));
+    unsigned char* base = (unsigned char*)m->force_tmp.p;
+    int* d_start = (int*)base;
+    int* d_atoms = d_start + n_cg + 1;
+    double* d = (double*)(base + ((b_int + 7) & ~(size_t)7));
+    double* d_mass = d;
+    double* d_pos = d_mass + n_aa;
+    double* d_force = atom_force ? d_pos + 3 * (size_t)n_aa : nullptr;
+    double* d_vir = atom_virial ? (d_force ? d_force : d_pos) + 3 * (size_t)n_aa : nullptr;
+    double* d_out = (d_vir ? d_vir + 9 * (size_t)n_aa : (d_force ? d_force + 3 * (size_t)n_aa : d_pos + 3 * (size_t)n_aa));
+    double* o_pos = d_out;
+    double* o_force = o_pos + 3 * (size_t)n_cg;
+    double* o_vir = o_force + 3 * (size_t)n_cg;
+    NEP_CUDA(cudaMemcpyAsync(d_start, group_start, sizeof(int) * (n_cg + 1), cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(d_atoms, group_atoms, sizeof(int) * n_members, cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(d_mass, atom_mass, sizeof(double) * n_aa, cudaMemcpyHostToDevice, m->cur));
+    NEP_CUDA(cudaMemcpyAsync(d_pos, atom_pos, sizeof(double) * 3 * n_aa, cudaMemcpyHostToDevice, m->cur));
+    if (d_force) NEP_CUDA(cudaMemcpyAsync(d_force, atom_force, sizeof(double) * 3 * n_aa, cudaMemcpyHostToDevice, m->cur));
+    if (d_vir) NEP_CUDA(cudaMemcpyAsync(d_vir, atom_virial, sizeof(double) * 9 * n_aa, cudaMemcpyHostToDevice, m->cur));
+    if (accumulate) {
+        if (bead_force) NEP_CUDA(cudaMemcpyAsync(o_force, bead_force, sizeof(double) * 3 * n_cg, cudaMemcpyHostToDevice, m->cur));
+        if (bead_virial) NEP_CUDA(cudaMemcpyAsync(o_vir, bead_virial, sizeof(double) * 9 * n_cg, cudaMemcpyHostToDevice, m->cur));
+    }
+    cudaError_t e = launch_cg_map(n_cg, n_aa, d_start, d_atoms, d_mass, d_pos, d_force, d_vir, g, accumulate,
+                                  bead_pos ? o_pos : nullptr, bead_force ? o_force : nullptr,
+                                  bead_virial ? o_vir : nullptr, m->cur);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cg map: ") + cudaGetErrorString(e));
+    if (bead_pos) NEP_CUDA(cudaMemcpyAsync(bead_pos, o_pos, sizeof(double) * 3 * n_cg, cudaMemcpyDeviceToHost, m->cur));
+    if (bead_force && d_force)
+        NEP_CUDA(cudaMemcpyAsync(bead_force, o_force, sizeof(double) * 3 * n_cg, cudaMemcpyDeviceToHost, m->cur));
+    if (bead_virial && d_vir)
+        NEP_CUDA(cudaMemcpyAsync(bead_virial, o_vir, sizeof(double) * 9 * n_cg, cudaMemcpyDeviceToHost, m->cur));
+    return leave(m, stream);
+}
+
+int nep_virial_correction(double* virial, int n_atoms, int n_beads, double temperature_K)
+{
+    if (!virial || n_atoms < 0 || n_beads < 0 || !(temperature_K >= 0.0)) return fail(NEP_ERR_ARG, "bad argument");
+    const double add = (double)(n_atoms - n_beads) * 8.617333262e-5 * temperature_K;
+    virial[0] += add;
+    virial[4] += add;
+    virial[8] += add;
+    return NEP_OK;
+}
+
+int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
+                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
+    Guard guard(m->device);
+    NEP_TRY(inspect_async(m, true));
+    CellGrid g;
+    NEP_TRY(make_grid(m, box, pbc, g));
+    NEP_TRY(enter(m, stream));
+    initial_capacity(m, n, box);
+    const int* types_d = types;
+    const double* pos_d = pos;
+    if (mem == NEP_HOST) {
+        NEP_TRY(m->types_d.ensure(sizeof(int) * n));
+        NEP_TRY(m->pos_d.ensure(sizeof(double) * 3 * (size_t)n));
+        NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
+        NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
+        types_d = m->types_d.as<int>();
+        pos_d = m->pos_d.as<double>();
+    }
+    int rc;
+    if (m->precision == NEP_FP64) {
+        rc = single_plan<double>(m, n, g);
+        if (rc == NEP_OK) rc = ensure_plan_workspace(m, m->plan);
+        if (rc == NEP_OK) rc = evaluate_plan<double>(m, m->plan, types_d, pos_d, m->force_tmp.as<double>(), nullptr,
+                                                     nullptr, m->totals.as<double>());
+    } else {
+        rc = single_plan<float>(m, n, g);
+        if (rc == NEP_OK) rc = ensure_plan_workspace(m, m->plan);
+        if (rc == NEP_OK) rc = evaluate_plan<float>(m, m->plan, types_d, pos_d, m->force_tmp.as<double>(), nullptr,
+                                                    nullptr, m->totals.as<double>());
+        if (rc == NEP_OK) rc = autotune_plan<float>(m, m->plan, m->force_tmp.as<double>());
+    }
+    NEP_TRY(rc);
+    NEP_TRY(leave(m, stream));
+    if (mb_desc) *mb_desc = m->mb_desc;
+    if (mb_force) *mb_force = m->mb_force;
+    return NEP_OK;
+}
+
+int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if ((mb_desc != 2 && mb_desc != 3) || (mb_force != 2 && mb_force != 3))
+        return fail(NEP_ERR_ARG, "variants are 2 or 3 resident blocks per SM");
+    m->autotune = autotune != 0;
+    m->mb_desc = mb_desc;
+    m->mb_force = mb_force;
+    m->graph.reset();
+    return NEP_OK;
+}
+
+int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force)
+{
+    if (!m) return fail(NEP_ERR_ARG, "null model");
+    if (mb_desc) *mb_desc = m->mb_desc;
+    if (mb_force) *mb_force = m->mb_force;
+    return NEP_OK;
+}
+
 int nep_sync(nep_model* m)
 {
     if (!m) return fail(NEP_ERR_ARG, "null model");
@@ -1553,7 +1732,8 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
     a.totals = totals;
-    e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur);
+    e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur, nullptr,
+                              m->mb_desc, m->mb_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     if (energy_total) NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
     if (virial_total)

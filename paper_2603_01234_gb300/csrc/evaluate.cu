@@ -29,15 +29,8 @@ namespace nep {
 
 __host__ __device__ constexpr int l_of(int k) { return k < 3 ? 1 : (k < 8 ? 2 : (k < 15 ? 3 : 4)); }
 constexpr int kNLM = 24;
-// resident blocks per SM the FP32 kernels are compiled for (caps registers per thread)
-#ifndef NEP_FORCE_MIN_BLOCKS
-#define NEP_FORCE_MIN_BLOCKS 2
-#endif
-#ifndef NEP_DESC_MIN_BLOCKS
-#define NEP_DESC_MIN_BLOCKS 3
-#endif
-constexpr int kForceMinBlocks = NEP_FORCE_MIN_BLOCKS;
-constexpr int kDescMinBlocks = NEP_DESC_MIN_BLOCKS;
+// The FP32 kernels are compiled for 2 and for 3 resident blocks per SM (which caps
+// registers per thread); the runtime picks one per handle (autotuned).
 
 // sin(pi x), cos(pi x) for x = r / r_c in [0, 1].  FP32 uses the hardware
 // approximations (absolute error below 4e-7 on [0, pi]); FP64 the accurate routine.
@@ -180,8 +173,8 @@ __device__ __forceinline__ void stage_params(const real* __restrict__ src, real*
     __syncthreads();
 }
 
-template <typename real, int NR, int NA, int KR, int KA>
-__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kDescMinBlocks : 1) k_descriptor(EvalArgs<real> a)
+template <typename real, int NR, int NA, int KR, int KA, int MB>
+__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descriptor(EvalArgs<real> a)
 {
     constexpr int ND = NR + NA * 4;
     constexpr int KRP = (KR + 3) & ~3;
@@ -393,8 +386,8 @@ __device__ __forceinline__ void loadN(const real* p, real* o)
     for (int k = N & ~3; k < N; ++k) o[k] = p[k];
 }
 
-template <typename real, int NR, int NA, int KR, int KA>
-__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? kForceMinBlocks : 1) k_force(EvalArgs<real> a)
+template <typename real, int NR, int NA, int KR, int KA, int MB>
+__global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(EvalArgs<real> a)
 {
     constexpr int KRP = (KR + 3) & ~3;
     // i's Phi is read through L1 (a shared-memory copy would take L1 capacity that
@@ -600,30 +593,40 @@ bool evaluate_shape_supported(int nR, int nA, int KR, int KA)
 template <typename real>
 cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, size_t smem_force)
 {
-#define NEP_CASE(a_, b_, c_, d_)                                                                              \
-    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                       \
-        cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_>,                              \
+#define NEP_SET(a_, b_, c_, d_, mb_)                                                                          \
+    {                                                                                                         \
+        cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_>,                         \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
         if (e != cudaSuccess) return e;                                                                       \
-        return cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    (int)smem_force);                                                         \
+        e = cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_, mb_>,                                          \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);               \
+        if (e != cudaSuccess) return e;                                                                       \
+    }
+#define NEP_CASE(a_, b_, c_, d_)                                  \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {           \
+        NEP_SET(a_, b_, c_, d_, 2)                                \
+        NEP_SET(a_, b_, c_, d_, 3)                                \
+        return cudaSuccess;                                       \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE
+#undef NEP_SET
     return cudaErrorInvalidValue;
 }
 
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
-                            size_t smem_force, cudaStream_t st, cudaEvent_t mid)
+                            size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force)
 {
     const int nb = n_items;
-#define NEP_CASE(a_, b_, c_, d_)                                                          \
-    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                   \
-        k_descriptor<real, a_, b_, c_, d_><<<nb, kBlock, smem_desc, st>>>(a);             \
-        if (mid) cudaEventRecord(mid, st);                                                \
-        k_force<real, a_, b_, c_, d_><<<nb, kBlock, smem_force, st>>>(a);                 \
-        return cudaGetLastError();                                                        \
+#define NEP_CASE(a_, b_, c_, d_)                                                                            \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                     \
+        if (mb_desc == 2) k_descriptor<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_desc, st>>>(a);          \
+        else k_descriptor<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_desc, st>>>(a);                       \
+        if (mid) cudaEventRecord(mid, st);                                                                  \
+        if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);             \
+        else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                           \
+        return cudaGetLastError();                                                                          \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE
@@ -634,7 +637,7 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
     template bool evaluate_shape_supported<real>(int, int, int, int);                                     \
     template cudaError_t evaluate_set_smem<real>(int, int, int, int, size_t, size_t);                     \
     template cudaError_t launch_evaluate<real>(int, int, int, int, const EvalArgs<real>&, int, size_t, size_t, \
-                                               cudaStream_t, cudaEvent_t);
+                                               cudaStream_t, cudaEvent_t, int, int);
 NEP_INSTANTIATE(float)
 NEP_INSTANTIATE(double)
 #undef NEP_INSTANTIATE

@@ -131,9 +131,11 @@ template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st);
 
 // Shape-dispatched evaluation; returns cudaErrorInvalidValue for an uncompiled shape.
+// mb_desc / mb_force: resident blocks per SM of the FP32 kernel variants (2 or 3).
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
-                            size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr);
+                            size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr, int mb_desc = 3,
+                            int mb_force = 2);
 
 template <typename real>
 bool evaluate_shape_supported(int nR, int nA, int KR, int KA);
@@ -153,5 +155,10 @@ cudaError_t launch_scale(int n, double* pos, double sx, double sy, double sz, cu
 cudaError_t launch_bussi(int n, const int* types, const double* mass, int T, double* vel, double* partial,
                          unsigned int* counter, const double* noise, int* step, double c, double kbar, double n_f,
                          double* alpha, cudaStream_t st);
+
+// Coarse-grained mapping: bead positions (Eq. 9), summed forces (Eq. 12) and virials (Eq. 14).
+cudaError_t launch_cg_map(int n_cg, int n_aa, const int* start, const int* atoms, const double* mass,
+                          const double* pos, const double* force, const double* virial, const CellGrid& g,
+                          int accumulate, double* bpos, double* bforce, double* bvirial, cudaStream_t st);
 
 }  // namespace nep

@@ -1,6 +1,8 @@
 """The C-ABI library builds, loads and exports every function include/nep.h declares;
 host-side argument checks work without a GPU."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -51,3 +53,12 @@ def test_create_rejects_bad_arguments_without_device():
     with pytest.raises(binding.NepError) as e:
         binding.nep_create(m)
     assert e.value.code == binding.NEP_ERR_UNSUPPORTED
+
+
+def test_virial_correction_closed_form():
+    """Eq. 17: W -> W + (N_AA - N_CG) k_B T I (host function, no device)."""
+    binding.load(build_if_missing=True)
+    w = np.arange(9, dtype=np.float64)
+    out = binding.nep_virial_correction(w, 1536, 512, 300.0)
+    add = (1536 - 512) * 8.617333262e-5 * 300.0
+    np.testing.assert_allclose(out, w + add * np.eye(3).reshape(9))

@@ -125,3 +125,24 @@ def test_error_paths(nep_lib):
     # the handle stays usable after errors
     assert_parity(m.compute(system), oracle.compute(model, system), "fp32")
     m.close()
+
+
+def test_kernel_variants_identical_and_autotune(nep_lib):
+    """Every register-cap variant computes the same numbers; the autotuner picks one."""
+    model, system = water_model(), inputs.water_box(3000, seed=17)
+    m = binding.Model(model, "fp32")
+    ref = None
+    for md_ in (2, 3):
+        for mf in (2, 3):
+            binding.nep_set_tuning(m.h, 0, md_, mf)
+            got = m.compute(system)
+            if ref is None:
+                ref = got
+            else:
+                np.testing.assert_array_equal(got["force"], ref["force"])
+                np.testing.assert_array_equal(got["virial"], ref["virial"])
+                assert got["energy"] == ref["energy"]
+    md_, mf = binding.nep_autotune(m.h, system.types, system.pos, system.box, system.pbc)
+    assert md_ in (2, 3) and mf in (2, 3)
+    assert binding.nep_get_tuning(m.h) == (md_, mf)
+    m.close()
