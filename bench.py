@@ -39,6 +39,11 @@ UNIT = "bead-steps/s"
 DT_FS = 10.0
 FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock"
 
+# DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
+# profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
+FORCE_TRAFFIC = {"evaluate_cu_sha1": "666ec4633bd239c1aa468d03becb512d6c6c6ba9", "bytes_per_particle": 889.8,
+                 "capture": "profiles/force_descriptor_water200k_ncu.md"}
+
 
 N_BEADS = 100_000
 WORKLOAD = "water100k"
@@ -391,8 +396,14 @@ def run_ours(args):
     achieved = work[dom] / (dom_ms / 1000.0) / 1e12
     sm_max = (clk.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
     peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    traffic = None
+    if dom == "force_virial":
+        import hashlib
+        src = os.path.join(ROOT, "paper_2603_01234_gb300", "csrc", "evaluate.cu")
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() == FORCE_TRAFFIC["evaluate_cu_sha1"]:
+            traffic = FORCE_TRAFFIC["bytes_per_particle"] * n
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": dom, "flop_per_launch": work[dom], "ms_per_launch": dom_ms,
+            "traffic": traffic, "traffic_source": FORCE_TRAFFIC["capture"], "kernel": dom, "flop_per_launch": work[dom], "ms_per_launch": dom_ms,
             "peak_note": FLOPS_PEAK_NOTE + f" ({sm_max:.0f} MHz max clock)"}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (152 * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
