@@ -1457,7 +1457,7 @@ int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force)
 {
     if (!m) return fail(NEP_ERR_ARG, "null model");
     if ((mb_desc != 2 && mb_desc != 3) || (mb_force != 2 && mb_force != 3))
-        return fail(NEP_ERR_ARG, "variants are 2 or 3 resident blocks per SM");
+        return fail(NEP_ERR_ARG, "kernel variants are 2 or 3");
     m->autotune = autotune != 0;
     m->mb_desc = mb_desc;
     m->mb_force = mb_force;

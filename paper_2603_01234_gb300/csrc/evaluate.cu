@@ -331,10 +331,11 @@ __device__ __forceinline__ real warp_sum(real v)
 
 // FP64 block partials of (E, W[9]); the last block of a request sums its request's
 // partials in item order (deterministic) into totals[req].
+template <int BS>
 __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& it, const ReqInfo& rq,
                                               double* partial, unsigned int* counter, double* totals)
 {
-    __shared__ double red[kBlock / 32][10];
+    __shared__ double red[BS / 32][10];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -346,7 +347,7 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& i
     if (threadIdx.x < 10) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) s += red[w][threadIdx.x];
+        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
         partial[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
     }
     __threadfence();
@@ -386,6 +387,206 @@ __device__ __forceinline__ void loadN(const real* p, real* o)
     for (int k = N & ~3; k < N; ++k) o[k] = p[k];
 }
 
+// Per-thread state of the force pass for one particle i.
+template <typename real, int KRP>
+struct ForceCtx {
+    PosRec<real> ri;
+    int i, ti, T;
+    real len[3];
+    real F[3];
+    real W[9];
+};
+
+// Radial pairs of slots s0, s0 + ds, ... :
+//   f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u,  F_i += f_ij - f_ji,
+//   W_i += r_ij (x) f_ji.  The pair body has no branch, so the scheduler can
+//   interleave the four bodies of each walk step.
+template <typename real, int NR, int KR>
+__device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                             ForceCtx<real, (KR + 3) & ~3>& c, int s0, int ds)
+{
+    constexpr int KRP = (KR + 3) & ~3;
+    const real* e_i = a.e + (size_t)c.i * a.e_stride;
+    const int cR = min(a.cntR[c.i], a.mnR);
+    const int cnt = cR > s0 ? (cR - s0 + ds - 1) / ds : 0;
+    const int T = c.T, ti = c.ti;
+    auto radial_pair = [&](uint32_t e, const real* eij) {
+        const int j = (int)(e & kJMask);
+        const PosRec<real> rj = a.rec[j];
+        real eji[KRP];
+        loadN<real, KRP>(a.e + (size_t)j * a.e_stride + ti * KRP, eji);
+        real dx, dy, dz;
+        pair_vec(c.len, c.ri, rj, e, dx, dy, dz);
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        const real inv_r = rsqrt_r(r2);
+        const real r = r2 * inv_r;
+        real f[KR], df[KR];
+        basis_d<real, KR>(r, P[off.rcRi + ti * T + rj.t], f, df);
+        real ai = real(0), bj = real(0);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            ai += eij[k] * df[k];
+            bj += eji[k] * df[k];
+        }
+        const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+        const real fs = ai + bj;
+        c.F[0] += fs * ux;
+        c.F[1] += fs * uy;
+        c.F[2] += fs * uz;
+        const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const real bd = bj * d[p];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) c.W[3 * p + q] -= bd * u[q];
+        }
+    };
+    const uint32_t* nl = a.nlR + (size_t)s0 * a.n + c.i;
+    const size_t stride = (size_t)ds * a.n;
+    if (T == 1) {
+        real ei1[KRP];  // the one partner type's vector
+        loadN<real, KRP>(e_i, ei1);
+        walk4(nl, stride, cnt, [&](uint32_t e) { radial_pair(e, ei1); });
+    } else {
+        walk4(nl, stride, cnt, [&](uint32_t e) {
+            real eij[KRP];
+            loadN<real, KRP>(e_i + a.rec[e & kJMask].t * KRP, eij);
+            radial_pair(e, eij);
+        });
+    }
+}
+
+// Angular pairs, harmonic components k in [K0, K1) of every pair.  For
+// A = g(r) Y(u): dA/dr = (g' - l g / r) Y u + (g / r) grad Y; the reverse pair uses
+// Y(-u) = (-1)^l Y(u), so f_ji is the same contraction with Phi_j (-1)^l, negated.
+template <typename real, int NA, int KA, int K0, int K1, typename Ctx>
+__device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                                Ctx& c)
+{
+    const int T = c.T, ti = c.ti;
+    const real* phi_i = a.phi + (size_t)c.i * kNLM * NA;
+    const int cA = min(a.cntA[c.i], a.mnA);
+    NbrWalk<real> wa(a.nlA, a.n, c.i, cA, a.rec);
+    for (int s = 0; s < cA; ++s) {
+        uint32_t e;
+        PosRec<real> rj;
+        wa.next(s, e, rj);
+        const int j = (int)(e & kJMask);
+        real dx, dy, dz;
+        pair_vec(c.len, c.ri, rj, e, dx, dy, dz);
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        const real inv_r = rsqrt_r(r2);
+        const real r = r2 * inv_r;
+        const int tij = ti * T + rj.t, tji = rj.t * T + ti;
+        real f[KA], df[KA];
+        basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
+        real gi[NA], dgi[NA], gj[NA], dgj[NA];
+        {
+            const real* cc = P + off.cA + tij * NA * KA;
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                real s0 = real(0), s1 = real(0);
+#pragma unroll
+                for (int k = 0; k < KA; ++k) {
+                    s0 += cc[nn * KA + k] * f[k];
+                    s1 += cc[nn * KA + k] * df[k];
+                }
+                gi[nn] = s0;
+                dgi[nn] = s1;
+            }
+        }
+        if (tji == tij) {
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                gj[nn] = gi[nn];
+                dgj[nn] = dgi[nn];
+            }
+        } else {
+            const real* cc = P + off.cA + tji * NA * KA;
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                real s0 = real(0), s1 = real(0);
+#pragma unroll
+                for (int k = 0; k < KA; ++k) {
+                    s0 += cc[nn * KA + k] * f[k];
+                    s1 += cc[nn * KA + k] * df[k];
+                }
+                gj[nn] = s0;
+                dgj[nn] = s1;
+            }
+        }
+        const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+        const ShMono<real> mono = sh_mono(ux, uy, uz);
+        const real* phi_j = a.phi + (size_t)j * kNLM * NA;
+        real si = real(0), sj = real(0);
+        real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
+#pragma unroll
+        for (int k = K0; k < K1; ++k) {
+            const real lr = real(l_of(k)) * inv_r;
+            real pi_[NA], pj[NA];
+            loadN<real, NA>(phi_i + k * NA, pi_);
+            loadN<real, NA>(phi_j + k * NA, pj);
+            real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                Gi_ += pi_[nn] * gi[nn];
+                dGi += pi_[nn] * dgi[nn];
+                Gj_ += pj[nn] * gj[nn];
+                dGj += pj[nn] * dgj[nn];
+            }
+            if (l_of(k) & 1) {
+                Gj_ = -Gj_;
+                dGj = -dGj;
+            }
+            real y, gx, gy, gz;
+            sh_val_grad(k, mono, y, gx, gy, gz);
+            si += (dGi - lr * Gi_) * y;
+            sj += (dGj - lr * Gj_) * y;
+            const real Gs = Gi_ + Gj_;
+            ga[0] += Gs * gx;
+            ga[1] += Gs * gy;
+            ga[2] += Gs * gz;
+            gb[0] += Gj_ * gx;
+            gb[1] += Gj_ * gy;
+            gb[2] += Gj_ * gz;
+        }
+        // F_i += f_ij - f_ji;  -f_ji = sj u + gb / r;  W_i += r_ij (x) f_ji
+        const real u[3] = {ux, uy, uz}, d[3] = {dx, dy, dz};
+        real vj[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            c.F[p] += (si + sj) * u[p] + ga[p] * inv_r;
+            vj[p] = sj * u[p] + gb[p] * inv_r;
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) c.W[3 * p + q] -= d[p] * vj[q];
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void force_outputs(const EvalArgs<real>& a, const ReqInfo& rq, int i, const real* F,
+                                              const real* W, double (&tot)[10])
+{
+    const int ui = a.perm[i];
+    const int lu = ui - rq.begin;  // index within the request's output blocks
+    const real Ui = a.U[i];
+    double* fo = a.force + (size_t)3 * rq.begin + lu;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
+    if (a.virial) {
+        double* vo = a.virial + (size_t)9 * rq.begin + lu;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) vo[(size_t)k * rq.n] = (double)W[k];
+    }
+    if (a.site) a.site[ui] = (double)Ui;
+    tot[0] = (double)Ui;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tot[1 + k] = (double)W[k];
+}
+
+// One thread per particle.
 template <typename real, int NR, int NA, int KR, int KA, int MB>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(EvalArgs<real> a)
 {
@@ -404,177 +605,21 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
 #pragma unroll
     for (int k = 0; k < 10; ++k) tot[k] = 0.0;
     if (i < it.end) {
-        const int T = md.T;
-        const real len[3] = {(real)rq.g.len[0], (real)rq.g.len[1], (real)rq.g.len[2]};
-        const PosRec<real> ri = a.rec[i];
-        const int ti = ri.t;
-        real F[3] = {real(0), real(0), real(0)};
-        real W[9];
+        ForceCtx<real, KRP> c;
+        c.i = i;
+        c.T = md.T;
+        c.ri = a.rec[i];
+        c.ti = c.ri.t;
+        for (int k = 0; k < 3; ++k) c.len[k] = (real)rq.g.len[k];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) W[k] = real(0);
-
-        // ---- radial pairs: f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u ----
-        const real* e_i = a.e + (size_t)i * a.e_stride;
-        real ei1[KRP];  // the one partner type's vector, when the model has one type
-        if (T == 1) loadN<real, KRP>(e_i, ei1);
-        const int cR = min(a.cntR[i], a.mnR);
-        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
-            const int j = (int)(e & kJMask);
-            const PosRec<real> rj = a.rec[j];
-            real eji[KRP];
-            loadN<real, KRP>(a.e + (size_t)j * a.e_stride + ti * KRP, eji);
-            real dx, dy, dz;
-            pair_vec(len, ri, rj, e, dx, dy, dz);
-            const real r2 = dx * dx + dy * dy + dz * dz;
-            const real inv_r = rsqrt_r(r2);
-            const real r = r2 * inv_r;
-            real f[KR], df[KR];
-            basis_d<real, KR>(r, P[off.rcRi + ti * T + rj.t], f, df);
-            real eij[KRP];
-            if (T == 1) {
+        for (int k = 0; k < 3; ++k) c.F[k] = real(0);
 #pragma unroll
-                for (int k = 0; k < KRP; ++k) eij[k] = ei1[k];
-            } else {
-                loadN<real, KRP>(e_i + rj.t * KRP, eij);
-            }
-            real ai = real(0), bj = real(0);
-#pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                ai += eij[k] * df[k];
-                bj += eji[k] * df[k];
-            }
-            const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-            const real fs = ai + bj;
-            F[0] += fs * ux;
-            F[1] += fs * uy;
-            F[2] += fs * uz;
-            const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                const real bd = bj * d[p];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) W[3 * p + q] -= bd * u[q];
-            }
-        });
-
-        // ---- angular pairs ----
-        const real* phi_i = a.phi + (size_t)i * kNLM * NA;
-        const int cA = min(a.cntA[i], a.mnA);
-        NbrWalk<real> wa(a.nlA, a.n, i, cA, a.rec);
-        for (int s = 0; s < cA; ++s) {
-            uint32_t e;
-            PosRec<real> rj;
-            wa.next(s, e, rj);
-            const int j = (int)(e & kJMask);
-            real dx, dy, dz;
-            pair_vec(len, ri, rj, e, dx, dy, dz);
-            const real r2 = dx * dx + dy * dy + dz * dz;
-            const real inv_r = rsqrt_r(r2);
-            const real r = r2 * inv_r;
-            const int tij = ti * T + rj.t, tji = rj.t * T + ti;
-            real f[KA], df[KA];
-            basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
-            real gi[NA], dgi[NA], gj[NA], dgj[NA];
-            {
-                const real* c = P + off.cA + tij * NA * KA;
-#pragma unroll
-                for (int nn = 0; nn < NA; ++nn) {
-                    real s0 = real(0), s1 = real(0);
-#pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        s0 += c[nn * KA + k] * f[k];
-                        s1 += c[nn * KA + k] * df[k];
-                    }
-                    gi[nn] = s0;
-                    dgi[nn] = s1;
-                }
-            }
-            if (tji == tij) {
-#pragma unroll
-                for (int nn = 0; nn < NA; ++nn) {
-                    gj[nn] = gi[nn];
-                    dgj[nn] = dgi[nn];
-                }
-            } else {
-                const real* c = P + off.cA + tji * NA * KA;
-#pragma unroll
-                for (int nn = 0; nn < NA; ++nn) {
-                    real s0 = real(0), s1 = real(0);
-#pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        s0 += c[nn * KA + k] * f[k];
-                        s1 += c[nn * KA + k] * df[k];
-                    }
-                    gj[nn] = s0;
-                    dgj[nn] = s1;
-                }
-            }
-            const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-            const ShMono<real> mono = sh_mono(ux, uy, uz);
-            const real* phi_j = a.phi + (size_t)j * kNLM * NA;
-            real si = real(0), sj = real(0);
-            real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
-#pragma unroll
-            for (int k = 0; k < kNLM; ++k) {
-                const real lr = real(l_of(k)) * inv_r;
-                real pi_[NA], pj[NA];
-                loadN<real, NA>(phi_i + k * NA, pi_);
-                loadN<real, NA>(phi_j + k * NA, pj);
-                real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
-#pragma unroll
-                for (int nn = 0; nn < NA; ++nn) {
-                    Gi_ += pi_[nn] * gi[nn];
-                    dGi += pi_[nn] * dgi[nn];
-                    Gj_ += pj[nn] * gj[nn];
-                    dGj += pj[nn] * dgj[nn];
-                }
-                if (l_of(k) & 1) {  // reverse pair: Y(-u) = (-1)^l Y(u)
-                    Gj_ = -Gj_;
-                    dGj = -dGj;
-                }
-                real y, gx, gy, gz;
-                sh_val_grad(k, mono, y, gx, gy, gz);
-                si += (dGi - lr * Gi_) * y;
-                sj += (dGj - lr * Gj_) * y;
-                const real Gs = Gi_ + Gj_;
-                ga[0] += Gs * gx;
-                ga[1] += Gs * gy;
-                ga[2] += Gs * gz;
-                gb[0] += Gj_ * gx;
-                gb[1] += Gj_ * gy;
-                gb[2] += Gj_ * gz;
-            }
-            // F_i += f_ij - f_ji;  -f_ji = sj u + gb / r;  W_i += r_ij (x) f_ji
-            const real u[3] = {ux, uy, uz}, d[3] = {dx, dy, dz};
-            real vj[3];
-#pragma unroll
-            for (int p = 0; p < 3; ++p) {
-                F[p] += (si + sj) * u[p] + ga[p] * inv_r;
-                vj[p] = sj * u[p] + gb[p] * inv_r;
-            }
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) W[3 * p + q] -= d[p] * vj[q];
-        }
-
-        const int ui = a.perm[i];
-        const int lu = ui - rq.begin;  // index within the request's output blocks
-        const real Ui = a.U[i];
-        double* fo = a.force + (size_t)3 * rq.begin + lu;
-#pragma unroll
-        for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
-        if (a.virial) {
-            double* vo = a.virial + (size_t)9 * rq.begin + lu;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) vo[(size_t)k * rq.n] = (double)W[k];
-        }
-        if (a.site) a.site[ui] = (double)Ui;
-        tot[0] = (double)Ui;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)W[k];
+        for (int k = 0; k < 9; ++k) c.W[k] = real(0);
+        force_radial<real, NR, KR>(a, P, off, c, 0, 1);
+        force_angular_k<real, NA, KA, 0, kNLM>(a, P, off, c);
+        force_outputs(a, rq, i, c.F, c.W, tot);
     }
-    reduce_totals(tot, it, rq, a.partial, a.counter, a.totals);
+    reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
 }
 
 // ---- shape dispatch -----------------------------------------------------------

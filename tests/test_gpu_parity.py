@@ -128,7 +128,7 @@ def test_error_paths(nep_lib):
 
 
 def test_kernel_variants_identical_and_autotune(nep_lib):
-    """Every register-cap variant computes the same numbers; the autotuner picks one."""
+    """Register-cap variants compute the same numbers bit for bit; the autotuner picks one."""
     model, system = water_model(), inputs.water_box(3000, seed=17)
     m = binding.Model(model, "fp32")
     ref = None
@@ -142,6 +142,8 @@ def test_kernel_variants_identical_and_autotune(nep_lib):
                 np.testing.assert_array_equal(got["force"], ref["force"])
                 np.testing.assert_array_equal(got["virial"], ref["virial"])
                 assert got["energy"] == ref["energy"]
+    with pytest.raises(binding.NepError):
+        binding.nep_set_tuning(m.h, 0, 3, 4)
     md_, mf = binding.nep_autotune(m.h, system.types, system.pos, system.box, system.pbc)
     assert md_ in (2, 3) and mf in (2, 3)
     assert binding.nep_get_tuning(m.h) == (md_, mf)
