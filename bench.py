@@ -41,7 +41,7 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 
 # DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
 # profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
-FORCE_TRAFFIC = {"evaluate_cu_sha1": "666ec4633bd239c1aa468d03becb512d6c6c6ba9", "bytes_per_particle": 889.8,
+FORCE_TRAFFIC = {"evaluate_cu_sha1": "faf9f4f3bd5477745dc6d8191342fc307af716fe", "bytes_per_particle": 875.1,
                  "capture": "profiles/force_descriptor_water200k_ncu.md"}
 
 

@@ -175,8 +175,8 @@ int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const i
  * nep_sync(), and thermo rows are valid after nep_sync().  Otherwise the call
  * returns when the steps are done.
  * Neighbour-list capacity is probed synchronously once per configuration shape
- * (n and cell grid) with 30% headroom, and raised when a later call sees counts
- * above 90% of it.  NEP_ERR_NEIGHBOR_OVERFLOW means a list outgrew its capacity:
+ * (n and cell grid) and set to 1.5 times the largest count plus 8; it is raised
+ * the same way when a chunk of steps sees counts above 80% of it.  NEP_ERR_NEIGHBOR_OVERFLOW means a list outgrew its capacity:
  * the state of that call is undefined and the capacity is raised for the next.
  */
 int nep_md_step(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
@@ -201,6 +201,33 @@ int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* mas
                     const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
                     double dt_fs, double temperature_K, double tau_fs, const double* noise, int sample_every,
                     double* thermo, int mem, void* stream);
+
+/*
+ * n_steps homogeneous non-equilibrium MD (HNEMD) steps for the thermal
+ * conductivity (Sec. III.B; the method of Fan et al., Phys. Rev. B 99, 064308,
+ * 2019).  Each step is the nep_md_step_nvt step (or the NVE step when noise is
+ * NULL) with a driving force added to the force after every evaluation:
+ *   F_i += F_e . W_i - (1/n) sum_j F_e . W_j,   (F_e . W_i)_b = sum_a Fe_a W_i[a][b],
+ * W_i the per-particle virial of Eq. 15.  The forces then add power F_e . J_pot
+ * and no net momentum.  After the step's thermostat the heat current
+ *   J_pot = sum_i W_i v_i,   J_kin = sum_i (1/2 m_i v_i^2 + U_i) v_i
+ * (Fan et al., Phys. Rev. B 92, 094301, 2015; eV Angstrom / fs) is taken, and its
+ * average over each sampling interval is written.  The thermal conductivity
+ * follows as kappa_ab = <J_a> / (T V Fe_b).
+ *   fe             host [3], F_e in 1/Angstrom
+ *   noise          host [n_steps][2] as in nep_md_step_nvt, or NULL for no
+ *                  thermostat (temperature_K and tau_fs are then ignored)
+ *   heat           host [n_steps / sample_every][6]: (J_pot, J_kin) averaged over
+ *                  the sample_every steps of each interval; NULL for none
+ *                  (requires sample_every > 0 otherwise)
+ *   force          the total force, driving force included: on entry when
+ *                  forces_valid is 1 (as left by a previous call), on return
+ * Every other argument and rule as in nep_md_step.
+ */
+int nep_md_step_hnemd(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                      const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+                      double dt_fs, const double fe[3], double temperature_K, double tau_fs, const double* noise,
+                      int sample_every, double* thermo, double* heat, int mem, void* stream);
 
 /*
  * Coarse-grained mapping of an atomistic configuration onto beads (Sec. II.B-C):

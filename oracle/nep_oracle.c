@@ -17,6 +17,13 @@
  *   Eq. 15  W_i = sum_{j != i} r_ij (x) dU_j/dr_ji,  r_ij = r_j - r_i
  *   Eq. 16  W = sum_i W_i
  *
+ * Heat transport (the HNEMD runs of Sec. III.B follow Fan et al., Phys. Rev. B 99,
+ * 064308 (2019), and the heat current of Fan et al., Phys. Rev. B 92, 094301 (2015)):
+ *   J_pot = sum_i W_i v_i                        (W_i of Eq. 15 acting on v_i)
+ *   J_kin = sum_i (1/2 m_i v_i^2 + U_i) v_i
+ *   F_i^ext = F_e . W_i - (1/N) sum_j F_e . W_j  ((F_e . W)_b = sum_a Fe_a W_ab)
+ * so that the driving forces add power F_e . J_pot and no net momentum.
+ *
  * Readings where the paper is silent (each is listed in the design notes):
  *   - Y_lm are the complex orthonormal spherical harmonics with the Condon-Shortley
  *     phase; theta is the polar angle of r_ij, phi its azimuth.
@@ -705,6 +712,50 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
 }
 
 /*
+ * HNEMD driving force (Fan et al. 2019): F_i += F_e . W_i - (1/N) sum_j F_e . W_j,
+ * with (F_e . W_i)_b = sum_a Fe_a W_i[a][b] and W_i the per-particle virial of
+ * Eq. 15 (SoA [9][n], row-major 3x3).  force SoA [3][n], updated in place.
+ */
+void oracle_hnemd_force(int n, const double fe[3], const double *W, double *force)
+{
+    double mean[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) mean[b] += fe[a] * W[(size_t)(3 * a + b) * n + i];
+    for (int b = 0; b < 3; ++b) mean[b] /= n;
+    for (int i = 0; i < n; ++i)
+        for (int b = 0; b < 3; ++b) {
+            double f = 0.0;
+            for (int a = 0; a < 3; ++a) f += fe[a] * W[(size_t)(3 * a + b) * n + i];
+            force[(size_t)b * n + i] += f - mean[b];
+        }
+}
+
+/*
+ * Heat current of a many-body potential (Fan et al. 2015), in eV Angstrom / fs:
+ *   J_pot[a] = sum_i sum_b W_i[a][b] v_i[b]
+ *   J_kin[a] = sum_i (1/2 m_i |v_i|^2 + U_i) v_i[a]
+ * vel SoA [3][n] (Angstrom/fs), U [n] (eV), W SoA [9][n]; out[6] = J_pot, J_kin.
+ */
+void oracle_heat_current(int n, const int *types, const double *masses, const double *vel, const double *U,
+                         const double *W, double out[6])
+{
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double v[3], v2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            v[a] = vel[(size_t)a * n + i];
+            v2 += v[a] * v[a];
+        }
+        double Ei = 0.5 * masses[types[i]] * v2 / ORACLE_ACC + U[i];
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) out[a] += W[(size_t)(3 * a + b) * n + i] * v[b];
+            out[3 + a] += Ei * v[a];
+        }
+    }
+}
+
+/*
  * Velocity-Verlet (the integrator of the MD step):
  *   v += dt/2 F/m;  r += dt v;  wrap periodic axes;  F = F(r);  v += dt/2 F/m.
  * With noise != NULL every step ends with stochastic velocity rescaling (Bussi,
@@ -712,16 +763,20 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
  *   K' = c K + (1 - c) (Kbar / N_f) (R1^2 + S) + 2 R1 sqrt(c (1 - c) K Kbar / N_f)
  * with c = exp(-dt / tau), N_f = 3n - 3, Kbar = N_f k_B T / 2 and the step's
  * noise (R1, S), and all velocities are scaled by sqrt(K' / K).
- * pos, vel, force: SoA [3][n], in/out; force must hold F(pos) on entry.
+ * With fe != NULL the HNEMD driving force of F_e = fe[3] (1/Angstrom) is added to
+ * the force after every evaluation (oracle_hnemd_force), before the second kick.
+ * pos, vel, force: SoA [3][n], in/out; force must hold the total force at pos on
+ * entry (with the driving force when fe != NULL).
  * masses: per type (amu).  thermo (optional) [n_steps][2]: potential energy and
- * kinetic energy after each step.
+ * kinetic energy after each step.  heat (optional) [n_steps][6]: J_pot and J_kin
+ * (eV Angstrom / fs) after each step, thermostat included.
  */
 int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
               const double *rcR, const double *rcA, const double *cR, const double *cA,
               const double *w0, const double *b0, const double *w1, const double *b1,
               int n, const int *types, double *pos, double *vel, double *force, const double *masses,
               const double box[3], const int pbc[3], int use_cells, int n_steps, double dt, double *thermo,
-              double temperature, double tau, const double *noise)
+              double temperature, double tau, const double *noise, const double *fe, double *heat)
 {
     double *U = (double *)malloc((size_t)n * sizeof(double) + 8);
     double *W = (double *)malloc((size_t)9 * n * sizeof(double) + 8);
@@ -740,6 +795,7 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
             free(U); free(W);
             return -1;
         }
+        if (fe) oracle_hnemd_force(n, fe, W, force);
         double ke = 0.0;
         for (int i = 0; i < n; ++i) {
             double mi = masses[types[i]], im = ORACLE_ACC / mi;
@@ -761,6 +817,7 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
             thermo[2 * step] = e;
             thermo[2 * step + 1] = ke / ORACLE_ACC;
         }
+        if (heat) oracle_heat_current(n, types, masses, vel, U, W, heat + (size_t)6 * step);
     }
     free(U); free(W);
     return 0;

@@ -49,8 +49,12 @@ def lib():
         _lib.oracle_neighbors.restype = C.c_long
         _lib.oracle_compute.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, i, p, i, i, p, p, p, p, p, p]
         _lib.oracle_compute.restype = i
-        _lib.oracle_md.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p, d, d, p]
+        _lib.oracle_md.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p, d, d, p, p, p]
         _lib.oracle_md.restype = i
+        _lib.oracle_hnemd_force.argtypes = [i, p, p, p]
+        _lib.oracle_hnemd_force.restype = None
+        _lib.oracle_heat_current.argtypes = [i, p, p, p, p, p, p]
+        _lib.oracle_heat_current.restype = None
     return _lib
 
 
@@ -183,10 +187,14 @@ def compute(model, system, sample=None, use_cells=None, want_q=False, q_route=0)
     return OracleResult(e.value if sample is None else np.nan, wt, U, F, W, q)
 
 
-def md(model, system, pos, vel, force, n_steps, dt, use_cells=None, temperature=0.0, tau=1.0, noise=None):
+def md(model, system, pos, vel, force, n_steps, dt, use_cells=None, temperature=0.0, tau=1.0, noise=None,
+       fe=None):
     """Velocity-Verlet for n_steps (NVE, or NVT with stochastic velocity rescaling
-    when noise [n_steps][2] is given); pos/vel/force are updated copies.
-    Returns (pos, vel, force, thermo[n_steps][2] = (E_pot, E_kin))."""
+    when noise [n_steps][2] is given; with fe[3] the HNEMD driving force is added
+    after every evaluation, and `force` must then include it on entry -- see
+    hnemd_force).  pos/vel/force are updated copies.
+    Returns (pos, vel, force, thermo[n_steps][2] = (E_pot, E_kin)), plus
+    heat[n_steps][6] = (J_pot, J_kin) after each step when fe is given."""
     L = lib()
     n = system.n
     if use_cells is None:
@@ -198,12 +206,33 @@ def md(model, system, pos, vel, force, n_steps, dt, use_cells=None, temperature=
     masses = _f64(system.masses)
     thermo = np.zeros((n_steps, 2))
     nz = _f64(noise) if noise is not None else None
+    fe_ = _f64(fe) if fe is not None else None
+    heat = np.zeros((max(1, n_steps), 6)) if fe is not None else None
     rc = L.oracle_md(*ints, *[_ptr(a) for a in arrs], n, _ptr(types), _ptr(pos), _ptr(vel), _ptr(force),
                      _ptr(masses), _ptr(box), _ptr(pbc), int(use_cells), int(n_steps), float(dt), _ptr(thermo),
-                     float(temperature), float(tau), _ptr(nz))
+                     float(temperature), float(tau), _ptr(nz), _ptr(fe_), _ptr(heat))
     if rc != 0:
         raise RuntimeError("oracle_md failed")
+    if fe is not None:
+        return pos, vel, force, thermo, heat[:n_steps]
     return pos, vel, force, thermo
+
+
+def hnemd_force(fe, virial, force):
+    """force [3][n] plus the HNEMD driving force of fe[3] from per-particle virials
+    virial [9][n] (a new array)."""
+    f = _f64(force).copy()
+    w = _f64(virial)
+    lib().oracle_hnemd_force(f.shape[1], _ptr(_f64(fe)), _ptr(w), _ptr(f))
+    return f
+
+
+def heat_current(system, vel, site_energy, virial):
+    """(J_pot[3], J_kin[3]) in eV Angstrom / fs."""
+    out = np.zeros(6)
+    lib().oracle_heat_current(system.n, _ptr(_i32(system.types)), _ptr(_f64(system.masses)), _ptr(_f64(vel)),
+                              _ptr(_f64(site_energy)), _ptr(_f64(virial)), _ptr(out))
+    return out[:3], out[3:]
 
 
 def wrap(system):
@@ -219,7 +248,8 @@ def wrap(system):
 
 
 __all__ = ["cg_map", "fc", "dfc", "fk", "dfk", "chebyshev", "dchebyshev", "gn", "dgn", "legendre", "dlegendre",
-           "assoc_legendre", "ylm", "neighbors", "compute", "md", "wrap", "OracleResult", "lib"]
+           "assoc_legendre", "ylm", "neighbors", "compute", "md", "hnemd_force",
+           "heat_current", "wrap", "OracleResult", "lib"]
 
 
 def cg_map(group_start, group_atoms, mass, pos, box, pbc, force=None, virial=None):

@@ -34,7 +34,7 @@ EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
             "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
             "nep_compute_static", "nep_compute_batch", "nep_md_step_nvt", "nep_cg_map",
-            "nep_virial_correction", "nep_autotune", "nep_set_tuning", "nep_get_tuning"]
+            "nep_virial_correction", "nep_autotune", "nep_set_tuning", "nep_get_tuning", "nep_md_step_hnemd"]
 
 _lib = None
 
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
     lib.nep_compute_batch.restype = i
     lib.nep_md_step_nvt.argtypes = [p, i, p, p, p, p, p, p, p, i, i, d, d, d, p, i, p, i, p]
     lib.nep_md_step_nvt.restype = i
+    lib.nep_md_step_hnemd.argtypes = [p, i, p, p, p, p, p, p, p, i, i, d, p, d, d, p, i, p, p, i, p]
+    lib.nep_md_step_hnemd.restype = i
     lib.nep_cg_map.argtypes = [p, i, p, p, i, p, p, p, p, p, p, i, i, p, p, p, p]
     lib.nep_cg_map.restype = i
     lib.nep_virial_correction.argtypes = [p, i, i, d]
@@ -270,6 +272,23 @@ def nep_md_step_nvt(h, types, masses, box, pbc, pos, vel, force, forces_valid, n
                                   _ptr(force), int(forces_valid), int(n_steps), float(dt_fs), float(temperature_K),
                                   float(tau_fs), _ptr(noise), int(sample_every), _ptr(thermo), mem,
                                   _stream_of(pos, stream)), "nep_md_step_nvt")
+
+
+def nep_md_step_hnemd(h, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs, fe,
+                      temperature_K=0.0, tau_fs=1.0, noise=None, sample_every=0, thermo=None, heat=None, stream=None):
+    """HNEMD steps (driving force fe[3], optional thermostat noise); heat [samples][6]
+    receives the interval-averaged (J_pot, J_kin)."""
+    mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
+    n = int(types.shape[0])
+    masses = _host(masses, np.float64)
+    box = _host(box, np.float64)
+    pbc = _host(pbc, np.int32)
+    fe = _host(fe, np.float64)
+    noise = None if noise is None else _host(noise, np.float64)
+    _check(load().nep_md_step_hnemd(h, n, _ptr(types), _ptr(masses), _ptr(box), _ptr(pbc), _ptr(pos), _ptr(vel),
+                                    _ptr(force), int(forces_valid), int(n_steps), float(dt_fs), _ptr(fe),
+                                    float(temperature_K), float(tau_fs), _ptr(noise), int(sample_every),
+                                    _ptr(thermo), _ptr(heat), mem, _stream_of(pos, stream)), "nep_md_step_hnemd")
 
 
 def bussi_noise(n_steps, n_particles, seed):

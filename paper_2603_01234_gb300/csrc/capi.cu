@@ -190,6 +190,7 @@ struct nep_model {
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
     Buf noise_d, bussi;  // thermostat: random numbers of the call; [step, alpha] words
+    Buf md_virial, md_site, heat, heat_rows;  // HNEMD: per-particle W_i and U_i; acc[6] + counter; rows
     int* h_flags = nullptr;        // pinned: maxcnt[2], err
     double* h_totals = nullptr;    // pinned [10 * requests]
     size_t h_totals_cap = 0;
@@ -372,7 +373,7 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
     NEP_TRY(m->phi.ensure(rs * 24 * m->nA * (size_t)n));
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
-    NEP_TRY(m->partial2.ensure(sizeof(double) * ((n + kBlock - 1) / kBlock)));
+    NEP_TRY(m->partial2.ensure(sizeof(double) * 6 * ((n + kBlock - 1) / kBlock)));
     NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
     const size_t old_req = m->counters.cap / sizeof(unsigned int);
     NEP_TRY(m->counters.ensure(sizeof(unsigned int) * (n_req + 2)));
@@ -679,11 +680,34 @@ struct Thermostat {
     double c = 1.0, kbar = 0.0, n_f = 1.0;
 };
 
+// HNEMD driving force and heat-current sampling of an MD call (inactive when on == 0).
+struct Drive {
+    int on = 0;
+    double fe[3] = {0.0, 0.0, 0.0};
+    double* virial = nullptr;  // device [9][n] per-particle virial of the step
+    double* site = nullptr;    // device [n] site energies of the step
+    double* acc = nullptr;     // device [6] interval sums; followed by the block counter
+    double* rows = nullptr;    // device [samples][6] interval averages
+};
+
+// The force evaluation of an MD step, with the driving force added when it is on.
+template <typename real>
+int md_forces(nep_model* m, const Plan& p, int n, double* force, const Drive& dr, cudaEvent_t mid = nullptr)
+{
+    NEP_TRY(run_evaluate<real>(m, p, force, dr.on ? dr.virial : nullptr, dr.on ? dr.site : nullptr,
+                               m->totals.as<double>(), mid));
+    if (dr.on) {
+        cudaError_t e = launch_hnemd_force(n, dr.fe, dr.virial, m->totals.as<double>(), force, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("driving force: ") + cudaGetErrorString(e));
+    }
+    return NEP_OK;
+}
+
 // One MD step's launches (used eagerly and under stream capture).
 template <typename real>
 int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_m_acc, const double* mass,
                      const CellGrid& g, double* pos, double* vel, double* force, double dt, bool sample,
-                     int step_stride, const Thermostat& th)
+                     int step_stride, const Thermostat& th, const Drive& dr)
 {
     const Plan& p = m->plan;
     cudaEvent_t* ev = nullptr;
@@ -702,7 +726,7 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
     if (ev) NEP_CUDA(cudaEventRecord(ev[2], m->cur));
     NEP_TRY(run_neighbors<real>(m, p));
     if (ev) NEP_CUDA(cudaEventRecord(ev[3], m->cur));
-    NEP_TRY(run_evaluate<real>(m, p, force, nullptr, nullptr, m->totals.as<double>(), ev ? ev[4] : nullptr));
+    NEP_TRY(md_forces<real>(m, p, n, force, dr, ev ? ev[4] : nullptr));
     if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
     e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
@@ -710,6 +734,12 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
         e = launch_bussi(n, types_d, mass, m->T, vel, m->partial2.as<double>(), m->counters.as<unsigned int>(),
                          th.noise, m->bussi.as<int>(), th.c, th.kbar, th.n_f, m->bussi.as<double>() + 1, m->cur);
         if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("thermostat: ") + cudaGetErrorString(e));
+    }
+    if (dr.on) {
+        e = launch_heat(n, types_d, mass, m->T, vel, dr.site, dr.virial, m->partial2.as<double>(),
+                        reinterpret_cast<unsigned int*>(dr.acc + 6), dr.acc, dr.rows, m->sample_index.as<int>(),
+                        sample ? 1 : 0, step_stride, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("heat current: ") + cudaGetErrorString(e));
     }
     if (sample) {
         e = launch_sample(n, types_d, mass, m->T, vel, m->totals.as<double>(), m->partial2.as<double>(),
@@ -756,7 +786,7 @@ template <typename real>
 int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
             const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
             double dt, int sample_every, double* thermo, int mem, void* stream, double temp_K = 0.0,
-            double tau_fs = 0.0, const double* noise = nullptr)
+            double tau_fs = 0.0, const double* noise = nullptr, const double* fe = nullptr, double* heat = nullptr)
 {
     CellGrid g;
     NEP_TRY(make_grid(m, box, pbc, g));
@@ -794,6 +824,21 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         force_d = m->force_d.as<double>();
     }
     NEP_TRY(ensure_plan_workspace(m, p));
+    const int n_samples = sample_every > 0 ? n_steps / sample_every : 0;
+    Drive dr;
+    if (fe) {
+        NEP_TRY(m->md_virial.ensure(sizeof(double) * 9 * (size_t)n));
+        NEP_TRY(m->md_site.ensure(sizeof(double) * (size_t)n));
+        NEP_TRY(m->heat.ensure(sizeof(double) * 8));
+        NEP_TRY(m->heat_rows.ensure(sizeof(double) * 6 * std::max(1, n_samples)));
+        NEP_CUDA(cudaMemsetAsync(m->heat.p, 0, sizeof(double) * 8, m->cur));  // sums and counter
+        dr.on = 1;
+        for (int a = 0; a < 3; ++a) dr.fe[a] = fe[a];
+        dr.virial = m->md_virial.as<double>();
+        dr.site = m->md_site.as<double>();
+        dr.acc = m->heat.as<double>();
+        dr.rows = m->heat_rows.as<double>();
+    }
 
     // Size the neighbour lists (one synchronous probe) only for a new
     // configuration shape; continuation calls rely on the deferred status.
@@ -817,7 +862,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
             if (m->autotune) NEP_TRY(autotune_plan<real>(m, p, m->force_tmp.as<double>()));
             NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
         }
-        if (!forces_valid) NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>()));
+        if (!forces_valid) NEP_TRY(md_forces<real>(m, p, n, force_d, dr));
     }
     Thermostat th;
     if (noise) {
@@ -832,7 +877,6 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         th.n_f = 3.0 * n - 3.0;
         th.kbar = 0.5 * th.n_f * 8.617333262e-5 * temp_K;
     }
-    const int n_samples = sample_every > 0 ? n_steps / sample_every : 0;
     NEP_TRY(m->thermo.ensure(sizeof(double) * 12 * std::max(1, n_samples)));
     NEP_TRY(m->sample_index.ensure(sizeof(int)));
     if (n_samples > 0) NEP_CUDA(cudaMemsetAsync(m->sample_index.p, 0, sizeof(int), m->cur));
@@ -865,15 +909,17 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&th, sizeof th);
         put(&m->mb_desc, sizeof m->mb_desc);
         put(&m->mb_force, sizeof m->mb_force);
-        const void* tptr[] = {m->bussi.p};
+        const void* tptr[] = {m->bussi.p, dr.virial, dr.site, dr.acc, dr.rows};
         put(tptr, sizeof tptr);
+        put(&dr.on, sizeof dr.on);
+        put(dr.fe, sizeof dr.fe);
         if (m->graph.exec && m->graph.key == key) return NEP_OK;
         m->graph.reset();
         NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
         int rc = NEP_OK;
         for (int s = 0; s < chunk && rc == NEP_OK; ++s)
             rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                        sample_every > 0 && s == chunk - 1, sample_every, th);
+                                        sample_every > 0 && s == chunk - 1, sample_every, th, dr);
         cudaGraph_t graph = nullptr;
         cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
         if (rc != NEP_OK) {
@@ -927,13 +973,15 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     }
     for (; done < n_steps; ++done)
         NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every, th));
+                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every, th, dr));
     NEP_CUDA(cudaMemcpyAsync(m->h_async, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
     NEP_CUDA(cudaEventRecord(m->ev_flags, m->cur));
     m->async_pending = true;
     m->async_stream = m->cur;
     if (n_samples > 0)
         NEP_CUDA(cudaMemcpyAsync(thermo, m->thermo.p, sizeof(double) * 12 * n_samples, cudaMemcpyDeviceToHost, m->cur));
+    if (heat && n_samples > 0)
+        NEP_CUDA(cudaMemcpyAsync(heat, m->heat_rows.p, sizeof(double) * 6 * n_samples, cudaMemcpyDeviceToHost, m->cur));
     if (mem == NEP_HOST) {
         NEP_CUDA(cudaMemcpyAsync(pos, pos_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
         NEP_CUDA(cudaMemcpyAsync(vel, vel_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
@@ -1132,7 +1180,8 @@ int nep_destroy(nep_model* m)
                    &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
                    &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
-                   &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev, &m->noise_d, &m->bussi};
+                   &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev, &m->noise_d, &m->bussi,
+                   &m->md_virial, &m->md_site, &m->heat, &m->heat_rows};
     for (Buf* b : bufs) b->release();
     if (m->h_flags) cudaFreeHost(m->h_flags);
     if (m->h_totals) cudaFreeHost(m->h_totals);
@@ -1336,6 +1385,27 @@ int nep_md_step_nvt(nep_model* m, int n, const int32_t* types, const double* mas
                                  sample_every, thermo, mem, stream, temperature_K, tau_fs, noise)
                : md_impl<float>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
                                 sample_every, thermo, mem, stream, temperature_K, tau_fs, noise);
+}
+
+int nep_md_step_hnemd(nep_model* m, int n, const int32_t* types, const double* masses, const double box[3],
+                      const int32_t pbc[3], double* pos, double* vel, double* force, int forces_valid, int n_steps,
+                      double dt_fs, const double fe[3], double temperature_K, double tau_fs, const double* noise,
+                      int sample_every, double* thermo, double* heat, int mem, void* stream)
+{
+    NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
+    if (!(dt_fs > 0.0) || !isfinite(dt_fs)) return fail(NEP_ERR_ARG, "dt must be positive");
+    if (!fe || !isfinite(fe[0]) || !isfinite(fe[1]) || !isfinite(fe[2]))
+        return fail(NEP_ERR_ARG, "the driving force parameter must be three finite numbers");
+    if (noise && (!(temperature_K >= 0.0) || !(tau_fs > 0.0)))
+        return fail(NEP_ERR_ARG, "need temperature >= 0 and tau > 0");
+    if (noise && n < 2) return fail(NEP_ERR_ARG, "the thermostat needs n >= 2");
+    if (heat && sample_every <= 0) return fail(NEP_ERR_ARG, "heat rows need sample_every > 0");
+    Guard guard(m->device);
+    return m->precision == NEP_FP64
+               ? md_impl<double>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                 sample_every, thermo, mem, stream, temperature_K, tau_fs, noise, fe, heat)
+               : md_impl<float>(m, n, types, masses, box, pbc, pos, vel, force, forces_valid, n_steps, dt_fs,
+                                sample_every, thermo, mem, stream, temperature_K, tau_fs, noise, fe, heat);
 }
 
 int nep_cg_map(nep_model* m, int n_cg, const int32_t* group_start, const int32_t* group_atoms, int n_aa,

@@ -7,6 +7,12 @@
 //   k_bussi_ke     E_kin and the stochastic-velocity-rescaling factor (Bussi,
 //                  Donadio, Parrinello 2007) from the step's two random numbers
 //   k_scale_vel    v *= alpha
+//   k_hnemd_force  HNEMD driving force (Fan et al., Phys. Rev. B 99, 064308, 2019)
+//                  F_i += F_e . W_i - F_e . W / N, with W_i the per-particle virial
+//                  of Eq. 15 and W = sum_i W_i (Eq. 16)
+//   k_heat         heat current J_pot = sum_i W_i v_i, J_kin = sum_i (1/2 m v^2 + U_i) v_i
+//                  (Fan et al., Phys. Rev. B 92, 094301, 2015), summed over the steps
+//                  of a sampling interval and written as the interval's average
 #include "nep_common.cuh"
 
 namespace nep {
@@ -160,6 +166,86 @@ __global__ void __launch_bounds__(kBlock) k_scale_vel(int n, double* __restrict_
     vel[(size_t)2 * n + i] *= a;
 }
 
+// (F_e . W)_b = sum_a Fe_a W[a][b]; W is row-major [9][n], totals[1 + 3a + b] its sum.
+__global__ void __launch_bounds__(kBlock) k_hnemd_force(int n, double fe0, double fe1, double fe2,
+                                                        const double* __restrict__ virial,
+                                                        const double* __restrict__ totals, double* __restrict__ force)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double inv_n = 1.0 / n;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const double mean = (fe0 * totals[1 + b] + fe1 * totals[4 + b] + fe2 * totals[7 + b]) * inv_n;
+        const double f = fe0 * virial[(size_t)b * n + i] + fe1 * virial[(size_t)(3 + b) * n + i] +
+                         fe2 * virial[(size_t)(6 + b) * n + i];
+        force[(size_t)b * n + i] += f - mean;
+    }
+}
+
+// acc[6] accumulates (J_pot, J_kin) over the steps of a sampling interval; at a
+// sampling step the last block writes acc / step_stride to row *sample_index of
+// rows (read before k_sample advances it) and clears acc.
+__global__ void __launch_bounds__(kBlock) k_heat(int n, const int* __restrict__ types, TypeTable mass,
+                                                 const double* __restrict__ vel, const double* __restrict__ site,
+                                                 const double* __restrict__ virial, double* __restrict__ partial,
+                                                 unsigned int* __restrict__ counter, double* __restrict__ acc,
+                                                 double* __restrict__ rows, const int* __restrict__ sample_index,
+                                                 int sample, int step_stride)
+{
+    __shared__ double red[kBlock / 32][6];
+    __shared__ bool last;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double j[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        double v[3], v2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[a] = vel[(size_t)a * n + i];
+            v2 += v[a] * v[a];
+        }
+        const double Ei = 0.5 * mass.v[types[i]] * v2 / kAcc + site[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) j[a] += virial[(size_t)(3 * a + b) * n + i] * v[b];
+            j[3 + a] = Ei * v[a];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) j[k] += __shfl_xor_sync(0xffffffffu, j[k], o);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[threadIdx.x >> 5][k] = j[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) s += red[w][threadIdx.x];
+        partial[(size_t)6 * blockIdx.x + threadIdx.x] = s;
+        __threadfence();  // each writer publishes its partial before the block is counted
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 6) {
+        const volatile double* p = partial;
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)6 * b + threadIdx.x];
+        const double t = acc[threadIdx.x] + s;
+        if (sample) {
+            rows[(size_t)6 * (*sample_index) + threadIdx.x] = t / step_stride;
+            acc[threadIdx.x] = 0.0;
+        } else {
+            acc[threadIdx.x] = t;
+        }
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
 __global__ void k_scale(int n, double* __restrict__ pos, double sx, double sy, double sz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,6 +298,23 @@ cudaError_t launch_bussi(int n, const int* types, const double* mass, int T, dou
     k_bussi_ke<<<nb, kBlock, 0, st>>>(n, types, make_table(mass, T), vel, partial, counter, noise, step, c, kbar, n_f,
                                       alpha);
     k_scale_vel<<<nb, kBlock, 0, st>>>(n, vel, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hnemd_force(int n, const double fe[3], const double* virial, const double* totals, double* force,
+                               cudaStream_t st)
+{
+    k_hnemd_force<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, fe[0], fe[1], fe[2], virial, totals, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heat(int n, const int* types, const double* mass, int T, const double* vel, const double* site,
+                        const double* virial, double* partial, unsigned int* counter, double* acc, double* rows,
+                        const int* sample_index, int sample, int step_stride, cudaStream_t st)
+{
+    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
+    k_heat<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(mass, T), vel, site, virial, partial,
+                                                         counter, acc, rows, sample_index, sample, step_stride);
     return cudaGetLastError();
 }
 

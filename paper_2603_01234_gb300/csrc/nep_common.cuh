@@ -156,6 +156,16 @@ cudaError_t launch_bussi(int n, const int* types, const double* mass, int T, dou
                          unsigned int* counter, const double* noise, int* step, double c, double kbar, double n_f,
                          double* alpha, cudaStream_t st);
 
+// HNEMD driving force F_i += F_e . W_i - F_e . W / N (virial [9][n], totals[1..9] = W).
+cudaError_t launch_hnemd_force(int n, const double fe[3], const double* virial, const double* totals, double* force,
+                               cudaStream_t st);
+// Heat current (J_pot, J_kin) of the step added to acc[6]; at a sampling step the
+// interval average goes to rows[*sample_index][6] and acc is cleared.
+// partial: [blocks][6] doubles.
+cudaError_t launch_heat(int n, const int* types, const double* mass, int T, const double* vel, const double* site,
+                        const double* virial, double* partial, unsigned int* counter, double* acc, double* rows,
+                        const int* sample_index, int sample, int step_stride, cudaStream_t st);
+
 // Coarse-grained mapping: bead positions (Eq. 9), summed forces (Eq. 12) and virials (Eq. 14).
 cudaError_t launch_cg_map(int n_cg, int n_aa, const int* start, const int* atoms, const double* mass,
                           const double* pos, const double* force, const double* virial, const CellGrid& g,
