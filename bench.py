@@ -421,7 +421,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(system),
             "ns_per_day": (1000.0 / ms_step) * DT_FS * 0.0864,
-            "gpu_launches": 10 * args.steps,  # per step: kick/drift, 5 cell-build, neighbours, descriptor, force, kick
+            "gpu_launches": 11 * args.steps,  # per step: kick/drift, 5 cell-build, neighbours, descriptor, force, force outputs, kick
             "stages_ms_per_step": {k: v / max(1, tsteps) for k, v in stages.items()},
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,

@@ -188,6 +188,7 @@ struct nep_model {
     Buf cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
+    Buf acc;  // FP32 force scatter accumulators [n][16] (64-bit fixed point)
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
     Buf noise_d, bussi;  // thermostat: random numbers of the call; [step, alpha] words
     Buf md_virial, md_site, heat, heat_rows;  // HNEMD: per-particle W_i and U_i; acc[6] + counter; rows
@@ -371,8 +372,9 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->cntA.ensure(sizeof(int) * n));
     NEP_TRY(m->U.ensure(rs * n));
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
-    NEP_TRY(m->phi.ensure(rs * 24 * m->nA * (size_t)n));
+    NEP_TRY(m->phi.ensure(rs * 24 * phi_pad(m->nA) * (size_t)n));
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
+    if (m->precision == NEP_FP32) NEP_TRY(m->acc.ensure(sizeof(unsigned long long) * 16 * (size_t)n));
     NEP_TRY(m->partial2.ensure(sizeof(double) * 6 * ((n + kBlock - 1) / kBlock)));
     NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
     const size_t old_req = m->counters.cap / sizeof(unsigned int);
@@ -487,6 +489,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.force = force;
     a.virial = virial;
     a.site = site;
+    a.acc = m->acc.as<unsigned long long>();
     a.partial = m->partial.as<double>();
     a.counter = m->counters.as<unsigned int>() + 2;
     a.totals = totals;
@@ -896,7 +899,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         };
         const void* ptrs[] = {types_d, pos_d, vel_d, force_d, m->nlR.p, m->nlA.p, m->cell_start.p, m->thermo.p,
                               m->partial.p, m->rec_s.p, m->phi.p, m->e.p, m->cur, p.dev.p, m->counters.p,
-                              m->totals.p};
+                              m->totals.p, m->acc.p};
         put(ptrs, sizeof ptrs);
         put(&n, sizeof n);
         put(&g, sizeof g);
@@ -1181,7 +1184,7 @@ int nep_destroy(nep_model* m)
                    &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
                    &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev, &m->noise_d, &m->bussi,
-                   &m->md_virial, &m->md_site, &m->heat, &m->heat_rows};
+                   &m->md_virial, &m->md_site, &m->heat, &m->heat_rows, &m->acc};
     for (Buf* b : bufs) b->release();
     if (m->h_flags) cudaFreeHost(m->h_flags);
     if (m->h_totals) cudaFreeHost(m->h_totals);
@@ -1638,7 +1641,7 @@ constexpr int kStaticMaxN = 4096;        // particles per call
 constexpr int kStaticMaxCells = 32768;   // cells of the call's grid
 constexpr int kStaticMNR = 256;          // radial neighbours per particle
 constexpr int kStaticMNA = 128;          // angular neighbours per particle
-constexpr int kStaticMaxNA = 5;          // n_A of the compiled shapes
+constexpr int kStaticMaxNA = phi_pad(5);  // padded n_A of the compiled shapes
 constexpr int kStaticMaxT = 4;           // particle types of the model
 constexpr int kStaticMaxKRP = 12;        // padded K_R
 constexpr int kStaticMaxItems = (kStaticMaxN + kBlock - 1) / kBlock;
@@ -1651,7 +1654,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct StaticLayout {
     size_t cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, U, e, phi, force;
     size_t nlR, nlA, cell_count, cell_local, block_off, cell_fill, cell_start;
-    size_t partial, counters, totals, flags, tables, end;
+    size_t partial, counters, totals, flags, tables, acc, end;
 };
 
 constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t nA, size_t ekrp)
@@ -1682,6 +1685,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     L.totals = p; p = align256(p + 8 * 10);
     L.flags = p; p = align256(p + 16);
     L.tables = p; p = align256(p + kStaticTableBytes);
+    L.acc = p; p = align256(p + (rs == 4 ? 8 * 16 * n : 0));  // FP32 force scatter accumulators
     L.end = p;
     return L;
 }
@@ -1720,7 +1724,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
 {
     unsigned char* base = nullptr;
     NEP_TRY(static_scratch(m->device, &base));
-    const StaticLayout L = static_layout(n, g.ncell, sizeof(real), m->nA, (size_t)m->T * m->KRP);
+    const StaticLayout L = static_layout(n, g.ncell, sizeof(real), phi_pad(m->nA), (size_t)m->T * m->KRP);
     if (L.end > kStaticScratchBytes) return fail(NEP_ERR_ARG, "static scratch too small for this call");
     // the request, its work items and the model table, staged through the handle's
     // pinned buffer (allocated by nep_create) into the scratch
@@ -1799,6 +1803,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;
     a.site = site_energy;
+    a.acc = sizeof(real) == 4 ? (unsigned long long*)(base + L.acc) : nullptr;
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
     a.totals = totals;

@@ -187,6 +187,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     stage_params(md.params, P, off.total);
     const int i = it.begin + threadIdx.x;
     if (i >= it.end) return;
+    if (a.acc) {  // the scatter accumulators of i start the force pass at zero
+        ulonglong2* z = reinterpret_cast<ulonglong2*>(a.acc + (size_t)i * 16);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) z[k] = make_ulonglong2(0ull, 0ull);
+    }
     const int T = md.T, H = md.H;
     const real len[3] = {(real)rq.g.len[0], (real)rq.g.len[1], (real)rq.g.len[2]};
     const PosRec<real> ri = a.rec[i];
@@ -314,11 +319,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             ei[t * KRP + k] = v;
         }
     }
-    real* ph = a.phi + (size_t)i * kNLM * NA;
+    // Phi is stored component-major, [24][n][NAP]: for one component the rows of
+    // consecutive particles are adjacent, so a warp's row loads are contiguous
+    constexpr int NAP = phi_pad(NA);
+    real* ph = a.phi + (size_t)i * NAP;
+    const size_t kstride = (size_t)a.n * NAP;
 #pragma unroll
     for (int k = 0; k < kNLM; ++k)
 #pragma unroll
-        for (int nn = 0; nn < NA; ++nn) ph[k * NA + nn] = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+        for (int nn = 0; nn < NAP; ++nn)
+            ph[k * kstride + nn] = nn < NA ? real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k] : real(0);
 }
 
 template <typename real>
@@ -464,7 +474,9 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
                                                 Ctx& c)
 {
     const int T = c.T, ti = c.ti;
-    const real* phi_i = a.phi + (size_t)c.i * kNLM * NA;
+    constexpr int NAP = phi_pad(NA);
+    const size_t kstride = (size_t)a.n * NAP;
+    const real* phi_i = a.phi + (size_t)c.i * NAP;
     const int cA = min(a.cntA[c.i], a.mnA);
     NbrWalk<real> wa(a.nlA, a.n, c.i, cA, a.rec);
     for (int s = 0; s < cA; ++s) {
@@ -517,15 +529,15 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
         }
         const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
         const ShMono<real> mono = sh_mono(ux, uy, uz);
-        const real* phi_j = a.phi + (size_t)j * kNLM * NA;
+        const real* phi_j = a.phi + (size_t)j * NAP;
         real si = real(0), sj = real(0);
         real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
 #pragma unroll
         for (int k = K0; k < K1; ++k) {
             const real lr = real(l_of(k)) * inv_r;
             real pi_[NA], pj[NA];
-            loadN<real, NA>(phi_i + k * NA, pi_);
-            loadN<real, NA>(phi_j + k * NA, pj);
+            loadN<real, NA>(phi_i + k * kstride, pi_);
+            loadN<real, NA>(phi_j + k * kstride, pj);
             real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
@@ -622,6 +634,178 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
     reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
 }
 
+// ---- FP32 scatter form -----------------------------------------------------------
+// Each ordered angular pair is evaluated once, by the thread of its centre i, which
+// contracts only Phi_i: f_ij = dU_i/dr_ij.  F_i gains f_ij in registers; F_j loses
+// it and W_j gains r_ji (x) f_ij through 64-bit fixed-point atomic adds.  Integer
+// sums do not depend on the order in which the adds arrive, so the results stay
+// bitwise reproducible.  The radial pairs stay in gather form (their reverse term
+// needs only j's 8-entry gradient vector).
+constexpr float kFixScale = 4294967296.0f;  // 2^32 fixed-point units per eV/A (or eV)
+constexpr double kFixUnit = 1.0 / 4294967296.0;
+
+__device__ __forceinline__ void fix_add(unsigned long long* p, float v)
+{
+    atomicAdd(p, (unsigned long long)__float2ll_rn(v * kFixScale));
+}
+
+__device__ __forceinline__ double fix_value(unsigned long long v) { return (double)(long long)v * kFixUnit; }
+
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+template <typename real, int NA, int KA, typename Ctx>
+__device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                                      Ctx& c, bool per_bead)
+{
+    const int T = c.T, ti = c.ti;
+    constexpr int NAP = phi_pad(NA);
+    const size_t kstride = (size_t)a.n * NAP;
+    const real* phi_i = a.phi + (size_t)c.i * NAP;
+    const int cA = min(a.cntA[c.i], a.mnA);
+    NbrWalk<real> wa(a.nlA, a.n, c.i, cA, a.rec);
+    for (int s = 0; s < cA; ++s) {
+        uint32_t e;
+        PosRec<real> rj;
+        wa.next(s, e, rj);
+        const int j = (int)(e & kJMask);
+        real dx, dy, dz;
+        pair_vec(c.len, c.ri, rj, e, dx, dy, dz);
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        const real inv_r = rsqrt_r(r2);
+        const real r = r2 * inv_r;
+        const int tij = ti * T + rj.t;
+        real f[KA], df[KA];
+        basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
+        real g[NA], dg[NA];
+        const real* cc = P + off.cA + tij * NA * KA;
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) {
+            real s0 = real(0), s1 = real(0);
+#pragma unroll
+            for (int k = 0; k < KA; ++k) {
+                s0 += cc[nn * KA + k] * f[k];
+                s1 += cc[nn * KA + k] * df[k];
+            }
+            g[nn] = s0;
+            dg[nn] = s1;
+        }
+        const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
+        const ShMono<real> mono = sh_mono(ux, uy, uz);
+        real sr = real(0);
+        real ga[3] = {real(0), real(0), real(0)};
+#pragma unroll
+        for (int k = 0; k < kNLM; ++k) {
+            real pi_[NA];
+            loadN<real, NA>(phi_i + k * kstride, pi_);
+            real G = real(0), dG = real(0);
+#pragma unroll
+            for (int nn = 0; nn < NA; ++nn) {
+                G += pi_[nn] * g[nn];
+                dG += pi_[nn] * dg[nn];
+            }
+            real y, gx, gy, gz;
+            sh_val_grad(k, mono, y, gx, gy, gz);
+            sr += (dG - real(l_of(k)) * inv_r * G) * y;
+            ga[0] += G * gx;
+            ga[1] += G * gy;
+            ga[2] += G * gz;
+        }
+        const real fij[3] = {sr * ux + ga[0] * inv_r, sr * uy + ga[1] * inv_r, sr * uz + ga[2] * inv_r};
+        unsigned long long* acc_j = a.acc + (size_t)j * 16;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            c.F[p] += fij[p];
+            fix_add(acc_j + p, -fij[p]);
+        }
+        const real d[3] = {dx, dy, dz};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                // W_j += r_ji (x) f_ij; the product is rounded on its own so that the
+                // totals do not depend on whether it is also scattered
+                const real w = mul_rn(-d[p], fij[q]);
+                c.W[3 * p + q] += w;  // c.W feeds only the totals here
+                if (per_bead) fix_add(acc_j + 3 + 3 * p + q, w);
+            }
+    }
+}
+
+// One thread per particle: radial pairs in gather form, angular pairs scattered.
+// Without per-particle virial output only the force is scattered; the virial
+// contributions of a thread's pairs go straight into the FP64 totals.
+template <typename real, int NR, int NA, int KR, int KA, int MB>
+__global__ void __launch_bounds__(kBlock, MB) k_force_scatter(EvalArgs<real> a)
+{
+    constexpr int KRP = (KR + 3) & ~3;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* P = reinterpret_cast<real*>(smem_raw);
+    const WorkItem it = a.items[blockIdx.x];
+    const ReqInfo& rq = a.reqs[it.req];
+    const ModelDesc<real> md = a.models[rq.model];
+    const ParamLayout off = md.off;
+    stage_params(md.params, P, off.n_cut_coef);
+    const int i = it.begin + threadIdx.x;
+    double tot[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) tot[k] = 0.0;
+    if (i < it.end) {
+        ForceCtx<real, KRP> c;
+        c.i = i;
+        c.T = md.T;
+        c.ri = a.rec[i];
+        c.ti = c.ri.t;
+        for (int k = 0; k < 3; ++k) c.len[k] = (real)rq.g.len[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.F[k] = real(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c.W[k] = real(0);
+        force_radial<real, NR, KR>(a, P, off, c, 0, 1);
+        unsigned long long* acc_i = a.acc + (size_t)i * 16;
+        const bool per_bead = a.virial != nullptr;
+        if (per_bead)  // W_i's radial part is complete here
+#pragma unroll
+            for (int k = 0; k < 9; ++k) fix_add(acc_i + 3 + k, c.W[k]);
+        force_angular_scatter<real, NA, KA>(a, P, off, c, per_bead);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) fix_add(acc_i + p, c.F[p]);
+        const real Ui = a.U[i];
+        if (a.site) a.site[a.perm[i]] = (double)Ui;
+        tot[0] = (double)Ui;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)c.W[k];
+    }
+    reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
+}
+
+// The accumulated F_i (and W_i) to the caller-order FP64 outputs.
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_scatter_outputs(EvalArgs<real> a)
+{
+    const WorkItem it = a.items[blockIdx.x];
+    const ReqInfo& rq = a.reqs[it.req];
+    const int i = it.begin + threadIdx.x;
+    if (i >= it.end) return;
+    const ulonglong2* acc = reinterpret_cast<const ulonglong2*>(a.acc + (size_t)i * 16);
+    const int lu = a.perm[i] - rq.begin;
+    const ulonglong2 w01 = acc[0], w23 = acc[1];
+    double* fo = a.force + (size_t)3 * rq.begin + lu;
+    fo[0] = fix_value(w01.x);
+    fo[rq.n] = fix_value(w01.y);
+    fo[(size_t)2 * rq.n] = fix_value(w23.x);
+    if (a.virial) {
+        double* vo = a.virial + (size_t)9 * rq.begin + lu;
+        vo[0] = fix_value(w23.y);
+#pragma unroll
+        for (int q = 2; q < 6; ++q) {  // words 2q, 2q + 1 are W[2q - 3], W[2q - 2]
+            const ulonglong2 w = acc[q];
+            vo[(size_t)(2 * q - 3) * rq.n] = fix_value(w.x);
+            vo[(size_t)(2 * q - 2) * rq.n] = fix_value(w.y);
+        }
+    }
+}
+
 // ---- shape dispatch -----------------------------------------------------------
 #define NEP_SHAPES(X) X(5, 4, 8, 8) X(5, 5, 9, 9)
 
@@ -643,8 +827,12 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
         cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_>,                         \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
         if (e != cudaSuccess) return e;                                                                       \
-        e = cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_, mb_>,                                          \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);               \
+        if constexpr (sizeof(real) == 4)                                                                      \
+            e = cudaFuncSetAttribute(k_force_scatter<real, a_, b_, c_, d_, mb_>,                              \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
+        else                                                                                                  \
+            e = cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_, mb_>,                                      \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
         if (e != cudaSuccess) return e;                                                                       \
     }
 #define NEP_CASE(a_, b_, c_, d_)                                  \
@@ -664,13 +852,22 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force)
 {
     const int nb = n_items;
+    if constexpr (sizeof(real) == 4) {
+        if (!a.acc) return cudaErrorInvalidValue;  // the FP32 form scatters into a.acc
+    }
 #define NEP_CASE(a_, b_, c_, d_)                                                                            \
     if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                     \
         if (mb_desc == 2) k_descriptor<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_desc, st>>>(a);          \
         else k_descriptor<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_desc, st>>>(a);                       \
         if (mid) cudaEventRecord(mid, st);                                                                  \
-        if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);             \
-        else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                           \
+        if constexpr (sizeof(real) == 4) {                                                                  \
+            if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \
+            else k_force_scatter<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);               \
+            k_scatter_outputs<real><<<nb, kBlock, 0, st>>>(a);                                              \
+        } else {                                                                                            \
+            if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);         \
+            else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                       \
+        }                                                                                                   \
         return cudaGetLastError();                                                                          \
     }
     NEP_SHAPES(NEP_CASE)

@@ -24,6 +24,10 @@ constexpr int kMaxTypes = 16;
 constexpr int kBlock = 128;          // threads per block = particles per work item
 constexpr int kScanItems = 4096;     // cells per block of the scan
 
+// Row length of Phi_i per harmonic component: n_A padded to a multiple of 4 so that
+// every row starts on a 16-byte boundary (vector loads).
+__host__ __device__ constexpr int phi_pad(int nA) { return (nA + 3) & ~3; }
+
 __host__ __device__ inline uint32_t pack_entry(int j, int dx, int dy, int dz)
 {
     return (uint32_t)j | ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6)) << kJBits);
@@ -109,11 +113,12 @@ struct EvalArgs {
     real* U;                    // [n] sorted site energies
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
-    real* phi;                  // [n][24][NA] dU/dA_nlm
+    real* phi;                  // [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null
     double* site;               // [n] or null
+    unsigned long long* acc;    // FP32 scatter form: [n][16] fixed-point F[3], W[9] (2^-32 units)
     double* partial;            // [items][10] per-block (E, W[9])
     unsigned int* counter;      // [requests] last-block counters (self-resetting)
     double* totals;             // [requests][10]: E, W[9]
@@ -132,6 +137,7 @@ cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t sm
 
 // Shape-dispatched evaluation; returns cudaErrorInvalidValue for an uncompiled shape.
 // mb_desc / mb_force: resident blocks per SM of the FP32 kernel variants (2 or 3).
+// The FP32 form needs a.acc (the scatter accumulators); the FP64 form ignores it.
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr, int mb_desc = 3,

@@ -82,3 +82,7 @@ def small_systems():
     yield "aacg300", aacg_model(), s
     w = inputs.nanowire(n_total=3000, n_cells_x=12, seed=13, margin=5.0)
     yield "nanowire3000", nanowire_model(), w
+    # the second compiled shape: n_R = n_A = 5, K_R = K_A = 9 (n_A not a multiple of 4)
+    m = inputs.random_model(n_types=2, n_desc_radial=5, n_desc_angular=5, n_basis_radial=9, n_basis_angular=9,
+                            hidden=20, rc_radial=6.0, rc_angular=4.5, seed=14)
+    yield "shape5599_2types", m, inputs.random_periodic(400, [18.0, 18.0, 18.0], seed=15, min_dist=1.6, n_types=2)
