@@ -229,45 +229,52 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         const real* cutA = cut + TT + ri.t * T;
         const real cR1 = cutR[0], cA1 = cutA[0];  // the one pair type of a one-type model
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
+        const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
         for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
             int z = cz + dz;
-            if (g.pbc[2]) z = ((z % g.nc[2]) + g.nc[2]) % g.nc[2];
-            else if (z < 0 || z >= g.nc[2]) continue;
+            if (g.pbc[2]) {  // |dz| <= 2, so at most two corrections even for one cell per axis
+                while (z < 0) z += ncz;
+                while (z >= ncz) z -= ncz;
+            } else if (z < 0 || z >= ncz) {
+                continue;
+            }
             for (int dy = -g.S[1]; dy <= g.S[1]; ++dy) {
                 int y = cy + dy;
-                if (g.pbc[1]) y = ((y % g.nc[1]) + g.nc[1]) % g.nc[1];
-                else if (y < 0 || y >= g.nc[1]) continue;
+                if (g.pbc[1]) {
+                    while (y < 0) y += ncy;
+                    while (y >= ncy) y -= ncy;
+                } else if (y < 0 || y >= ncy) {
+                    continue;
+                }
                 for (int dx = -g.S[0]; dx <= g.S[0]; ++dx) {
                     int x = cx + dx;
-                    if (g.pbc[0]) x = ((x % g.nc[0]) + g.nc[0]) % g.nc[0];
-                    else if (x < 0 || x >= g.nc[0]) continue;
-                    const int cell = q.cell_base + (z * g.nc[1] + y) * g.nc[0] + x;
+                    if (g.pbc[0]) {
+                        while (x < 0) x += ncx;
+                        while (x >= ncx) x -= ncx;
+                    } else if (x < 0 || x >= ncx) {
+                        continue;
+                    }
+                    const int cell = q.cell_base + (z * ncy + y) * ncx + x;
                     const real ox = (real)dx * lx, oy = (real)dy * ly, oz = (real)dz * lz;
                     const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
                     const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
-                    // the centre cell skips i itself: two ranges instead of a test per candidate
-                    const bool centre = (dx == 0 && dy == 0 && dz == 0);
-                    const int split = centre ? i : ke;
-                    for (int part = 0; part < 2; ++part) {
-                        const int k0 = part == 0 ? kb : split + 1;
-                        const int k1 = part == 0 ? min(split, ke) : ke;
-#pragma unroll 4
-                        for (int k = k0; k < k1; ++k) {
-                            const PosRec<real> rj = a.rec[k];
-                            const real ddx = (rj.x + ox) - ri.x, ddy = (rj.y + oy) - ri.y, ddz = (rj.z + oz) - ri.z;
-                            const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            const real cR2 = T == 1 ? cR1 : cutR[rj.t];
-                            const real cA2 = T == 1 ? cA1 : cutA[rj.t];
-                            const uint32_t ent = (uint32_t)k | code;
-                            if (r2 < cR2) {
-                                if (nr < a.mnR) a.nlR[(size_t)nr * a.n + i] = ent;
-                                ++nr;
-                            }
-                            if (r2 < cA2) {
-                                if (na < a.mnA) a.nlA[(size_t)na * a.n + i] = ent;
-                                ++na;
-                            }
-                        }
+                    // i itself (zero offset) is the one candidate at r = 0 to leave out
+                    const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
+                    // branch-free body: the tests predicate the stores and the counts
+#pragma unroll 2
+                    for (int k = kb; k < ke; ++k) {
+                        const PosRec<real> rj = a.rec[k];
+                        const real ddx = (rj.x + ox) - ri.x, ddy = (rj.y + oy) - ri.y, ddz = (rj.z + oz) - ri.z;
+                        const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        const real cR2 = T == 1 ? cR1 : cutR[rj.t];
+                        const real cA2 = T == 1 ? cA1 : cutA[rj.t];
+                        const uint32_t ent = (uint32_t)k | code;
+                        const bool other = k != self;
+                        const bool inR = (r2 < cR2) & other, inA = (r2 < cA2) & other;
+                        if (inR & (nr < a.mnR)) a.nlR[(size_t)nr * a.n + i] = ent;
+                        if (inA & (na < a.mnA)) a.nlA[(size_t)na * a.n + i] = ent;
+                        nr += inR;
+                        na += inA;
                     }
                 }
             }
