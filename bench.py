@@ -6,9 +6,11 @@ system, reported as bead-steps/s and ns/day.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one velocity-Verlet step of the whole system.  Timed region: K steps, each
-bracketed by CUDA events on the launch stream, with a 256 MiB write between steps to
-flush the 126 MB L2 (the step's working set, ~115 MB, is smaller than L2).  Inputs are
-resident in HBM before timing.  With N > 1 (torchrun) every rank runs an independent
+one library call that replays the step's captured CUDA graph, bracketed by CUDA events
+on the launch stream, with a 256 MiB write between steps to flush the 126 MB L2 (the
+step's working set is smaller than L2).  Inputs are resident in HBM before timing.
+Per-stage times come from a second pass of K steps launched eagerly with CUDA events
+between the stages.  With N > 1 (torchrun) every rank runs an independent
 replica (the method shards by independent systems; no collective on the data path);
 value = all ranks' bead-steps / the slowest rank's time.
 
@@ -281,12 +283,13 @@ def run_ours(args):
     pairs_r, pairs_a = int(cnt_r.sum()), int(cnt_a.sum())
 
     step(k=0, fv=0)  # initial forces
-    binding.nep_set_timing(m.h, 1)
+    # timed steps: each one nep_md_step call of one step, which replays the
+    # handle's captured graph of the step's kernels; L2 flushed before each
+    binding.nep_set_timing(m.h, 0)
     for _ in range(args.warmup):
         flush.zero_()
         step()
     binding.nep_sync(m.h)
-    binding.nep_set_timing(m.h, 1)  # reset the stage sums
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = Clocks(local)
     if dist:
@@ -304,6 +307,13 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
+    # per-stage device times: the same steps again, launched eagerly with CUDA
+    # events between the stages on the launch stream (L2 flushed before each step)
+    binding.nep_set_timing(m.h, 1)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    binding.nep_sync(m.h)
     stages, tsteps = binding.nep_get_timing(m.h)
     binding.nep_set_timing(m.h, 0)
     if dist:
@@ -423,6 +433,9 @@ def run_ours(args):
             "ns_per_day": (1000.0 / ms_step) * DT_FS * 0.0864,
             "gpu_launches": 11 * args.steps,  # per step: kick/drift, 5 cell-build, neighbours, descriptor, force, force outputs, kick
             "stages_ms_per_step": {k: v / max(1, tsteps) for k, v in stages.items()},
+            "stages_how": "separate pass of the same number of steps, eager launches, CUDA events between "
+                          "stages on the launch stream, L2 flushed before each step; force_virial is the force "
+                          "kernel plus its output kernel",
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
             "steady_state_graph": steady, "plain_fp64": plain, "serving": serve}
