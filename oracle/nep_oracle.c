@@ -31,8 +31,9 @@
  *   - j != i excludes only the zero-shift self image; periodic images of i count.
  *   - Descriptor order: q_0..q_{n_R-1}, then for l = 1..l_max, n = 0..n_A-1: q_nl.
  *   - Every parameter is per central type t_i; c is indexed (t_i, t_j).
- *   - Positions on periodic axes are wrapped to [0, L) by x - L floor(x / L)
- *     (a result equal to L becomes 0) before neighbours are searched.
+ *   - Positions on periodic axes are wrapped to [0, L) before neighbours are
+ *     searched: a position in [0, L) is kept, any other becomes x - L floor(x / L)
+ *     (a result that rounds to L, or below 0, becomes 0).
  *
  * Forces are the analytic gradient F_k = -dE/dr_k.  The angular part of that
  * gradient is taken from the addition-theorem form of q_nl,
@@ -209,6 +210,7 @@ typedef struct {
 
 static double wrap1(double x, double L)
 {
+    if (x >= 0.0 && x < L) return x;  /* inside the box: kept */
     double w = x - L * floor(x / L);
     if (w >= L) w = 0.0;
     if (w < 0.0) w = 0.0;

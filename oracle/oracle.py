@@ -241,9 +241,10 @@ def wrap(system):
     for a in range(3):
         if system.pbc[a]:
             L_ = system.box[a]
+            inside = (pos[a] >= 0.0) & (pos[a] < L_)
             w = pos[a] - L_ * np.floor(pos[a] / L_)
             w[(w >= L_) | (w < 0.0)] = 0.0
-            pos[a] = w
+            pos[a] = np.where(inside, pos[a], w)
     return pos
 
 

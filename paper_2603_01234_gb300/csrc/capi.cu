@@ -232,6 +232,7 @@ int make_grid(const nep_model* m, double rc_max, const double box[3], const int3
         if (nc > 1024) nc = 1024;
         g.nc[a] = nc;
         g.len[a] = box[a] / nc;
+        g.inv_len[a] = 1.0 / g.len[a];
         if (g.pbc[a]) {
             int S = (int)ceil(rc_max / g.len[a] - 1e-12);
             if (S < 1) S = 1;

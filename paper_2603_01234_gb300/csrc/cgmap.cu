@@ -36,10 +36,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_map(int n_cg, int n_aa, const int
         }
         for (int a = 0; a < 3; ++a) {
             double x = ref[a] + acc[a] / msum;
-            if (g.pbc[a]) {
-                x = x - g.box[a] * floor(x / g.box[a]);
-                if (x >= g.box[a] || x < 0.0) x = 0.0;
-            }
+            if (g.pbc[a]) x = wrap_periodic(x, g.box[a]);
             bpos[(size_t)a * n_cg + I] = x;
         }
     }

@@ -37,12 +37,8 @@ __global__ void __launch_bounds__(kBlock) k_kick_drift(int n, const int* __restr
         const size_t k = (size_t)a * n + i;
         const double v = vel[k] + half_dt * force[k] * im;
         vel[k] = v;
-        double x = pos[k] + dt * v;
-        if (g.pbc[a]) {
-            x = x - g.box[a] * floor(x / g.box[a]);
-            if (x >= g.box[a] || x < 0.0) x = 0.0;
-        }
-        pos[k] = x;
+        const double x = pos[k] + dt * v;
+        pos[k] = g.pbc[a] ? wrap_periodic(x, g.box[a]) : x;
     }
 }
 

@@ -35,11 +35,8 @@ __global__ void __launch_bounds__(kBlock) k_bin(const WorkItem* __restrict__ ite
             atomicOr(err, 1);
             x = 0.0;
         }
-        if (g.pbc[a]) {
-            x = x - g.box[a] * floor(x / g.box[a]);
-            if (x >= g.box[a] || x < 0.0) x = 0.0;
-        }
-        double cf = floor(x / g.len[a]);
+        if (g.pbc[a]) x = wrap_periodic(x, g.box[a]);
+        const double cf = floor(x * g.inv_len[a]);
         int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
         c3[a] = c;
         xr[a] = (real)(x - (double)c * g.len[a]);

@@ -48,9 +48,21 @@ struct CellGrid {
     int S[3];       // search range in cells per axis
     int pbc[3];
     int ncell;
-    double len[3];  // cell side
+    double len[3];      // cell side
+    double inv_len[3];  // 1 / len (cell index by multiplication)
     double box[3];
 };
+
+// Wrap onto a periodic axis of length L: positions already in [0, L) are kept;
+// others become x - L floor(x / L), and a result that rounds to L (or below 0)
+// becomes 0.  Moving particles leave the box rarely, so the FP64 division (slow
+// on this GPU) runs only for the few outside.
+__host__ __device__ inline double wrap_periodic(double x, double L)
+{
+    if (x >= 0.0 && x < L) return x;
+    x = x - L * floor(x / L);
+    return (x >= L || x < 0.0) ? 0.0 : x;
+}
 
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
