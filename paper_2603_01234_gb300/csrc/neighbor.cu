@@ -227,6 +227,9 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         const real cR1 = cutR[0], cA1 = cutA[0];  // the one pair type of a one-type model
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
         const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
+        const size_t stride = (size_t)a.n;
+        uint32_t* outR = a.nlR + i;  // next slot of each list (column i, slot-major)
+        uint32_t* outA = a.nlA + i;
         for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
             int z = cz + dz;
             if (g.pbc[2]) {  // |dz| <= 2, so at most two corrections even for one cell per axis
@@ -252,7 +255,8 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
                         continue;
                     }
                     const int cell = q.cell_base + (z * ncy + y) * ncx + x;
-                    const real ox = (real)dx * lx, oy = (real)dy * ly, oz = (real)dz * lz;
+                    // j's position relative to i is (r_j + offset) - r_i = r_j - b
+                    const real bx = ri.x - (real)dx * lx, by = ri.y - (real)dy * ly, bz = ri.z - (real)dz * lz;
                     const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
                     const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
                     // i itself (zero offset) is the one candidate at r = 0 to leave out
@@ -261,15 +265,17 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 #pragma unroll 2
                     for (int k = kb; k < ke; ++k) {
                         const PosRec<real> rj = a.rec[k];
-                        const real ddx = (rj.x + ox) - ri.x, ddy = (rj.y + oy) - ri.y, ddz = (rj.z + oz) - ri.z;
+                        const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
                         const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                         const real cR2 = T == 1 ? cR1 : cutR[rj.t];
                         const real cA2 = T == 1 ? cA1 : cutA[rj.t];
                         const uint32_t ent = (uint32_t)k | code;
                         const bool other = k != self;
                         const bool inR = (r2 < cR2) & other, inA = (r2 < cA2) & other;
-                        if (inR & (nr < a.mnR)) a.nlR[(size_t)nr * a.n + i] = ent;
-                        if (inA & (na < a.mnA)) a.nlA[(size_t)na * a.n + i] = ent;
+                        if (inR & (nr < a.mnR)) *outR = ent;
+                        if (inA & (na < a.mnA)) *outA = ent;
+                        outR += inR ? stride : 0;
+                        outA += inA ? stride : 0;
                         nr += inR;
                         na += inA;
                     }
