@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
                     // branch-free body: the tests predicate the stores and the counts
 #pragma unroll 2
                     for (int k = kb; k < ke; ++k) {
-                        const PosRec<real> rj = a.rec[k];
+                        const PosRec<real> rj = ldg_rec(a.rec + k);
                         const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
                         const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                         const real cR2 = T == 1 ? cR1 : cutR[rj.t];

@@ -42,6 +42,32 @@ struct alignas(4 * sizeof(real)) PosRec {
     int t;
 };
 
+static_assert(sizeof(PosRec<float>) == 16 && sizeof(PosRec<double>) == 32, "record layout");
+
+// A record through the read-only data path (the records do not change while a
+// kernel reads them).
+__device__ __forceinline__ PosRec<float> ldg_rec(const PosRec<float>* p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    PosRec<float> r;
+    r.x = v.x;
+    r.y = v.y;
+    r.z = v.z;
+    r.t = __float_as_int(v.w);
+    return r;
+}
+__device__ __forceinline__ PosRec<double> ldg_rec(const PosRec<double>* p)
+{
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    PosRec<double> r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.t = (int)(unsigned int)(__double_as_longlong(b.y) & 0xffffffffll);  // t is the word's low half
+    return r;
+}
+
 // Cell grid of one configuration.
 struct CellGrid {
     int nc[3];      // cells per axis
