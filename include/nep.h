@@ -60,6 +60,13 @@ extern "C" {
 #define NEP_FP64 0  /* every step in double precision: the plain reference form */
 #define NEP_FP32 1  /* FP32 descriptors, network and pair forces; FP64 reductions,
                        positions, velocities and integration */
+#define NEP_FP32_BF16 2  /* NEP_FP32 with BF16 hidden-layer weights: W0 (Eq. 2) is rounded
+                            to BF16 once, and both products of the hidden layer (the
+                            pre-activations W0 q and dU/dq = W0^T (w1 (1 - h^2))) run on
+                            tensor cores with each activation split into two BF16 terms
+                            and FP32 accumulation.  The results are the FP32 form's for
+                            the model with BF16-rounded W0, and forces stay the gradient
+                            of its energy. */
 
 /* memory kind of the caller's particle arrays */
 #define NEP_HOST 0
@@ -91,7 +98,7 @@ const char* nep_last_error(void);
  *   w0[T][H][N_des], b0[T][H], w1[T][H], b1[T]            per-type network (Eq. 2)
  *     with N_des = n_R + n_A * l_max, descriptor order q_0..q_{n_R-1}, then for
  *     l = 1..l_max, n = 0..n_A-1: q_nl.
- *   precision          NEP_FP64 or NEP_FP32
+ *   precision          NEP_FP64, NEP_FP32 or NEP_FP32_BF16
  * All arrays are host memory, row-major double, read during the call only.
  * Returns NEP_ERR_UNSUPPORTED for (n_R, n_A, K_R, K_A, l_max) without a compiled
  * kernel; the compiled set is listed by nep_supported_shape().

@@ -27,6 +27,8 @@ NEP_ERR_CUDA = -6
 NEP_ERR_UNSUPPORTED = -7
 NEP_FP64 = 0
 NEP_FP32 = 1
+NEP_FP32_BF16 = 2
+PRECISIONS = {"fp64": NEP_FP64, "fp32": NEP_FP32, "bf16": NEP_FP32_BF16}
 NEP_HOST = 0
 NEP_DEVICE = 1
 
@@ -394,13 +396,14 @@ def nep_set_capacity(h, radial, angular):
 
 # ---- convenience wrapper -------------------------------------------------------
 class Model:
-    """A model handle.  precision: "fp32" or "fp64"."""
+    """A model handle.  precision: "fp32", "fp64" or "bf16" (FP32 with BF16
+    hidden-layer weights W0 and the hidden layer's products on tensor cores)."""
 
     def __init__(self, params, precision="fp32", device=0):
         self.params = params
         self.precision = precision
         self.device = device
-        self.h = nep_create(params, NEP_FP64 if precision == "fp64" else NEP_FP32, device)
+        self.h = nep_create(params, PRECISIONS[precision], device)
 
     def close(self):
         if self.h:

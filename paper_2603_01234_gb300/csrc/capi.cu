@@ -375,7 +375,7 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
     NEP_TRY(m->phi.ensure(rs * 24 * phi_pad(m->nA) * (size_t)n));
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
-    if (m->precision == NEP_FP32) NEP_TRY(m->acc.ensure(sizeof(unsigned long long) * 16 * (size_t)n));
+    if (m->precision != NEP_FP64) NEP_TRY(m->acc.ensure(sizeof(unsigned long long) * 16 * (size_t)n));
     NEP_TRY(m->partial2.ensure(sizeof(double) * 6 * ((n + kBlock - 1) / kBlock)));
     NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
     const size_t old_req = m->counters.cap / sizeof(unsigned int);
@@ -486,6 +486,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.e = m->e.as<real>();
     a.e_stride = p.Tmax * m->KRP;
     a.phi = m->phi.as<real>();
+    a.net_bf16 = m->precision == NEP_FP32_BF16;
     a.perm = m->perm.as<int>();
     a.force = force;
     a.virial = virial;
@@ -645,7 +646,7 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
 template <typename real>
 int autotune_plan(nep_model* m, const Plan& p, double* force_d)
 {
-    if (m->precision != NEP_FP32) return NEP_OK;  // one FP64 variant only
+    if (m->precision == NEP_FP64) return NEP_OK;  // one FP64 variant only
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     NEP_CUDA(cudaEventCreate(&e0));
     NEP_CUDA(cudaEventCreate(&e1));
@@ -1209,7 +1210,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     *out = nullptr;
     if (n_types < 1 || n_types > kMaxTypes) return fail(NEP_ERR_ARG, "n_types out of range [1, 16]");
     if (hidden < 1 || hidden > 4096) return fail(NEP_ERR_ARG, "hidden out of range");
-    if (precision != NEP_FP32 && precision != NEP_FP64) return fail(NEP_ERR_ARG, "unknown precision");
+    if (precision != NEP_FP32 && precision != NEP_FP64 && precision != NEP_FP32_BF16)
+        return fail(NEP_ERR_ARG, "unknown precision");
     if (!rc_radial || !rc_angular || !c_radial || !c_angular || !w0 || !b0 || !w1 || !b1)
         return fail(NEP_ERR_ARG, "null parameter array");
     if (!nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
@@ -1261,6 +1263,13 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.b0 = p; p += T * hidden;
     o.w1 = p; p += T * hidden;
     o.b1 = p; p += T;
+    o.w0f = o.w0b = -1;
+    const int nd = m->ND, hp = net_hp(hidden);
+    if (precision == NEP_FP32_BF16) {  // BF16 copies of W0 laid out as MMA B operands
+        p = (p + 3) & ~3;              // 16-byte aligned
+        o.w0f = p; p += T * hp * net_sf(nd) / 2;
+        o.w0b = p; p += T * net_ndp(nd) * (hp + 8) / 2;
+    }
     o.total = p;
     std::vector<double> h(p);
     for (int k = 0; k < TT; ++k) {
@@ -1286,10 +1295,34 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
     } else {
         std::vector<float> hf(h.begin(), h.end());
+        if (precision == NEP_FP32_BF16) {
+            // W0[t][mu][v] rounded to FP32 and then to BF16 (round to nearest even)
+            auto bf16 = [](double x) -> uint16_t {
+                const float f = (float)x;
+                uint32_t u;
+                memcpy(&u, &f, 4);
+                if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0;  // NaN
+                u += 0x7fffu + ((u >> 16) & 1u);
+                return (uint16_t)(u >> 16);
+            };
+            const int sf = net_sf(nd), ndp = net_ndp(nd), sb = hp + 8;
+            std::vector<uint16_t> wf((size_t)T * hp * sf, 0), wb((size_t)T * ndp * sb, 0);
+            for (int t = 0; t < T; ++t)
+                for (int mu = 0; mu < hidden; ++mu)
+                    for (int v = 0; v < nd; ++v) {
+                        const uint16_t b = bf16(w0[((size_t)t * hidden + mu) * nd + v]);
+                        wf[((size_t)t * hp + mu) * sf + v] = b;   // [t][mu][v]: X = Q W0^T
+                        wb[((size_t)t * ndp + v) * sb + mu] = b;  // [t][v][mu]: dQ = D W0
+                    }
+            memcpy(hf.data() + o.w0f, wf.data(), wf.size() * 2);
+            memcpy(hf.data() + o.w0b, wb.data(), wb.size() * 2);
+        }
         if (cudaMemcpy(m->params.p, hf.data(), sizeof(float) * p, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
     }
     m->smem_desc = m->real_size * o.total;
+    if (precision == NEP_FP32_BF16)  // plus the per-warp scratch of the network products
+        m->smem_desc = ((m->smem_desc + 15) & ~(size_t)15) + (size_t)(kBlock / 32) * net_scratch(nd);
     // the force kernel stages the cutoff + coefficient prefix only
     m->smem_force = m->real_size * o.n_cut_coef;
     if (m->smem_desc > 200 * 1024 || m->smem_force > 200 * 1024)
@@ -1800,6 +1833,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.e = (real*)(base + L.e);
     a.e_stride = m->T * m->KRP;
     a.phi = (real*)(base + L.phi);
+    a.net_bf16 = m->precision == NEP_FP32_BF16;
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;

@@ -22,6 +22,8 @@
 // For the reverse pair, u -> -u gives Y(-u) = (-1)^l Y(u) and
 // grad Y(-u) = (-1)^(l-1) grad Y(u), so f_ji is the same contraction with
 // Phi_j scaled by (-1)^l, negated.
+#include <cuda_bf16.h>
+
 #include "nep_common.cuh"
 #include "sh_poly.cuh"
 
@@ -173,7 +175,209 @@ __device__ __forceinline__ void stage_params(const real* __restrict__ src, real*
     __syncthreads();
 }
 
-template <typename real, int NR, int NA, int KR, int KA, int MB>
+// ---- the hidden layer (Eq. 2) on tensor cores with BF16 weights -----------------
+// A warp evaluates the network of its 32 particles (one per lane) as
+//   X = Q W0^T       (32 x ND by ND x H: the hidden pre-activations)
+//   dQ = D W0        (32 x H by H x ND: dU/dq, D = w1 (1 - h^2))
+// with mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  W0 is rounded to
+// BF16 once, on the host; each activation (Q, D) is split into a BF16 head and a
+// BF16 tail (x = hi + lo, exact to about 2^-16 relative) and multiplied as two
+// products, so the result is the FP32 evaluation of the model with BF16 weights
+// and the forces stay the gradient of its energy.  Q is transposed into fragment
+// order through a warp-private shared tile; the FP32 accumulators of X are exactly
+// the A fragments of the D product, so D never leaves registers; dQ comes back to
+// the lanes through the same tile.  Particles of a type other than t are masked
+// out of type t's products.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// (x0, x1) as packed BF16 heads and packed BF16 tails: x = head + tail
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& head, uint32_t& tail)
+{
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    head = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
+    tail = pack_bf16(x0 - __bfloat162float(h0), x1 - __bfloat162float(h1));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int ND>
+__device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off, int T, int H, int ti,
+                                         const float (&q)[ND], float& U, float (&dq)[ND], unsigned char* scratch)
+{
+    constexpr int KPF = net_kpf(ND), SF = net_sf(ND), NDP = net_ndp(ND), KS = KPF / 16, NB = NDP / 8;
+    constexpr int QT = 32 * (SF / 2);  // words of one Q tile
+    const int HP = net_hp(H), SB = HP + 8;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    uint32_t* Qw = reinterpret_cast<uint32_t*>(scratch);  // [2 (head, tail)][32][SF / 2] words
+#pragma unroll
+    for (int v = 0; v < KPF / 2; ++v) {
+        uint32_t hd, tl;
+        split_bf16(2 * v < ND ? q[2 * v] : 0.f, 2 * v + 1 < ND ? q[2 * v + 1] : 0.f, hd, tl);
+        Qw[lane * (SF / 2) + v] = hd;
+        Qw[QT + lane * (SF / 2) + v] = tl;
+    }
+    __syncwarp();
+    uint32_t af[2][2][KS][4];  // [head/tail][m tile][k step]
+#pragma unroll
+    for (int pt = 0; pt < 2; ++pt)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const int r0 = 16 * mt + g;
+                const uint32_t* Qp = Qw + pt * QT;
+                af[pt][mt][kk][0] = Qp[r0 * (SF / 2) + 8 * kk + c];
+                af[pt][mt][kk][1] = Qp[(r0 + 8) * (SF / 2) + 8 * kk + c];
+                af[pt][mt][kk][2] = Qp[r0 * (SF / 2) + 8 * kk + 4 + c];
+                af[pt][mt][kk][3] = Qp[(r0 + 8) * (SF / 2) + 8 * kk + 4 + c];
+            }
+    __syncwarp();  // the tile is reused for dQ below
+    int rt[2][2];  // types of this lane's fragment rows 16 mt + g + 8 h
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) rt[mt][h] = __shfl_sync(FULL, ti, 16 * mt + g + 8 * h);
+    const uint16_t* W0f = reinterpret_cast<const uint16_t*>(P + off.w0f);
+    const uint16_t* W0b = reinterpret_cast<const uint16_t*>(P + off.w0b);
+    const float* b0 = P + off.b0;
+    const float* w1 = P + off.w1;
+    float up[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    float dacc[2][NB][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dacc[mt][nb][e] = 0.f;
+    for (int ch = 0; ch < HP / 16; ++ch) {  // 16 hidden units at a time
+        float x[2][2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[mt][nl][e] = 0.f;
+        for (int t = 0; t < T; ++t) {
+            if (T > 1 && !__any_sync(FULL, ti == t)) continue;
+            const uint32_t* Wf = reinterpret_cast<const uint32_t*>(W0f + (size_t)t * HP * SF);
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl) {
+                const int nrow = 16 * ch + 8 * nl + g;  // hidden unit of this lane's B column
+                uint32_t b[KS][2];
+#pragma unroll
+                for (int kk = 0; kk < KS; ++kk) {
+                    b[kk][0] = Wf[nrow * (SF / 2) + 8 * kk + c];
+                    b[kk][1] = Wf[nrow * (SF / 2) + 8 * kk + 4 + c];
+                }
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int kk = 0; kk < KS; ++kk) {
+                        mma_bf16(acc, af[1][mt][kk], b[kk][0], b[kk][1]);  // tails first (smaller)
+                        mma_bf16(acc, af[0][mt][kk], b[kk][0], b[kk][1]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (T == 1 || rt[mt][e >> 1] == t) x[mt][nl][e] = acc[e];
+                }
+            }
+        }
+        // h = tanh(x - b0), the energy terms, and D = w1 (1 - h^2) in A-fragment order
+        uint32_t ca[2][2][4];  // [head/tail][m tile]
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float d[2][4];
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = 16 * ch + 8 * nl + 2 * c + (e & 1);
+                    const int t = rt[mt][e >> 1];
+                    float coef = 0.f;
+                    if (col < H) {
+                        const float h = tanhf(x[mt][nl][e] - b0[t * H + col]);
+                        const float w = w1[t * H + col];
+                        up[mt][e >> 1] += w * h;
+                        coef = w * (1.f - h * h);
+                    }
+                    d[nl][e] = coef;
+                }
+            split_bf16(d[0][0], d[0][1], ca[0][mt][0], ca[1][mt][0]);
+            split_bf16(d[0][2], d[0][3], ca[0][mt][1], ca[1][mt][1]);
+            split_bf16(d[1][0], d[1][1], ca[0][mt][2], ca[1][mt][2]);
+            split_bf16(d[1][2], d[1][3], ca[0][mt][3], ca[1][mt][3]);
+        }
+        for (int t = 0; t < T; ++t) {
+            if (T > 1 && !__any_sync(FULL, ti == t)) continue;
+            const uint32_t* Wb = reinterpret_cast<const uint32_t*>(W0b + (size_t)t * NDP * SB);
+            uint32_t cm[2][2][4];
+#pragma unroll
+            for (int pt = 0; pt < 2; ++pt)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    const bool k0 = T == 1 || rt[mt][0] == t, k1 = T == 1 || rt[mt][1] == t;
+                    cm[pt][mt][0] = k0 ? ca[pt][mt][0] : 0u;
+                    cm[pt][mt][1] = k1 ? ca[pt][mt][1] : 0u;
+                    cm[pt][mt][2] = k0 ? ca[pt][mt][2] : 0u;
+                    cm[pt][mt][3] = k1 ? ca[pt][mt][3] : 0u;
+                }
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) {
+                const int vrow = 8 * nb + g;  // descriptor index of this lane's B column
+                const uint32_t bb0 = Wb[vrow * (SB / 2) + 8 * ch + c], bb1 = Wb[vrow * (SB / 2) + 8 * ch + 4 + c];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(dacc[mt][nb], cm[1][mt], bb0, bb1);
+                    mma_bf16(dacc[mt][nb], cm[0][mt], bb0, bb1);
+                }
+            }
+        }
+    }
+    // U: sum the quad's partial sums, then each lane takes its own row's
+    float rs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float v = up[k >> 1][k & 1];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        rs[k] = v;  // row 16 (k >> 1) + 8 (k & 1) + g
+    }
+    float mine = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float v = __shfl_sync(FULL, rs[k], 4 * (lane & 7));
+        if ((lane >> 3) == k) mine = v;
+    }
+    U = mine - P[off.b1 + ti];
+    // dQ back to one row per lane
+    float* Dw = reinterpret_cast<float*>(scratch);  // [32][NDP + 1]
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                Dw[(16 * mt + g + 8 * (e >> 1)) * (NDP + 1) + 8 * nb + 2 * c + (e & 1)] = dacc[mt][nb][e];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < ND; ++v) dq[v] = Dw[lane * (NDP + 1) + v];
+    __syncwarp();
+}
+
+template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descriptor(EvalArgs<real> a)
 {
     constexpr int ND = NR + NA * 4;
@@ -185,9 +389,12 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
     stage_params(md.params, P, off.total);
-    const int i = it.begin + threadIdx.x;
-    if (i >= it.end) return;
-    if (a.acc) {  // the scatter accumulators of i start the force pass at zero
+    // NET = 1 evaluates the network warp-wide: a lane past the item's end follows
+    // the item's last particle and writes nothing
+    const bool live = NET == 0 || it.begin + (int)threadIdx.x < it.end;
+    const int i = live ? it.begin + threadIdx.x : it.end - 1;
+    if (NET == 0 && i >= it.end) return;
+    if (live && a.acc) {  // the scatter accumulators of i start the force pass at zero
         ulonglong2* z = reinterpret_cast<ulonglong2*>(a.acc + (size_t)i * 16);
 #pragma unroll
         for (int k = 0; k < 6; ++k) z[k] = make_ulonglong2(0ull, 0ull);
@@ -287,22 +494,30 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         for (int k = 0; k < kNLM; ++k) q[NR + (l_of(k) - 1) * NA + nn] += A[nn][k] * A[nn][k];
 
     // ---- network (Eq. 2) and dU/dq ----
-    const real* w0 = P + off.w0 + ti * H * ND;
-    const real* b0 = P + off.b0 + ti * H;
-    const real* w1 = P + off.w1 + ti * H;
-    real U = -P[off.b1 + ti];
+    real U;
     real dq[ND];
+    if constexpr (NET == 1) {
+        unsigned char* scratch = smem_raw + (((size_t)off.total * sizeof(real) + 15) & ~(size_t)15) +
+                                 (size_t)(threadIdx.x >> 5) * net_scratch(ND);
+        net_bf16<ND>(P, off, T, H, ti, q, U, dq, scratch);
+        if (!live) return;
+    } else {
+        const real* w0 = P + off.w0 + ti * H * ND;
+        const real* b0 = P + off.b0 + ti * H;
+        const real* w1 = P + off.w1 + ti * H;
+        U = -P[off.b1 + ti];
 #pragma unroll
-    for (int v = 0; v < ND; ++v) dq[v] = real(0);
-    for (int mu = 0; mu < H; ++mu) {
-        real x = -b0[mu];
+        for (int v = 0; v < ND; ++v) dq[v] = real(0);
+        for (int mu = 0; mu < H; ++mu) {
+            real x = -b0[mu];
 #pragma unroll
-        for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
-        const real h = tanh(x);
-        U += w1[mu] * h;
-        const real coef = w1[mu] * (real(1) - h * h);
+            for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
+            const real h = tanh(x);
+            U += w1[mu] * h;
+            const real coef = w1[mu] * (real(1) - h * h);
 #pragma unroll
-        for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
+            for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
+        }
     }
     a.U[i] = U;
     // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
@@ -827,6 +1042,11 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
         cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_>,                         \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
         if (e != cudaSuccess) return e;                                                                       \
+        if constexpr (sizeof(real) == 4) {                                                                    \
+            e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 1>,                              \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);            \
+            if (e != cudaSuccess) return e;                                                                   \
+        }                                                                                                     \
         if constexpr (sizeof(real) == 4)                                                                      \
             e = cudaFuncSetAttribute(k_force_scatter<real, a_, b_, c_, d_, mb_>,                              \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
@@ -857,8 +1077,16 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
     }
 #define NEP_CASE(a_, b_, c_, d_)                                                                            \
     if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                     \
-        if (mb_desc == 2) k_descriptor<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_desc, st>>>(a);          \
-        else k_descriptor<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_desc, st>>>(a);                       \
+        if (sizeof(real) == 4 && a.net_bf16) {                                                              \
+            if constexpr (sizeof(real) == 4) {                                                              \
+                if (mb_desc == 2) k_descriptor<real, a_, b_, c_, d_, 2, 1><<<nb, kBlock, smem_desc, st>>>(a); \
+                else k_descriptor<real, a_, b_, c_, d_, 3, 1><<<nb, kBlock, smem_desc, st>>>(a);            \
+            }                                                                                               \
+        } else if (mb_desc == 2) {                                                                          \
+            k_descriptor<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_desc, st>>>(a);                        \
+        } else {                                                                                            \
+            k_descriptor<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_desc, st>>>(a);                        \
+        }                                                                                                   \
         if (mid) cudaEventRecord(mid, st);                                                                  \
         if constexpr (sizeof(real) == 4) {                                                                  \
             if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \

@@ -24,6 +24,20 @@ constexpr int kMaxTypes = 16;
 constexpr int kBlock = 128;          // threads per block = particles per work item
 constexpr int kScanItems = 4096;     // cells per block of the scan
 
+// BF16 network tables (the hidden layer as two tensor-core products per warp of
+// 32 particles): padded sizes in BF16 elements.
+__host__ __device__ constexpr int net_kpf(int nd) { return (nd + 15) & ~15; }  // K of X = Q W0^T
+__host__ __device__ constexpr int net_sf(int nd) { return net_kpf(nd) + 8; }    // row stride (bank spread)
+__host__ __device__ constexpr int net_ndp(int nd) { return (nd + 7) & ~7; }     // N of dQ = D W0
+__host__ __device__ constexpr int net_hp(int h) { return (h + 15) & ~15; }       // N of X, K of dQ
+// per-warp shared scratch of the BF16 network, bytes
+__host__ __device__ constexpr int net_scratch(int nd)
+{
+    // two BF16 tiles of Q (head, tail), later one FP32 tile of dQ
+    return (2 * 32 * net_sf(nd) * 2 > 32 * (net_ndp(nd) + 1) * 4 ? 2 * 32 * net_sf(nd) * 2
+                                                                   : 32 * (net_ndp(nd) + 1) * 4);
+}
+
 // Row length of Phi_i per harmonic component: n_A padded to a multiple of 4 so that
 // every row starts on a 16-byte boundary (vector loads).
 __host__ __device__ constexpr int phi_pad(int nA) { return (nA + 3) & ~3; }
@@ -95,6 +109,8 @@ struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
     int cR, cA;                 // [T][T][nR][KR], [T][T][nA][KA]
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
+    int w0f, w0b;               // BF16-weight network form: W0 as BF16 MMA operands (-1 when absent),
+                                // [T][net_hp(H)][net_sf(ND)] and [T][net_ndp(ND)][net_hp(H) + 8]
     int n_cut_coef;             // elements of the cutoff + coefficient prefix
     int total;                  // all elements
 };
@@ -152,6 +168,7 @@ struct EvalArgs {
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
     real* phi;                  // [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
+    int net_bf16;               // 1: the hidden layer's products in BF16 on tensor cores
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null
