@@ -239,6 +239,23 @@ def run_reference(args):
     return 0
 
 
+# ---- replicas ---------------------------------------------------------------------
+def replica_throughput(ms_local, units_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas (one per rank): the units all
+    ranks processed divided by the slowest rank's time.  Returns (units per second,
+    job ms).  With dist (an initialised torch.distributed), every rank gets the same
+    answer."""
+    import torch
+    ms, units = float(ms_local), float(units_local)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), float(u.item())
+    return units / (ms / 1000.0), ms
+
+
 # ---- our arm --------------------------------------------------------------------
 def run_ours(args):
     import torch
@@ -316,11 +333,7 @@ def run_ours(args):
     binding.nep_sync(m.h)
     stages, tsteps = binding.nep_get_timing(m.h)
     binding.nep_set_timing(m.h, 0)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms / 1000.0)
+    value, ms = replica_throughput(ms, n * args.steps, dist, dev)
     ms_step = ms / args.steps
 
     # steady state: the same steps back to back through the graph-captured loop
