@@ -487,7 +487,6 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.e_stride = p.Tmax * m->KRP;
     a.phi = m->phi.as<real>();
     a.net_bf16 = m->precision == NEP_FP32_BF16;
-    a.err = m->flags.as<int>() + 2;
     a.perm = m->perm.as<int>();
     a.force = force;
     a.virial = virial;
@@ -627,9 +626,7 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
         if (site_energy)
             NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
         NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
-        NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
         NEP_TRY(leave(m, stream));
-        if (m->h_flags[2] & 4) return fail(NEP_ERR_TIMEOUT, "a tensor-core wait in the network ran out");
         if (energy_total) *energy_total = m->h_totals[0];
         if (virial_total)
             for (int k = 0; k < 9; ++k) virial_total[k] = m->h_totals[1 + k];
@@ -778,7 +775,6 @@ int inspect_async(nep_model* m, bool wait)
         // a later call on this stream runs after the current work; reset the words there
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->async_stream));
     }
-    if (err & 4) return fail(NEP_ERR_TIMEOUT, "a tensor-core wait in the network ran out during MD");
     if (err) return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
     if (grow_now) {
         const bool overflow = needR > m->mnR || needA > m->mnA;
@@ -1129,9 +1125,7 @@ int batch_impl(nep_model* const* models, int n_models, int n_req, const int32_t*
         if (site_energy)
             NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
         NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10 * n_req, cudaMemcpyDeviceToHost, m->cur));
-        NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
         NEP_TRY(leave(m, stream));
-        if (m->h_flags[2] & 4) return fail(NEP_ERR_TIMEOUT, "a tensor-core wait in the network ran out");
         for (int r = 0; r < n_req; ++r) {
             if (energy) energy[r] = m->h_totals[10 * r];
             if (virial_total)
@@ -1223,8 +1217,6 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     if (!nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
         return fail(NEP_ERR_UNSUPPORTED, "no compiled kernel for these descriptor / basis sizes");
     const int T = n_types;
-    if (precision == NEP_FP32_BF16 && tc_cols(T, hidden) > 512)
-        return fail(NEP_ERR_UNSUPPORTED, "BF16 form: types x padded hidden width exceeds 512 tensor-memory columns");
     for (int a = 0; a < T; ++a)
         for (int b = 0; b < T; ++b) {
             const double r1 = rc_radial[a * T + b], r2 = rc_angular[a * T + b];
@@ -1272,11 +1264,11 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.w1 = p; p += T * hidden;
     o.b1 = p; p += T;
     o.w0f = o.w0b = -1;
-    const int nd = m->ND, hp = net_hp(hidden), kpf = net_kpf(nd);
-    if (precision == NEP_FP32_BF16) {  // BF16 copies of W0 as tensor-core operand tiles
+    const int nd = m->ND, hp = net_hp(hidden);
+    if (precision == NEP_FP32_BF16) {  // BF16 copies of W0 laid out as MMA B operands
         p = (p + 3) & ~3;              // 16-byte aligned
-        o.w0f = p; p += T * hp * kpf * 2 / 4;
-        o.w0b = p; p += T * 32 * hp * 2 / 4;
+        o.w0f = p; p += T * hp * net_sf(nd) / 2;
+        o.w0b = p; p += T * net_ndp(nd) * (hp + 8) / 2;
     }
     o.total = p;
     std::vector<double> h(p);
@@ -1313,16 +1305,14 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
                 u += 0x7fffu + ((u >> 16) & 1u);
                 return (uint16_t)(u >> 16);
             };
-            // canonical K-major tiles: 8 x 8 core matrices of 128 bytes, 128 bytes apart
-            // along K and 16 K bytes apart along the rows; element offsets:
-            auto kmaj = [](int r, int k, int K) { return (size_t)((r >> 3) * K * 8 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7)); };
-            std::vector<uint16_t> wf((size_t)T * hp * kpf, 0), wb((size_t)T * 32 * hp, 0);
+            const int sf = net_sf(nd), ndp = net_ndp(nd), sb = hp + 8;
+            std::vector<uint16_t> wf((size_t)T * hp * sf, 0), wb((size_t)T * ndp * sb, 0);
             for (int t = 0; t < T; ++t)
                 for (int mu = 0; mu < hidden; ++mu)
                     for (int v = 0; v < nd; ++v) {
                         const uint16_t b = bf16(w0[((size_t)t * hidden + mu) * nd + v]);
-                        wf[(size_t)t * hp * kpf + kmaj(mu, v, kpf)] = b;  // rows mu, K v: X = Q W0^T
-                        wb[(size_t)t * 32 * hp + kmaj(v, mu, hp)] = b;    // rows v, K mu: dQ = D W0
+                        wf[((size_t)t * hp + mu) * sf + v] = b;   // [t][mu][v]: X = Q W0^T
+                        wb[((size_t)t * ndp + v) * sb + mu] = b;  // [t][v][mu]: dQ = D W0
                     }
             memcpy(hf.data() + o.w0f, wf.data(), wf.size() * 2);
             memcpy(hf.data() + o.w0b, wb.data(), wb.size() * 2);
@@ -1331,8 +1321,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             return cleanup(fail(NEP_ERR_CUDA, "parameter upload failed"));
     }
     m->smem_desc = m->real_size * o.total;
-    if (precision == NEP_FP32_BF16)  // the prefix before the weight tiles, then the operand area
-        m->smem_desc = ((m->real_size * o.w0f + 15) & ~(size_t)15) + (size_t)tc_scratch(T, hidden, nd);
+    if (precision == NEP_FP32_BF16)  // plus the per-warp scratch of the network products
+        m->smem_desc = ((m->smem_desc + 15) & ~(size_t)15) + (size_t)(kBlock / 32) * net_scratch(nd);
     // the force kernel stages the cutoff + coefficient prefix only
     m->smem_force = m->real_size * o.n_cut_coef;
     if (m->smem_desc > 200 * 1024 || m->smem_force > 200 * 1024)
@@ -1844,7 +1834,6 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.e_stride = m->T * m->KRP;
     a.phi = (real*)(base + L.phi);
     a.net_bf16 = m->precision == NEP_FP32_BF16;
-    a.err = flags + 2;
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;

@@ -175,226 +175,206 @@ __device__ __forceinline__ void stage_params(const real* __restrict__ src, real*
     __syncthreads();
 }
 
-// ---- the hidden layer (Eq. 2) on the tensor cores (tcgen05), BF16 weights ------
-// A block's 128 particles are the 128 rows of two products per type t:
-//   X_t = Q W0_t^T        (128 x ND by ND x H: the hidden pre-activations)
-//   dQ_t = D W0_t          (128 x H by H x ND: dU/dq, D = w1 (1 - h^2))
-// issued by one thread as tcgen05.mma (kind::f16, BF16 operands from shared memory,
-// FP32 accumulators in tensor memory).  Each thread writes its own row of Q (then
-// of D) into shared memory and reads its own row of X (then dQ) back from tensor
-// memory lane threadIdx.x with tcgen05.ld; with several types a warp reads the
-// region of each type its lanes hold and every lane keeps its own type's row.  W0 is rounded to BF16 once, on the host; each
-// activation is split into a BF16 head and tail (x = hi + lo, exact to about 2^-16
-// relative) multiplied as two products, so the result is the FP32 evaluation of
-// the model with BF16 weights and the forces stay the gradient of its energy.
-//
-// Operands use the canonical K-major layout without swizzle: 8 x 8 BF16 core
-// matrices of 128 contiguous bytes, 128 bytes apart along K (the descriptor's
-// leading offset) and 16 K bytes apart along the rows (its stride offset).
-
-// shared-memory matrix descriptor (K-major, no swizzle)
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t sbo)
+// ---- the hidden layer (Eq. 2) on tensor cores with BF16 weights -----------------
+// A warp evaluates the network of its 32 particles (one per lane) as
+//   X = Q W0^T       (32 x ND by ND x H: the hidden pre-activations)
+//   dQ = D W0        (32 x H by H x ND: dU/dq, D = w1 (1 - h^2))
+// with mma.sync m16n8k16 (BF16 operands, FP32 accumulation).  W0 is rounded to
+// BF16 once, on the host; each activation (Q, D) is split into a BF16 head and a
+// BF16 tail (x = hi + lo, exact to about 2^-16 relative) and multiplied as two
+// products, so the result is the FP32 evaluation of the model with BF16 weights
+// and the forces stay the gradient of its energy.  Q is transposed into fragment
+// order through a warp-private shared tile; the FP32 accumulators of X are exactly
+// the A fragments of the D product, so D never leaves registers; dQ comes back to
+// the lanes through the same tile.  Particles of a type other than t are masked
+// out of type t's products.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);  // .x (low half) = lo
+    return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128
-__device__ __forceinline__ uint32_t tc_idesc(int n)
+// (x0, x1) as packed BF16 heads and packed BF16 tails: x = head + tail
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& head, uint32_t& tail)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    head = pack_bf16(__bfloat162float(h0), __bfloat162float(h1));
+    tail = pack_bf16(x0 - __bfloat162float(h0), x1 - __bfloat162float(h1));
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t da, uint64_t db, uint32_t idesc, bool acc)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
 {
     asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-        "l"(da), "l"(db), "r"(idesc), "r"((uint32_t)acc));
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Wait (bounded) for the given phase of an mbarrier; false if it did not complete.
-__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t phase)
-{
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it)
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(smem_addr(mbar)), "r"(phase));
-    return done != 0;
-}
-
-// 16 consecutive FP32 columns of this thread's tensor-memory lane
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
-}
-
-// 16 columns at `taddr` + t * stride of the region of type t = ti.  The address of
-// tcgen05.ld is warp-wide, so the warp reads the region of every type present
-// among its lanes and each lane keeps its own type's.
-__device__ __forceinline__ void tc_ld_type(uint32_t taddr, int stride, int T, int ti, float (&v)[16])
-{
-    if (T == 1) {
-        tc_ld16(taddr, v);
-        return;
-    }
-    for (int t = 0; t < T; ++t) {
-        if (!__any_sync(0xffffffffu, ti == t)) continue;
-        float w[16];
-        tc_ld16(taddr + (uint32_t)(t * stride), w);
-        if (t == ti)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = w[k];
-    }
-}
-
-// 8 consecutive K values of one row as BF16 heads and tails (two 16-byte chunks)
-__device__ __forceinline__ void tc_put8(unsigned char* hi_row, unsigned char* lo_row, const float* x)
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * k]), h1 = __float2bfloat16_rn(x[2 * k + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(x[2 * k] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(x[2 * k + 1] - __bfloat162float(h1));
-        h[k] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-        l[k] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    }
-    *reinterpret_cast<uint4*>(hi_row) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4*>(lo_row) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
-// byte offset of row r, K chunk kc (8 values) in a canonical K-major tile with K columns
-__device__ __forceinline__ uint32_t tc_off(int r, int kc, int K)
-{
-    return (uint32_t)((r >> 3) * (K * 16) + kc * 128 + (r & 7) * 16);
-}
-
-// The network of this thread's particle (all 128 threads of the block take part;
-// `scratch` is the block's operand area of tc_scratch bytes, 16-byte aligned).
 template <int ND>
-__device__ __forceinline__ void net_tc(const float* P, const float* __restrict__ gparams, const ParamLayout& off,
-                                       int T, int H, int ti, const float (&q)[ND], float& U, float (&dq)[ND],
-                                       unsigned char* scratch, int* err)
+__device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off, int T, int H, int ti,
+                                         const float (&q)[ND], float& U, float (&dq)[ND], unsigned char* scratch)
 {
-    constexpr int KPF = net_kpf(ND), NDP = net_ndp(ND);
-    const int HP = net_hp(H), tid = threadIdx.x, warp = tid >> 5;
-    const int cols = tc_cols(T, H);
-    // every operand the tensor cores read starts on a 128-byte boundary
-    unsigned char* region = scratch + ((128u - (smem_addr(scratch) & 127u)) & 127u);
-    unsigned char* A_hi = region;
-    unsigned char* A_lo = region + tc_tile(H, ND);  // head and tail tiles
-    unsigned char* Wf = region + 2 * tc_tile(H, ND);  // [T][HP x KPF] tiles
-    unsigned char* Wb = Wf + (size_t)T * HP * KPF * 2;  // [T][32 x HP] tiles
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(region + 2 * tc_tile(H, ND) + tc_wtiles(T, H, ND));
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
-    {  // W0 tiles from the model's parameters (16-byte copies)
-        const uint4* src = reinterpret_cast<const uint4*>(gparams + off.w0f);
-        uint4* dst = reinterpret_cast<uint4*>(Wf);
-        for (int k = tid; k < tc_wtiles(T, H, ND) / 16; k += blockDim.x) dst[k] = src[k];
-    }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)));
-    // Q: this thread's row, K = KPF
-    {
-        float v[KPF];
+    constexpr int KPF = net_kpf(ND), SF = net_sf(ND), NDP = net_ndp(ND), KS = KPF / 16, NB = NDP / 8;
+    constexpr int QT = 32 * (SF / 2);  // words of one Q tile
+    const int HP = net_hp(H), SB = HP + 8;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    uint32_t* Qw = reinterpret_cast<uint32_t*>(scratch);  // [2 (head, tail)][32][SF / 2] words
 #pragma unroll
-        for (int k = 0; k < KPF; ++k) v[k] = k < ND ? q[k] : 0.f;
+    for (int v = 0; v < KPF / 2; ++v) {
+        uint32_t hd, tl;
+        split_bf16(2 * v < ND ? q[2 * v] : 0.f, 2 * v + 1 < ND ? q[2 * v + 1] : 0.f, hd, tl);
+        Qw[lane * (SF / 2) + v] = hd;
+        Qw[QT + lane * (SF / 2) + v] = tl;
+    }
+    __syncwarp();
+    uint32_t af[2][2][KS][4];  // [head/tail][m tile][k step]
 #pragma unroll
-        for (int kc = 0; kc < KPF / 8; ++kc) tc_put8(A_hi + tc_off(tid, kc, KPF), A_lo + tc_off(tid, kc, KPF), v + 8 * kc);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
-                     "r"(cols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tslot;
-    if (tid == 0) {  // X_t = Q W0_t^T into columns [t HP, (t + 1) HP)
-        const uint32_t idesc = tc_idesc(HP);
-        for (int t = 0; t < T; ++t)
-            for (int ks = 0; ks < KPF / 16; ++ks)
-                for (int part = 0; part < 2; ++part) {
-                    const unsigned char* Ap = part ? A_lo : A_hi;
-                    tc_mma(tmem + (uint32_t)(t * HP), tc_desc(smem_addr(Ap) + ks * 256, KPF * 16),
-                           tc_desc(smem_addr(Wf + (size_t)t * HP * KPF * 2) + ks * 256, KPF * 16), idesc,
-                           ks > 0 || part > 0);
+    for (int pt = 0; pt < 2; ++pt)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int kk = 0; kk < KS; ++kk) {
+                const int r0 = 16 * mt + g;
+                const uint32_t* Qp = Qw + pt * QT;
+                af[pt][mt][kk][0] = Qp[r0 * (SF / 2) + 8 * kk + c];
+                af[pt][mt][kk][1] = Qp[(r0 + 8) * (SF / 2) + 8 * kk + c];
+                af[pt][mt][kk][2] = Qp[r0 * (SF / 2) + 8 * kk + 4 + c];
+                af[pt][mt][kk][3] = Qp[(r0 + 8) * (SF / 2) + 8 * kk + 4 + c];
+            }
+    __syncwarp();  // the tile is reused for dQ below
+    int rt[2][2];  // types of this lane's fragment rows 16 mt + g + 8 h
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) rt[mt][h] = __shfl_sync(FULL, ti, 16 * mt + g + 8 * h);
+    const uint16_t* W0f = reinterpret_cast<const uint16_t*>(P + off.w0f);
+    const uint16_t* W0b = reinterpret_cast<const uint16_t*>(P + off.w0b);
+    const float* b0 = P + off.b0;
+    const float* w1 = P + off.w1;
+    float up[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    float dacc[2][NB][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dacc[mt][nb][e] = 0.f;
+    for (int ch = 0; ch < HP / 16; ++ch) {  // 16 hidden units at a time
+        float x[2][2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[mt][nl][e] = 0.f;
+        for (int t = 0; t < T; ++t) {
+            if (T > 1 && !__any_sync(FULL, ti == t)) continue;
+            const uint32_t* Wf = reinterpret_cast<const uint32_t*>(W0f + (size_t)t * HP * SF);
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl) {
+                const int nrow = 16 * ch + 8 * nl + g;  // hidden unit of this lane's B column
+                uint32_t b[KS][2];
+#pragma unroll
+                for (int kk = 0; kk < KS; ++kk) {
+                    b[kk][0] = Wf[nrow * (SF / 2) + 8 * kk + c];
+                    b[kk][1] = Wf[nrow * (SF / 2) + 8 * kk + 4 + c];
                 }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(mbar)));
-    }
-    bool ok = tc_wait(mbar, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // h = tanh(x - b0), the energy, and D = w1 (1 - h^2), 16 hidden units at a time
-    const float* b0 = P + off.b0 + ti * H;
-    const float* w1 = P + off.w1 + ti * H;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    float u = 0.f;
-    for (int c = 0; c < HP / 16; ++c) {
-        float x[16], d[16];
-        tc_ld_type(lane_addr + (uint32_t)(16 * c), HP, T, ti, x);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int col = 16 * c + k;
-            d[k] = 0.f;
-            if (col < H) {
-                const float h = tanhf(x[k] - b0[col]);
-                u += w1[col] * h;
-                d[k] = w1[col] * (1.f - h * h);
+                for (int mt = 0; mt < 2; ++mt) {
+                    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int kk = 0; kk < KS; ++kk) {
+                        mma_bf16(acc, af[1][mt][kk], b[kk][0], b[kk][1]);  // tails first (smaller)
+                        mma_bf16(acc, af[0][mt][kk], b[kk][0], b[kk][1]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (T == 1 || rt[mt][e >> 1] == t) x[mt][nl][e] = acc[e];
+                }
             }
         }
-        tc_put8(A_hi + tc_off(tid, 2 * c, HP), A_lo + tc_off(tid, 2 * c, HP), d);
-        tc_put8(A_hi + tc_off(tid, 2 * c + 1, HP), A_lo + tc_off(tid, 2 * c + 1, HP), d + 8);
-    }
-    U = u - P[off.b1 + ti];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // every X row is read before the columns are reused
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {  // dQ_t = D W0_t into columns [32 t, 32 t + 32)
-        const uint32_t idesc = tc_idesc(32);
-        for (int t = 0; t < T; ++t)
-            for (int ks = 0; ks < HP / 16; ++ks)
-                for (int part = 0; part < 2; ++part) {
-                    const unsigned char* Ap = part ? A_lo : A_hi;
-                    tc_mma(tmem + (uint32_t)(32 * t), tc_desc(smem_addr(Ap) + ks * 256, HP * 16),
-                           tc_desc(smem_addr(Wb + (size_t)t * 32 * HP * 2) + ks * 256, HP * 16), idesc,
-                           ks > 0 || part > 0);
+        // h = tanh(x - b0), the energy terms, and D = w1 (1 - h^2) in A-fragment order
+        uint32_t ca[2][2][4];  // [head/tail][m tile]
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float d[2][4];
+#pragma unroll
+            for (int nl = 0; nl < 2; ++nl)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int col = 16 * ch + 8 * nl + 2 * c + (e & 1);
+                    const int t = rt[mt][e >> 1];
+                    float coef = 0.f;
+                    if (col < H) {
+                        const float h = tanhf(x[mt][nl][e] - b0[t * H + col]);
+                        const float w = w1[t * H + col];
+                        up[mt][e >> 1] += w * h;
+                        coef = w * (1.f - h * h);
+                    }
+                    d[nl][e] = coef;
                 }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(mbar)));
-    }
-    ok = tc_wait(mbar, 1) && ok;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            split_bf16(d[0][0], d[0][1], ca[0][mt][0], ca[1][mt][0]);
+            split_bf16(d[0][2], d[0][3], ca[0][mt][1], ca[1][mt][1]);
+            split_bf16(d[1][0], d[1][1], ca[0][mt][2], ca[1][mt][2]);
+            split_bf16(d[1][2], d[1][3], ca[0][mt][3], ca[1][mt][3]);
+        }
+        for (int t = 0; t < T; ++t) {
+            if (T > 1 && !__any_sync(FULL, ti == t)) continue;
+            const uint32_t* Wb = reinterpret_cast<const uint32_t*>(W0b + (size_t)t * NDP * SB);
+            uint32_t cm[2][2][4];
 #pragma unroll
-    for (int c = 0; c < NDP / 16 + (NDP % 16 ? 1 : 0); ++c) {
-        float v[16];
-        tc_ld_type(lane_addr + (uint32_t)(16 * c), 32, T, ti, v);
+            for (int pt = 0; pt < 2; ++pt)
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (16 * c + k < ND) dq[16 * c + k] = v[k];
+                for (int mt = 0; mt < 2; ++mt) {
+                    const bool k0 = T == 1 || rt[mt][0] == t, k1 = T == 1 || rt[mt][1] == t;
+                    cm[pt][mt][0] = k0 ? ca[pt][mt][0] : 0u;
+                    cm[pt][mt][1] = k1 ? ca[pt][mt][1] : 0u;
+                    cm[pt][mt][2] = k0 ? ca[pt][mt][2] : 0u;
+                    cm[pt][mt][3] = k1 ? ca[pt][mt][3] : 0u;
+                }
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) {
+                const int vrow = 8 * nb + g;  // descriptor index of this lane's B column
+                const uint32_t bb0 = Wb[vrow * (SB / 2) + 8 * ch + c], bb1 = Wb[vrow * (SB / 2) + 8 * ch + 4 + c];
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(dacc[mt][nb], cm[1][mt], bb0, bb1);
+                    mma_bf16(dacc[mt][nb], cm[0][mt], bb0, bb1);
+                }
+            }
+        }
     }
-    if (!ok) {  // a wait ran out: report it and poison this particle's results
-        if (err) atomicOr(err, 4);
-        U = __int_as_float(0x7fc00000);
+    // U: sum the quad's partial sums, then each lane takes its own row's
+    float rs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float v = up[k >> 1][k & 1];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        rs[k] = v;  // row 16 (k >> 1) + 8 (k & 1) + g
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    float mine = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float v = __shfl_sync(FULL, rs[k], 4 * (lane & 7));
+        if ((lane >> 3) == k) mine = v;
+    }
+    U = mine - P[off.b1 + ti];
+    // dQ back to one row per lane
+    float* Dw = reinterpret_cast<float*>(scratch);  // [32][NDP + 1]
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                Dw[(16 * mt + g + 8 * (e >> 1)) * (NDP + 1) + 8 * nb + 2 * c + (e & 1)] = dacc[mt][nb][e];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < ND; ++v) dq[v] = Dw[lane * (NDP + 1) + v];
+    __syncwarp();
 }
 
 template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0>
@@ -408,11 +388,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
-    // NET = 1 keeps the BF16 weight tiles out of the staged prefix (they are copied
-    // to an aligned operand area instead)
-    const int staged = NET == 1 ? off.w0f : off.total;
-    stage_params(md.params, P, staged);
-    // NET = 1 evaluates the network block-wide: a lane past the item's end follows
+    stage_params(md.params, P, off.total);
+    // NET = 1 evaluates the network warp-wide: a lane past the item's end follows
     // the item's last particle and writes nothing
     const bool live = NET == 0 || it.begin + (int)threadIdx.x < it.end;
     const int i = live ? it.begin + threadIdx.x : it.end - 1;
@@ -520,8 +497,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     real U;
     real dq[ND];
     if constexpr (NET == 1) {
-        unsigned char* scratch = smem_raw + (((size_t)staged * sizeof(real) + 15) & ~(size_t)15);
-        net_tc<ND>(P, md.params, off, T, H, ti, q, U, dq, scratch, a.err);
+        unsigned char* scratch = smem_raw + (((size_t)off.total * sizeof(real) + 15) & ~(size_t)15) +
+                                 (size_t)(threadIdx.x >> 5) * net_scratch(ND);
+        net_bf16<ND>(P, off, T, H, ti, q, U, dq, scratch);
         if (!live) return;
     } else {
         const real* w0 = P + off.w0 + ti * H * ND;

@@ -24,27 +24,19 @@ constexpr int kMaxTypes = 16;
 constexpr int kBlock = 128;          // threads per block = particles per work item
 constexpr int kScanItems = 4096;     // cells per block of the scan
 
-// BF16-weight network on the tensor cores: padded sizes (BF16 elements) of the
-// products X = Q W0^T (K = net_kpf, N = net_hp) and dQ = D W0 (K = net_hp, N = 32)
-// for one block of 128 particles.
-__host__ __device__ constexpr int net_kpf(int nd) { return (nd + 15) & ~15; }
-__host__ __device__ constexpr int net_ndp(int nd) { return (nd + 7) & ~7; }
-__host__ __device__ constexpr int net_hp(int h) { return (h + 15) & ~15; }
-// bytes of one 128-row operand tile (Q or D)
-__host__ __device__ constexpr int tc_tile(int h, int nd) { return 128 * 2 * (net_kpf(nd) > net_hp(h) ? net_kpf(nd) : net_hp(h)); }
-// tensor-memory columns of a block: per type N = net_hp(h) for X, 32 for dQ (reused)
-__host__ __device__ constexpr int tc_cols(int t, int h)
+// BF16 network tables (the hidden layer as two tensor-core products per warp of
+// 32 particles): padded sizes in BF16 elements.
+__host__ __device__ constexpr int net_kpf(int nd) { return (nd + 15) & ~15; }  // K of X = Q W0^T
+__host__ __device__ constexpr int net_sf(int nd) { return net_kpf(nd) + 8; }    // row stride (bank spread)
+__host__ __device__ constexpr int net_ndp(int nd) { return (nd + 7) & ~7; }     // N of dQ = D W0
+__host__ __device__ constexpr int net_hp(int h) { return (h + 15) & ~15; }       // N of X, K of dQ
+// per-warp shared scratch of the BF16 network, bytes
+__host__ __device__ constexpr int net_scratch(int nd)
 {
-    const int need = t * (net_hp(h) > 32 ? net_hp(h) : 32);
-    int c = 32;
-    while (c < need) c *= 2;
-    return c;
+    // two BF16 tiles of Q (head, tail), later one FP32 tile of dQ
+    return (2 * 32 * net_sf(nd) * 2 > 32 * (net_ndp(nd) + 1) * 4 ? 2 * 32 * net_sf(nd) * 2
+                                                                   : 32 * (net_ndp(nd) + 1) * 4);
 }
-// shared scratch of a block: up to 128 bytes to reach a 128-byte boundary, the head
-// and tail operand tiles, the W0 tiles of every type (forward, then backward), then
-// the mbarrier and the tensor-memory address
-__host__ __device__ constexpr int tc_wtiles(int t, int h, int nd) { return t * (net_hp(h) * net_kpf(nd) + 32 * net_hp(h)) * 2; }
-__host__ __device__ constexpr int tc_scratch(int t, int h, int nd) { return 128 + 2 * tc_tile(h, nd) + tc_wtiles(t, h, nd) + 16; }
 
 // Row length of Phi_i per harmonic component: n_A padded to a multiple of 4 so that
 // every row starts on a 16-byte boundary (vector loads).
@@ -117,9 +109,8 @@ struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
     int cR, cA;                 // [T][T][nR][KR], [T][T][nA][KA]
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
-    int w0f, w0b;               // BF16-weight network form: W0 as BF16 tensor-core operand tiles
-                                // (-1 when absent): per type [net_hp(H) x net_kpf(ND)] and
-                                // [32 x net_hp(H)], canonical K-major layout
+    int w0f, w0b;               // BF16-weight network form: W0 as BF16 MMA operands (-1 when absent),
+                                // [T][net_hp(H)][net_sf(ND)] and [T][net_ndp(ND)][net_hp(H) + 8]
     int n_cut_coef;             // elements of the cutoff + coefficient prefix
     int total;                  // all elements
 };
@@ -177,8 +168,7 @@ struct EvalArgs {
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
     real* phi;                  // [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
-    int net_bf16;               // 1: the hidden layer's products on the tensor cores (BF16 weights)
-    int* err;                   // status word: bit 4 = a tensor-core wait ran out (or null)
+    int net_bf16;               // 1: the hidden layer's products in BF16 on tensor cores
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null
