@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             const int tp = ti * T + rj.t;
             real f[KR];
             basis<real, KR>(r, P[off.rcRi + tp], f);
-            const real* c = P + off.cR + tp * NR * KR;
+            const real* c = P + off.cR + tp * off.cRs;
 #pragma unroll
             for (int nn = 0; nn < NR; ++nn) {
                 real g = real(0);
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         const int tp = ti * T + rj.t;
         real f[KA];
         basis<real, KA>(r, P[off.rcAi + tp], f);
-        const real* c = P + off.cA + tp * NA * KA;
+        const real* c = P + off.cA + tp * off.cAs;
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
 #pragma unroll
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
     real* ei = a.e + (size_t)i * a.e_stride;
     for (int t = 0; t < T; ++t) {
-        const real* c = P + off.cR + (ti * T + t) * NR * KR;
+        const real* c = P + off.cR + (ti * T + t) * off.cRs;
 #pragma unroll
         for (int k = 0; k < KRP; ++k) {
             real v = real(0);
@@ -555,7 +555,9 @@ __device__ __forceinline__ real warp_sum(real v)
 }
 
 // FP64 block partials of (E, W[9]); the last block of a request sums its request's
-// partials in item order (deterministic) into totals[req].
+// partials into totals[req]: every thread takes a fixed stride of the items
+// (counted from the request's first, so a request sums alike alone or in a batch),
+// then a fixed tree combines the threads, so the result does not depend on timing.
 template <int BS>
 __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& it, const ReqInfo& rq,
                                               double* partial, unsigned int* counter, double* totals)
@@ -582,11 +584,25 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& i
     __syncthreads();
     if (!last) return;
     __threadfence();
+    double s[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) s[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)n_items; b += BS) {
+        const double* q = partial + (size_t)(rq.item_begin + b) * 10;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) s[k] += __ldcg(q + k);  // L2: written by other blocks
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const double w = warp_sum(s[k]);
+        if (lane == 0) red[warp][k] = w;
+    }
+    __syncthreads();
     if (threadIdx.x < 10) {
-        double s = 0.0;
-        const volatile double* p = partial;
-        for (int b = rq.item_begin; b < rq.item_end; ++b) s += p[(size_t)b * 10 + threadIdx.x];
-        totals[(size_t)it.req * 10 + threadIdx.x] = s;
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < BS / 32; ++w) t += red[w][threadIdx.x];
+        totals[(size_t)it.req * 10 + threadIdx.x] = t;
     }
     if (threadIdx.x == 0) counter[it.req] = 0u;
 }
@@ -709,7 +725,7 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
         basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
         real gi[NA], dgi[NA], gj[NA], dgj[NA];
         {
-            const real* cc = P + off.cA + tij * NA * KA;
+            const real* cc = P + off.cA + tij * off.cAs;
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
                 real s0 = real(0), s1 = real(0);
@@ -729,7 +745,7 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
                 dgj[nn] = dgi[nn];
             }
         } else {
-            const real* cc = P + off.cA + tji * NA * KA;
+            const real* cc = P + off.cA + tji * off.cAs;
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
                 real s0 = real(0), s1 = real(0);
@@ -893,7 +909,7 @@ __device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, c
         real f[KA], df[KA];
         basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
         real g[NA], dg[NA];
-        const real* cc = P + off.cA + tij * NA * KA;
+        const real* cc = P + off.cA + tij * off.cAs;
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) {
             real s0 = real(0), s1 = real(0);

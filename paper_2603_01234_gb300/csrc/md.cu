@@ -25,6 +25,34 @@ struct TypeTable {
     double v[kMdMaxTypes];
 };
 
+// Sum of partial[b * NC + c] over the nb blocks, by the whole (last) block: fixed
+// strides per thread and a fixed tree, so the result does not depend on timing.
+// Every thread receives the totals.
+template <int NC>
+__device__ __forceinline__ void last_block_sum(const double* partial, unsigned nb, double (&out)[NC])
+{
+    __shared__ double red[kBlock / 32][NC];
+    double s[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) s[c] = 0.0;
+    for (unsigned b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s[c] += __ldcg(partial + (size_t)b * NC + c);  // L2: other blocks' words
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = s[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        double t = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) t += red[w][c];
+        out[c] = t;
+    }
+}
+
 __global__ void __launch_bounds__(kBlock) k_kick_drift(int n, const int* __restrict__ types, TypeTable inv_m_acc,
                                                        double half_dt, double dt, CellGrid g, double* __restrict__ pos,
                                                        double* __restrict__ vel, const double* __restrict__ force)
@@ -85,11 +113,12 @@ __global__ void __launch_bounds__(kBlock) k_sample(int n, const int* __restrict_
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    const volatile double* p = partial;
-    double s = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) s += p[b];
+    double tot[1];
+    last_block_sum<1>(partial, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    const double s = tot[0];
     const int row = *sample_index;
     double* t = thermo + (size_t)row * 12;
     t[0] = (double)((row + 1) * step_stride);
@@ -134,12 +163,12 @@ __global__ void __launch_bounds__(kBlock) k_bussi_ke(int n, const int* __restric
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    const volatile double* p = partial;
-    double K = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) K += p[b];
-    K /= kAcc;  // eV
+    double tot[1];
+    last_block_sum<1>(partial, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    const double K = tot[0] / kAcc;  // eV
     const int k = *step;
     const double r1 = noise[2 * k], chi = noise[2 * k + 1];
     double a2 = 1.0;
@@ -227,10 +256,13 @@ __global__ void __launch_bounds__(kBlock) k_heat(int n, const int* __restrict__ 
     __syncthreads();
     if (!last) return;
     __threadfence();
+    double tot[6];
+    last_block_sum<6>(partial, gridDim.x, tot);
     if (threadIdx.x < 6) {
-        const volatile double* p = partial;
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += p[(size_t)6 * b + threadIdx.x];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k == (int)threadIdx.x) s = tot[k];
         const double t = acc[threadIdx.x] + s;
         if (sample) {
             rows[(size_t)6 * (*sample_index) + threadIdx.x] = t / step_stride;

@@ -107,7 +107,9 @@ __host__ __device__ inline double wrap_periodic(double x, double L)
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
-    int cR, cA;                 // [T][T][nR][KR], [T][T][nA][KA]
+    int cR, cA;                 // [T][T] tables of [nR][KR] and [nA][KA], cRs / cAs apart
+    int cRs, cAs;               // odd strides between the type pairs' tables, so that lanes
+                                // reading different pairs' tables hit different banks
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
     int w0f, w0b;               // BF16-weight network form: W0 as BF16 MMA operands (-1 when absent),
                                 // [T][net_hp(H)][net_sf(ND)] and [T][net_ndp(ND)][net_hp(H) + 8]
