@@ -10,12 +10,17 @@
 //            (the radial gradient folded into the basis: dU_i/dr_ij|radial =
 //            sum_k e_i^{t_j}[k] f_k'(r_ij) u_ij);  Phi_nlm = dU_i/dA_nlm = 2 dU_i/dq_nl A_nlm
 //
-// k_force (one thread per sorted particle i, gather form, no atomics):
-//   for every neighbour j the pair gradients f_ij = dU_i/dr_ij and
-//   f_ji = dU_j/dr_ji are rebuilt from i's and j's stored gradients, and
-//     F_i = sum_j (f_ij - f_ji),   W_i = sum_j r_ij (x) f_ji   (Eq. 15)
-//   then E = sum U_i and W = sum W_i are reduced in FP64 (Eq. 1, 16) with a
-//   deterministic last-block pass.
+// Forces and virials (one thread per sorted particle i), with
+//   F_i = sum_j (f_ij - f_ji),   W_i = sum_j r_ij (x) f_ji   (Eq. 15),
+// f_ij = dU_i/dr_ij, and E = sum U_i, W = sum W_i reduced in FP64 (Eq. 1, 16) by
+// a deterministic last-block pass:
+//   k_force_scatter (FP32)  radial pairs in gather form (f_ij and f_ji from i's
+//                           and j's stored gradient vectors); angular pairs
+//                           evaluated once, by i, contracting Phi_i only, with
+//                           -f_ij (and W_j's term) sent to j through 64-bit
+//                           fixed-point atomic adds (order-independent sums);
+//                           k_scatter_outputs converts the sums to FP64 outputs
+//   k_force (FP64)          gather form for both kinds of pair, no atomics
 //
 // Angular pair gradient.  For A = g(r) Y(u), u = r/|r|, with Y a homogeneous
 // polynomial of degree l:  dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
