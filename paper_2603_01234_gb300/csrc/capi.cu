@@ -1256,10 +1256,9 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.rcA2 = p; p += TT;
     o.rcRi = p; p += TT;
     o.rcAi = p; p += TT;
-    o.cRs = (m->nR * m->KR) | 1;
-    o.cAs = (m->nA * m->KA) | 1;
-    o.cR = p; p += TT * o.cRs;
-    o.cA = p; p += TT * o.cAs;
+    const int cRs = coef_stride(m->nR, m->KR), cAs = coef_stride(m->nA, m->KA);
+    o.cR = p; p += TT * cRs;
+    o.cA = p; p += TT * cAs;
     o.n_cut_coef = p;
     o.w0 = p; p += T * hidden * m->ND;
     o.b0 = p; p += T * hidden;
@@ -1282,9 +1281,9 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     }
     for (int k = 0; k < TT; ++k) {  // pair tables at odd strides
         std::copy(c_radial + (size_t)k * m->nR * m->KR, c_radial + (size_t)(k + 1) * m->nR * m->KR,
-                  h.begin() + o.cR + k * o.cRs);
+                  h.begin() + o.cR + k * cRs);
         std::copy(c_angular + (size_t)k * m->nA * m->KA, c_angular + (size_t)(k + 1) * m->nA * m->KA,
-                  h.begin() + o.cA + k * o.cAs);
+                  h.begin() + o.cA + k * cAs);
     }
     std::copy(w0, w0 + T * hidden * m->ND, h.begin() + o.w0);
     std::copy(b0, b0 + T * hidden, h.begin() + o.b0);

@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             const int tp = ti * T + rj.t;
             real f[KR];
             basis<real, KR>(r, P[off.rcRi + tp], f);
-            const real* c = P + off.cR + tp * off.cRs;
+            const real* c = P + off.cR + tp * coef_stride(NR, KR);
 #pragma unroll
             for (int nn = 0; nn < NR; ++nn) {
                 real g = real(0);
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         const int tp = ti * T + rj.t;
         real f[KA];
         basis<real, KA>(r, P[off.rcAi + tp], f);
-        const real* c = P + off.cA + tp * off.cAs;
+        const real* c = P + off.cA + tp * coef_stride(NA, KA);
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
 #pragma unroll
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
     real* ei = a.e + (size_t)i * a.e_stride;
     for (int t = 0; t < T; ++t) {
-        const real* c = P + off.cR + (ti * T + t) * off.cRs;
+        const real* c = P + off.cR + (ti * T + t) * coef_stride(NR, KR);
 #pragma unroll
         for (int k = 0; k < KRP; ++k) {
             real v = real(0);
@@ -730,7 +730,7 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
         basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
         real gi[NA], dgi[NA], gj[NA], dgj[NA];
         {
-            const real* cc = P + off.cA + tij * off.cAs;
+            const real* cc = P + off.cA + tij * coef_stride(NA, KA);
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
                 real s0 = real(0), s1 = real(0);
@@ -750,7 +750,7 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
                 dgj[nn] = dgi[nn];
             }
         } else {
-            const real* cc = P + off.cA + tji * off.cAs;
+            const real* cc = P + off.cA + tji * coef_stride(NA, KA);
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
                 real s0 = real(0), s1 = real(0);
@@ -914,7 +914,7 @@ __device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, c
         real f[KA], df[KA];
         basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
         real g[NA], dg[NA];
-        const real* cc = P + off.cA + tij * off.cAs;
+        const real* cc = P + off.cA + tij * coef_stride(NA, KA);
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) {
             real s0 = real(0), s1 = real(0);

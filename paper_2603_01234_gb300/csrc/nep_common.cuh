@@ -38,6 +38,11 @@ __host__ __device__ constexpr int net_scratch(int nd)
                                                                    : 32 * (net_ndp(nd) + 1) * 4);
 }
 
+// Distance (elements) between the type pairs' coefficient tables of n x K entries:
+// odd, so that lanes reading different pairs' tables hit different shared-memory
+// banks.  A compile-time function of the shape, used alike by host and kernels.
+__host__ __device__ constexpr int coef_stride(int n, int k) { return (n * k) | 1; }
+
 // Row length of Phi_i per harmonic component: n_A padded to a multiple of 4 so that
 // every row starts on a 16-byte boundary (vector loads).
 __host__ __device__ constexpr int phi_pad(int nA) { return (nA + 3) & ~3; }
@@ -107,9 +112,7 @@ __host__ __device__ inline double wrap_periodic(double x, double L)
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
-    int cR, cA;                 // [T][T] tables of [nR][KR] and [nA][KA], cRs / cAs apart
-    int cRs, cAs;               // odd strides between the type pairs' tables, so that lanes
-                                // reading different pairs' tables hit different banks
+    int cR, cA;                 // [T][T] tables of [nR][KR] and [nA][KA], coef_stride apart
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
     int w0f, w0b;               // BF16-weight network form: W0 as BF16 MMA operands (-1 when absent),
                                 // [T][net_hp(H)][net_sf(ND)] and [T][net_ndp(ND)][net_hp(H) + 8]
