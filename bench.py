@@ -43,7 +43,7 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 
 # DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
 # profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
-FORCE_TRAFFIC = {"evaluate_cu_sha1": "08032a6985eca8f802b692573c1030c6e42cb42b", "bytes_per_particle": 963.0,
+FORCE_TRAFFIC = {"evaluate_cu_sha1": "2ba3f727809c4627dc36cba5d47789f32d4e5184", "bytes_per_particle": 960.9,
                  "capture": "profiles/force_descriptor_water200k_ncu.md"}
 
 
