@@ -15,6 +15,14 @@
  *   Eq. 7   f_k(r) = 1/2 [T_k(2 (r/r_c - 1)^2 - 1) + 1] f_c(r)
  *   Eq. 8   f_c(r) = 1/2 [1 + cos(pi r / r_c)] for r <= r_c, else 0
  *   Eq. 15  W_i = sum_{j != i} r_ij (x) dU_j/dr_ji,  r_ij = r_j - r_i
+ *
+ * Four- and five-body angular terms (Sec. II.A refers their definition to the
+ * GPUMD paper, Fan et al., J. Chem. Phys. 157, 114801 (2022); read here as):
+ *   q4_n = sum_{m1 m2 m3} (2 2 2; m1 m2 m3) A_n2m1 A_n2m2 A_n2m3   (Wigner 3j)
+ *   q5_n = (q_n1)^2 = (sum_m (-1)^m A_n1m A_n1(-m))^2
+ * the cubic invariant of the l = 2 moments and the quartic invariant of the l = 1
+ * moments; each is the only rotational invariant of its degree, so these fix them
+ * up to a constant factor, which the network weights absorb.
  *   Eq. 16  W = sum_i W_i
  *
  * Heat transport (the HNEMD runs of Sec. III.B follow Fan et al., Phys. Rev. B 99,
@@ -29,7 +37,9 @@
  *     phase; theta is the polar angle of r_ij, phi its azimuth.
  *   - A pair is a neighbour when r < r_c strictly (f_c and f_c' vanish at r_c).
  *   - j != i excludes only the zero-shift self image; periodic images of i count.
- *   - Descriptor order: q_0..q_{n_R-1}, then for l = 1..l_max, n = 0..n_A-1: q_nl.
+ *   - Descriptor order: q_0..q_{n_R-1}, then for l = 1..l_max, n = 0..n_A-1: q_nl,
+ *     then q4_0..q4_{n_A-1} (when l_max^4b = 2), then q5_0..q5_{n_A-1} (when
+ *     l_max^5b = 1).
  *   - Every parameter is per central type t_i; c is indexed (t_i, t_j).
  *   - Positions on periodic axes are wrapped to [0, L) before neighbours are
  *     searched: a position in [0, L) is kept, any other becomes x - L floor(x / L)
@@ -39,7 +49,13 @@
  * gradient is taken from the addition-theorem form of q_nl,
  *     q_nl = (2l+1)/(4 pi) sum_{a,b} g_n(r_a) g_n(r_b) P_l(u_a . u_b),
  * which is algebraically the same function as Eq. 4-5 but computed by a different
- * route, so that the finite-difference pin on forces cross-checks both.
+ * route, so that the finite-difference pin on forces cross-checks both.  The
+ * four-body gradient likewise comes from a Cartesian form: with the traceless
+ * tensor Q_n = sum_j g_n(r_j) (u_j u_j^T - I/3),
+ *     q4_n = kappa tr(Q_n^3),  kappa = (2 2 2; 0 0 0) (5 / 4 pi)^(3/2) 9/2
+ * (both sides are the cubic invariant of the l = 2 moments; one neighbour on the
+ * z axis, where A_2m = g sqrt(5 / 4 pi) delta_m0 and tr(Q^3) = 2 g^3 / 9, fixes
+ * kappa).  The five-body gradient is 2 q_n1 times that of q_n1.
  *
  * Units: Angstrom, eV, amu, fs.  All arithmetic is double precision.
  */
@@ -179,17 +195,41 @@ void oracle_ylm(int l, int m, double theta, double phi, double *re, double *im)
     *im = yi;
 }
 
+/* Wigner 3j symbol (j1 j2 j3; m1 m2 m3) for integer arguments, by Racah's
+ * single-sum formula. */
+double oracle_wigner3j(int j1, int j2, int j3, int m1, int m2, int m3)
+{
+    if (m1 + m2 + m3 != 0) return 0.0;
+    if (j3 < abs(j1 - j2) || j3 > j1 + j2) return 0.0;
+    if (abs(m1) > j1 || abs(m2) > j2 || abs(m3) > j3) return 0.0;
+    double tri = fact(j1 + j2 - j3) * fact(j1 - j2 + j3) * fact(-j1 + j2 + j3) / fact(j1 + j2 + j3 + 1);
+    double pre = sqrt(tri * fact(j1 + m1) * fact(j1 - m1) * fact(j2 + m2) * fact(j2 - m2) * fact(j3 + m3) *
+                      fact(j3 - m3));
+    double s = 0.0;
+    for (int k = 0; k <= j1 + j2 + j3; ++k) {
+        int a1 = j3 - j2 + k + m1, a2 = j3 - j1 + k - m2, a3 = j1 + j2 - j3 - k, a4 = j1 - k - m1,
+            a5 = j2 - k + m2;
+        if (a1 < 0 || a2 < 0 || a3 < 0 || a4 < 0 || a5 < 0) continue;
+        s += ((k % 2) ? -1.0 : 1.0) / (fact(k) * fact(a1) * fact(a2) * fact(a3) * fact(a4) * fact(a5));
+    }
+    int ph = j1 - j2 - m3;
+    return ((ph % 2 + 2) % 2 ? -1.0 : 1.0) * pre * s;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Model                                                                       */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-    int T, nR, nA, KR, KA, L, H;
+    int T, nR, nA, KR, KA, L, L4, L5, H;
     const double *rcR, *rcA;           /* [T][T] */
     const double *cR, *cA;             /* [T][T][nR][KR], [T][T][nA][KA] */
     const double *w0, *b0, *w1, *b1;   /* [T][H][Ndes], [T][H], [T][H], [T] */
 } omodel;
 
-static int ndes(const omodel *m) { return m->nR + m->nA * m->L; }
+static int ndes(const omodel *m) { return m->nR + m->nA * (m->L + (m->L4 > 0) + (m->L5 > 0)); }
+/* indices of q4_n and q5_n in the descriptor vector */
+static int q4_index(const omodel *m, int n) { return m->nR + m->nA * m->L + n; }
+static int q5_index(const omodel *m, int n) { return m->nR + m->nA * (m->L + (m->L4 > 0)) + n; }
 static const double *coefR(const omodel *m, int ti, int tj, int n) { return m->cR + (((size_t)ti * m->T + tj) * m->nR + n) * m->KR; }
 static const double *coefA(const omodel *m, int ti, int tj, int n) { return m->cA + (((size_t)ti * m->T + tj) * m->nA + n) * m->KA; }
 
@@ -459,8 +499,9 @@ static void descriptor_ylm(const omodel *m, int n, const int *types, const doubl
 {
     int ti = types[i];
     for (int k = 0; k < ndes(m); ++k) q[k] = 0.0;
-    /* A[n][l][m+l], complex, l <= 4 */
+    /* A[n][l][m+l], complex, l <= 4 (l <= 2 is also needed by the 4-body term) */
     double Ar[16][5][9], Ai[16][5][9];
+    int lacc = m->L > 2 ? m->L : 2;
     memset(Ar, 0, sizeof Ar);
     memset(Ai, 0, sizeof Ai);
     for (int a = l->start[i]; a < l->start[i + 1]; ++a) {
@@ -478,7 +519,7 @@ static void descriptor_ylm(const omodel *m, int n, const int *types, const doubl
             double theta = acos(d[2] / r), phi = atan2(d[1], d[0]);
             for (int nn = 0; nn < m->nA; ++nn) {
                 double g = oracle_gn(coefA(m, ti, tj, nn), m->KA, r, rc);
-                for (int ll = 1; ll <= m->L; ++ll)
+                for (int ll = 1; ll <= lacc; ++ll)
                     for (int mm = -ll; mm <= ll; ++mm) {
                         double yr, yi;
                         oracle_ylm(ll, mm, theta, phi, &yr, &yi);
@@ -499,6 +540,35 @@ static void descriptor_ylm(const omodel *m, int n, const int *types, const doubl
                 s += sg * (ar * br - ai * bi);
             }
             q[m->nR + (ll - 1) * m->nA + nn] = s;
+        }
+    /* four-body: sum over m1 + m2 + m3 = 0 of the 3j-weighted triple product (real
+     * part; the imaginary part cancels because A_l(-m) = (-1)^m conj(A_lm)) */
+    if (m->L4)
+        for (int nn = 0; nn < m->nA; ++nn) {
+            double s = 0.0;
+            for (int m1 = -2; m1 <= 2; ++m1)
+                for (int m2 = -2; m2 <= 2; ++m2) {
+                    int m3 = -m1 - m2;
+                    if (m3 < -2 || m3 > 2) continue;
+                    double c = oracle_wigner3j(2, 2, 2, m1, m2, m3);
+                    double ar = Ar[nn][2][m1 + 2], ai = Ai[nn][2][m1 + 2];
+                    double br = Ar[nn][2][m2 + 2], bi = Ai[nn][2][m2 + 2];
+                    double cr = Ar[nn][2][m3 + 2], ci = Ai[nn][2][m3 + 2];
+                    double pr = ar * br - ai * bi, pi = ar * bi + ai * br;
+                    s += c * (pr * cr - pi * ci);
+                }
+            q[q4_index(m, nn)] = s;
+        }
+    /* five-body: the square of the l = 1 pair coupling */
+    if (m->L5)
+        for (int nn = 0; nn < m->nA; ++nn) {
+            double s = 0.0;
+            for (int mm = -1; mm <= 1; ++mm) {
+                double ar = Ar[nn][1][mm + 1], ai = Ai[nn][1][mm + 1];
+                double br = Ar[nn][1][-mm + 1], bi = Ai[nn][1][-mm + 1];
+                s += ((mm % 2) ? -1.0 : 1.0) * (ar * br - ai * bi);
+            }
+            q[q5_index(m, nn)] = s * s;
         }
 }
 
@@ -556,9 +626,10 @@ static double network(const omodel *m, int t, const double *q, double *dUdq)
     return U;
 }
 
-/* dU_i/d(r_ij) for the pair a of bead i, given dU_i/dq (grad). */
+/* dU_i/d(r_ij) for the pair a of bead i, given bead i's descriptors q and dU_i/dq
+ * (grad). */
 static void pair_gradient(const omodel *m, int n, const int *types, const double *w, const double box[3],
-                          const olist *l, int i, int a, const double *grad, double out[3])
+                          const olist *l, int i, int a, const double *q, const double *grad, double out[3])
 {
     int ti = types[i];
     const opair *pa = &l->p[a];
@@ -596,11 +667,44 @@ static void pair_gradient(const omodel *m, int n, const int *types, const double
             double ga = gA[nn], dga = dgA[nn];
             double gb = oracle_gn(coefA(m, ti, tb, nn), m->KA, rb, m->rcA[ti * m->T + tb]);
             for (int ll = 1; ll <= m->L; ++ll) {
-                double G = grad[m->nR + (ll - 1) * m->nA + nn] * 2.0 * (2.0 * ll + 1.0) / (4.0 * M_PI);
+                double dq = grad[m->nR + (ll - 1) * m->nA + nn];
+                if (ll == 1 && m->L5) dq += 2.0 * q[m->nR + nn] * grad[q5_index(m, nn)];  /* q5 = q_n1^2 */
+                double G = dq * 2.0 * (2.0 * ll + 1.0) / (4.0 * M_PI);
                 double P = oracle_legendre(ll, c), dP = oracle_dlegendre(ll, c);
                 for (int k = 0; k < 3; ++k) out[k] += G * (dga * gb * P * ua[k] + ga * gb * dP * t[k]);
             }
         }
+    }
+    if (!m->L4) return;
+    /* four-body: d q4 / d r_a = 3 kappa tr(Q^2 dQ/dr_a), Q = sum_b g(r_b) (u_b u_b^T - I/3) */
+    const double kappa = oracle_wigner3j(2, 2, 2, 0, 0, 0) * pow(5.0 / (4.0 * M_PI), 1.5) * 4.5;
+    for (int nn = 0; nn < m->nA; ++nn) {
+        double Q[3][3] = {{0}};
+        for (int b = l->start[i]; b < l->start[i + 1]; ++b) {
+            const opair *pb = &l->p[b];
+            if (!pb->inA) continue;
+            int tb = types[pb->j];
+            double db[3];
+            pair_vec(w, n, box, i, pb, db);
+            double rb = sqrt(db[0] * db[0] + db[1] * db[1] + db[2] * db[2]);
+            double gb = oracle_gn(coefA(m, ti, tb, nn), m->KA, rb, m->rcA[ti * m->T + tb]);
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y) Q[x][y] += gb * (db[x] * db[y] / (rb * rb) - (x == y ? 1.0 / 3.0 : 0.0));
+        }
+        double Q2[3][3], trQ2 = 0.0;
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) {
+                Q2[x][y] = Q[x][0] * Q[0][y] + Q[x][1] * Q[1][y] + Q[x][2] * Q[2][y];
+                if (x == y) trQ2 += Q2[x][y];
+            }
+        double Q2u[3], uQ2u = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            Q2u[x] = Q2[x][0] * ua[0] + Q2[x][1] * ua[1] + Q2[x][2] * ua[2];
+            uQ2u += ua[x] * Q2u[x];
+        }
+        double G = 3.0 * kappa * grad[q4_index(m, nn)];
+        for (int k = 0; k < 3; ++k)
+            out[k] += G * (dgA[nn] * (uQ2u - trQ2 / 3.0) * ua[k] + 2.0 * gA[nn] * (Q2u[k] - uQ2u * ua[k]) / ra);
     }
 }
 
@@ -624,7 +728,7 @@ static int reverse_pair(const olist *l, int i, const opair *p)
  *          1 = Legendre double sum.
  * Returns 0, or -1 on allocation failure / missing reverse pair.
  */
-int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
+int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int L4, int L5, int H,
                    const double *rcR, const double *rcA, const double *cR, const double *cA,
                    const double *w0, const double *b0, const double *w1, const double *b1,
                    int n, const int *types, const double *pos, const double box[3], const int pbc[3],
@@ -632,8 +736,8 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
                    double *energy_total, double *virial_total, double *U, double *F, double *W,
                    double *q_out)
 {
-    omodel m = {T, nR, nA, KR, KA, L, H, rcR, rcA, cR, cA, w0, b0, w1, b1};
-    if (L > 4 || nA > 16 || nR > 16) return -1;
+    omodel m = {T, nR, nA, KR, KA, L, L4, L5, H, rcR, rcA, cR, cA, w0, b0, w1, b1};
+    if (L < 1 || L > 4 || nA > 16 || nR > 16 || (L4 != 0 && L4 != 2) || (L5 != 0 && L5 != 1)) return -1;
     int D = ndes(&m);
     double *w = (double *)malloc((size_t)3 * n * sizeof(double) + 8);
     oracle_wrap(n, pos, box, pbc, w);
@@ -654,13 +758,14 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
         memset(is_sample, 1, (size_t)n);
     }
     double *grad = (double *)calloc((size_t)n * D, sizeof(double));
+    double *qall = (double *)calloc((size_t)n * D, sizeof(double));
     double *Ui = (double *)calloc((size_t)n, sizeof(double));
     double *pg = (double *)calloc((size_t)l.start[n] * 3 + 3, sizeof(double));
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < n; ++i) {
         if (!need[i]) continue;
-        double q[16 + 16 * 4];
+        double *q = qall + (size_t)i * D;
         descriptor_ylm(&m, n, types, w, box, &l, i, q);
         if (q_route == 1) descriptor_legendre(&m, n, types, w, box, &l, i, q);
         Ui[i] = network(&m, types[i], q, grad + (size_t)i * D);
@@ -671,7 +776,8 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
     for (int i = 0; i < n; ++i) {
         if (!need[i]) continue;
         for (int a = l.start[i]; a < l.start[i + 1]; ++a)
-            pair_gradient(&m, n, types, w, box, &l, i, a, grad + (size_t)i * D, pg + (size_t)a * 3);
+            pair_gradient(&m, n, types, w, box, &l, i, a, qall + (size_t)i * D, grad + (size_t)i * D,
+                          pg + (size_t)a * 3);
     }
     /* F_i = sum_j (dU_i/dr_ij - dU_j/dr_ji);  W_i = sum_j r_ij (x) dU_j/dr_ji  (Eq. 15) */
 #pragma omp parallel for schedule(dynamic, 16)
@@ -707,7 +813,7 @@ int oracle_compute(int T, int nR, int nA, int KR, int KA, int L, int H,
             virial_total[k] = s;
         }
     }
-    free(grad); free(Ui); free(pg); free(need); free(is_sample);
+    free(grad); free(qall); free(Ui); free(pg); free(need); free(is_sample);
     free_list(&l);
     free(w);
     return err ? -1 : 0;
@@ -773,7 +879,7 @@ void oracle_heat_current(int n, const int *types, const double *masses, const do
  * kinetic energy after each step.  heat (optional) [n_steps][6]: J_pot and J_kin
  * (eV Angstrom / fs) after each step, thermostat included.
  */
-int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
+int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int L4, int L5, int H,
               const double *rcR, const double *rcA, const double *cR, const double *cA,
               const double *w0, const double *b0, const double *w1, const double *b1,
               int n, const int *types, double *pos, double *vel, double *force, const double *masses,
@@ -792,7 +898,7 @@ int oracle_md(int T, int nR, int nA, int KR, int KA, int L, int H,
             }
         }
         double e, vt[9];
-        if (oracle_compute(T, nR, nA, KR, KA, L, H, rcR, rcA, cR, cA, w0, b0, w1, b1, n, types, pos, box, pbc,
+        if (oracle_compute(T, nR, nA, KR, KA, L, L4, L5, H, rcR, rcA, cR, cA, w0, b0, w1, b1, n, types, pos, box, pbc,
                            use_cells, NULL, 0, 0, &e, vt, U, force, W, NULL)) {
             free(U); free(W);
             return -1;

@@ -47,9 +47,11 @@ def lib():
         _lib.oracle_ylm.restype = None
         _lib.oracle_neighbors.argtypes = [i, p, p, i, p, p, p, p, i, C.c_long, p]
         _lib.oracle_neighbors.restype = C.c_long
-        _lib.oracle_compute.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, i, p, i, i, p, p, p, p, p, p]
+        _lib.oracle_wigner3j.argtypes = [i] * 6
+        _lib.oracle_wigner3j.restype = d
+        _lib.oracle_compute.argtypes = [i] * 9 + [p] * 8 + [i, p, p, p, p, i, p, i, i, p, p, p, p, p, p]
         _lib.oracle_compute.restype = i
-        _lib.oracle_md.argtypes = [i] * 7 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p, d, d, p, p, p]
+        _lib.oracle_md.argtypes = [i] * 9 + [p] * 8 + [i, p, p, p, p, p, p, p, i, i, d, p, d, d, p, p, p]
         _lib.oracle_md.restype = i
         _lib.oracle_hnemd_force.argtypes = [i, p, p, p]
         _lib.oracle_hnemd_force.restype = None
@@ -117,6 +119,10 @@ def assoc_legendre(l, m, x):
     return lib().oracle_assoc_legendre(int(l), int(m), float(x))
 
 
+def wigner3j(j1, j2, j3, m1, m2, m3):
+    return lib().oracle_wigner3j(int(j1), int(j2), int(j3), int(m1), int(m2), int(m3))
+
+
 def ylm(l, m, theta, phi):
     re, im = C.c_double(), C.c_double()
     lib().oracle_ylm(int(l), int(m), float(theta), float(phi), C.byref(re), C.byref(im))
@@ -158,7 +164,7 @@ def _model_args(m):
     arrs = [_f64(m.rc_radial), _f64(m.rc_angular), _f64(m.c_radial), _f64(m.c_angular),
             _f64(m.w0), _f64(m.b0), _f64(m.w1), _f64(m.b1)]
     ints = [m.n_types, m.n_desc_radial, m.n_desc_angular, m.n_basis_radial, m.n_basis_angular,
-            m.l_max, m.hidden]
+            m.l_max, getattr(m, "l_max_4b", 0), getattr(m, "l_max_5b", 0), m.hidden]
     return ints, arrs
 
 
@@ -249,7 +255,7 @@ def wrap(system):
 
 
 __all__ = ["cg_map", "fc", "dfc", "fk", "dfk", "chebyshev", "dchebyshev", "gn", "dgn", "legendre", "dlegendre",
-           "assoc_legendre", "ylm", "neighbors", "compute", "md", "hnemd_force",
+           "assoc_legendre", "wigner3j", "ylm", "neighbors", "compute", "md", "hnemd_force",
            "heat_current", "wrap", "OracleResult", "lib"]
 
 

@@ -54,7 +54,10 @@ class ModelParams:
       b0                      [T][H]             hidden-layer biases
       w1                      [T][H]             output weights
       b1                      [T]                output bias
-    with n_R = n_max^R + 1, K_R = N_bas^R + 1, N_des = n_R + n_A * l_max.
+    with n_R = n_max^R + 1, K_R = N_bas^R + 1, and
+    N_des = n_R + n_A * (l_max + [l_max_4b = 2] + [l_max_5b = 1]): the four-body
+    descriptors q4_n (l = 2) follow the three-body ones, then the five-body q5_n
+    (l = 1); l_max_4b is 0 or 2, l_max_5b 0 or 1.
     """
 
     n_types: int
@@ -72,10 +75,16 @@ class ModelParams:
     b0: np.ndarray
     w1: np.ndarray
     b1: np.ndarray
+    l_max_4b: int = 0
+    l_max_5b: int = 0
 
     @property
     def n_des(self) -> int:
-        return self.n_desc_radial + self.n_desc_angular * self.l_max
+        return n_descriptors(self.n_desc_radial, self.n_desc_angular, self.l_max, self.l_max_4b, self.l_max_5b)
+
+
+def n_descriptors(n_desc_radial, n_desc_angular, l_max, l_max_4b=0, l_max_5b=0) -> int:
+    return n_desc_radial + n_desc_angular * (l_max + (l_max_4b > 0) + (l_max_5b > 0))
 
 
 def pair_table(n_types: int, per_type, mix: str = "mean") -> np.ndarray:
@@ -90,13 +99,13 @@ def pair_table(n_types: int, per_type, mix: str = "mean") -> np.ndarray:
 
 def random_model(n_types=1, n_desc_radial=5, n_desc_angular=4, n_basis_radial=8,
                  n_basis_angular=8, l_max=4, hidden=30, rc_radial=8.0, rc_angular=5.0,
-                 seed=0, scale=0.1) -> ModelParams:
+                 seed=0, scale=0.1, l_max_4b=0, l_max_5b=0) -> ModelParams:
     """Random-weight model: every parameter ~ N(0, scale^2), drawn in the order
     c_radial, c_angular, w0, b0, w1, b1.  rc_* are scalars (uniform table) or
     [T][T] tables."""
     rng = np.random.default_rng(seed)
     T = n_types
-    n_des = n_desc_radial + n_desc_angular * l_max
+    n_des = n_descriptors(n_desc_radial, n_desc_angular, l_max, l_max_4b, l_max_5b)
 
     def table(v):
         v = np.asarray(v, dtype=np.float64)
@@ -109,7 +118,8 @@ def random_model(n_types=1, n_desc_radial=5, n_desc_angular=4, n_basis_radial=8,
     w1 = scale * rng.standard_normal((T, hidden))
     b1 = scale * rng.standard_normal((T,))
     return ModelParams(T, n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular,
-                       l_max, hidden, table(rc_radial), table(rc_angular), cR, cA, w0, b0, w1, b1)
+                       l_max, hidden, table(rc_radial), table(rc_angular), cR, cA, w0, b0, w1, b1,
+                       l_max_4b, l_max_5b)
 
 
 # ----------------------------------------------------------------------------
