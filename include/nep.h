@@ -10,6 +10,8 @@
  *   q_n   = sum_{j != i} g_n(r_ij),            0 <= n < n_R           (Eq. 3)
  *   q_nl  = sum_m (-1)^m A_nlm A_nl(-m),        1 <= l <= l_max        (Eq. 4)
  *   A_nlm = sum_{j != i} g_n(r_ij) Y_lm(r_ij),  0 <= n < n_A           (Eq. 5)
+ *   q4_n  = sum_{m1 m2 m3} (2 2 2; m1 m2 m3) A_n2m1 A_n2m2 A_n2m3     (four-body)
+ *   q5_n  = (q_n1)^2                                                  (five-body)
  *   g_n(r) = sum_{k < K} c^{t_i t_j}_{nk} f_k(r)                        (Eq. 6)
  *   f_k(r) = 1/2 [T_k(2 (r/r_c - 1)^2 - 1) + 1] f_c(r)                  (Eq. 7)
  *   f_c(r) = 1/2 [1 + cos(pi r / r_c)] for r < r_c, else 0              (Eq. 8)
@@ -17,7 +19,11 @@
  *   W_i = sum_{j != i} r_ij (x) dU_j/dr_ji,  r_ij = r_j - r_i           (Eq. 15)
  *   W   = sum_i W_i                                                    (Eq. 16)
  * The radial descriptors use the radial cutoff and basis size, the angular ones
- * the angular cutoff and basis size (Sec. II.A).  Type information enters only
+ * the angular cutoff and basis size (Sec. II.A).  Sec. II.A takes the four- and
+ * five-body terms from the GPUMD paper (Fan et al., J. Chem. Phys. 157, 114801,
+ * 2022); the forms above are the cubic invariant of the l = 2 moments (Wigner 3j
+ * coupling, complex orthonormal Y_lm) and the quartic invariant of the l = 1
+ * moments, each the only rotational invariant of its degree.  Type information enters only
  * through c^{t_i t_j}, the per-type network and the per-pair cutoffs.
  *
  * Conventions
@@ -93,25 +99,32 @@ const char* nep_last_error(void);
  *   n_desc_radial      n_R = n_max^R + 1 radial descriptors (Eq. 3)
  *   n_desc_angular     n_A = n_max^A + 1 radial functions of the angular part
  *   l_max              l_max^3b (Eq. 4); currently 4
+ *   l_max_4b           0 (no four-body term) or 2 (q4_n, n < n_A)
+ *   l_max_5b           0 (no five-body term) or 1 (q5_n, n < n_A)
  *   hidden             N_neu, hidden-layer width (Eq. 2)
  *   c_radial[T][T][n_R][K_R], c_angular[T][T][n_A][K_A]   c^{t_i t_j}_{nk} (Eq. 6)
  *   w0[T][H][N_des], b0[T][H], w1[T][H], b1[T]            per-type network (Eq. 2)
- *     with N_des = n_R + n_A * l_max, descriptor order q_0..q_{n_R-1}, then for
- *     l = 1..l_max, n = 0..n_A-1: q_nl.
+ *     with N_des = n_R + n_A * (l_max + [l_max_4b = 2] + [l_max_5b = 1]),
+ *     descriptor order q_0..q_{n_R-1}, then for l = 1..l_max, n = 0..n_A-1: q_nl,
+ *     then q4_0..q4_{n_A-1} (if present), then q5_0..q5_{n_A-1} (if present).
+ *     The four- and five-body terms share the angular g_n (c_angular).
  *   precision          NEP_FP64, NEP_FP32 or NEP_FP32_BF16
  * All arrays are host memory, row-major double, read during the call only.
- * Returns NEP_ERR_UNSUPPORTED for (n_R, n_A, K_R, K_A, l_max) without a compiled
- * kernel; the compiled set is listed by nep_supported_shape().
+ * Returns NEP_ERR_UNSUPPORTED for (n_R, n_A, K_R, K_A, l_max, l_max_4b, l_max_5b)
+ * without a compiled kernel; the compiled set is listed by nep_supported_shape().
+ * Models batched together (nep_compute_batch) must agree on whether any
+ * many-body term is present.
  */
 int nep_create(nep_model** out, int n_types, const double* rc_radial, const double* rc_angular,
                int n_basis_radial, int n_basis_angular, int n_desc_radial, int n_desc_angular,
-               int l_max, int hidden, const double* c_radial, const double* c_angular,
+               int l_max, int l_max_4b, int l_max_5b, int hidden, const double* c_radial,
+               const double* c_angular,
                const double* w0, const double* b0, const double* w1, const double* b1,
                int precision, int device);
 
 /* 1 if kernels for these sizes are compiled in, else 0. */
 int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial,
-                        int n_basis_angular, int l_max);
+                        int n_basis_angular, int l_max, int l_max_4b, int l_max_5b);
 
 /* Free the model and its device workspace.  NULL is accepted. */
 int nep_destroy(nep_model* m);

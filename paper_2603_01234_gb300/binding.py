@@ -71,9 +71,9 @@ def load(build_if_missing: bool = False):
     lib.nep_error_string.argtypes = [i]
     lib.nep_error_string.restype = C.c_char_p
     lib.nep_last_error.restype = C.c_char_p
-    lib.nep_create.argtypes = [C.POINTER(p), i, p, p, i, i, i, i, i, i, p, p, p, p, p, p, i, i]
+    lib.nep_create.argtypes = [C.POINTER(p), i, p, p, i, i, i, i, i, i, i, i, p, p, p, p, p, p, i, i]
     lib.nep_create.restype = i
-    lib.nep_supported_shape.argtypes = [i, i, i, i, i]
+    lib.nep_supported_shape.argtypes = [i] * 7
     lib.nep_supported_shape.restype = i
     lib.nep_destroy.argtypes = [p]
     lib.nep_destroy.restype = i
@@ -153,20 +153,26 @@ def nep_version():
     return load().nep_version()
 
 
-def nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max):
-    return bool(load().nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
+def nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max, l_max_4b=0,
+                        l_max_5b=0):
+    return bool(load().nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max,
+                                           l_max_4b, l_max_5b))
 
 
 def nep_create(params, precision=NEP_FP32, device=0):
     """params: an inputs.ModelParams.  Returns an opaque handle (c_void_p)."""
     lib = load()
     h = C.c_void_p()
+    T, H = params.n_types, params.hidden
+    if np.size(params.w0) != T * H * params.n_des:
+        raise ValueError(f"w0 has {np.size(params.w0)} entries, expected [T][H][N_des] = {T * H * params.n_des}")
     arrs = [_host(params.rc_radial, np.float64), _host(params.rc_angular, np.float64),
             _host(params.c_radial, np.float64), _host(params.c_angular, np.float64),
             _host(params.w0, np.float64), _host(params.b0, np.float64), _host(params.w1, np.float64),
             _host(params.b1, np.float64)]
     _check(lib.nep_create(C.byref(h), params.n_types, _ptr(arrs[0]), _ptr(arrs[1]), params.n_basis_radial,
                           params.n_basis_angular, params.n_desc_radial, params.n_desc_angular, params.l_max,
+                          int(getattr(params, "l_max_4b", 0)), int(getattr(params, "l_max_5b", 0)),
                           params.hidden, *[_ptr(a) for a in arrs[2:]], int(precision), int(device)), "nep_create")
     return h
 

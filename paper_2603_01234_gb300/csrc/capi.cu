@@ -165,6 +165,8 @@ struct nep_model {
     int device = 0;
     int precision = NEP_FP32;
     int T = 1, nR = 0, nA = 0, KR = 0, KA = 0, L = 4, H = 0, ND = 0, KRP = 0;
+    int L4 = 0, L5 = 0;  // l_max of the four-body (0 or 2) and five-body (0 or 1) terms
+    int MBT = 0;         // 1: the kernels carry both many-body blocks (ND counts them)
     double rc_max = 0.0;
     std::vector<double> rcR, rcA;
     ParamLayout off{};
@@ -487,6 +489,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.e_stride = p.Tmax * m->KRP;
     a.phi = m->phi.as<real>();
     a.net_bf16 = m->precision == NEP_FP32_BF16;
+    a.many_body = m->MBT;
     a.perm = m->perm.as<int>();
     a.force = force;
     a.virial = virial;
@@ -1167,9 +1170,11 @@ const char* nep_error_string(int code)
 
 const char* nep_last_error(void) { return g_last_error.c_str(); }
 
-int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial, int n_basis_angular, int l_max)
+int nep_supported_shape(int n_desc_radial, int n_desc_angular, int n_basis_radial, int n_basis_angular, int l_max,
+                        int l_max_4b, int l_max_5b)
 {
-    return l_max == 4 && evaluate_shape_supported<float>(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular);
+    return l_max == 4 && (l_max_4b == 0 || l_max_4b == 2) && (l_max_5b == 0 || l_max_5b == 1) &&
+           evaluate_shape_supported<float>(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular);
 }
 
 int nep_destroy(nep_model* m)
@@ -1202,7 +1207,8 @@ int nep_destroy(nep_model* m)
 }
 
 int nep_create(nep_model** out, int n_types, const double* rc_radial, const double* rc_angular, int n_basis_radial,
-               int n_basis_angular, int n_desc_radial, int n_desc_angular, int l_max, int hidden,
+               int n_basis_angular, int n_desc_radial, int n_desc_angular, int l_max, int l_max_4b, int l_max_5b,
+               int hidden,
                const double* c_radial, const double* c_angular, const double* w0, const double* b0, const double* w1,
                const double* b1, int precision, int device)
 {
@@ -1214,7 +1220,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
         return fail(NEP_ERR_ARG, "unknown precision");
     if (!rc_radial || !rc_angular || !c_radial || !c_angular || !w0 || !b0 || !w1 || !b1)
         return fail(NEP_ERR_ARG, "null parameter array");
-    if (!nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max))
+    if (!nep_supported_shape(n_desc_radial, n_desc_angular, n_basis_radial, n_basis_angular, l_max, l_max_4b,
+                             l_max_5b))
         return fail(NEP_ERR_UNSUPPORTED, "no compiled kernel for these descriptor / basis sizes");
     const int T = n_types;
     for (int a = 0; a < T; ++a)
@@ -1239,8 +1246,15 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     m->KR = n_basis_radial;
     m->KA = n_basis_angular;
     m->L = l_max;
+    m->L4 = l_max_4b;
+    m->L5 = l_max_5b;
+    m->MBT = (l_max_4b > 0 || l_max_5b > 0) ? 1 : 0;
     m->H = hidden;
-    m->ND = m->nR + m->nA * m->L;
+    // device layout: with MBT both many-body blocks are present (q4 then q5); a
+    // model with only one of them gets zero weights on the other, which changes no
+    // sum (0 * q adds an exact zero) and no gradient
+    m->ND = m->nR + m->nA * (m->L + 2 * m->MBT);
+    const int nd_user = m->nR + m->nA * (m->L + (l_max_4b > 0) + (l_max_5b > 0));
     m->KRP = (m->KR + 3) & ~3;
     m->rcR.assign(rc_radial, rc_radial + T * T);
     m->rcA.assign(rc_angular, rc_angular + T * T);
@@ -1285,7 +1299,19 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
         std::copy(c_angular + (size_t)k * m->nA * m->KA, c_angular + (size_t)(k + 1) * m->nA * m->KA,
                   h.begin() + o.cA + k * cAs);
     }
-    std::copy(w0, w0 + T * hidden * m->ND, h.begin() + o.w0);
+    for (int t = 0; t < T; ++t)
+        for (int mu = 0; mu < hidden; ++mu) {
+            const double* src = w0 + ((size_t)t * hidden + mu) * nd_user;
+            double* dst = h.data() + o.w0 + ((size_t)t * hidden + mu) * m->ND;
+            const int d3 = m->nR + m->nA * m->L;
+            std::copy(src, src + d3, dst);
+            int k = d3;
+            if (l_max_4b > 0) {
+                std::copy(src + k, src + k + m->nA, dst + d3);
+                k += m->nA;
+            }
+            if (l_max_5b > 0) std::copy(src + k, src + k + m->nA, dst + d3 + m->nA);
+        }
     std::copy(b0, b0 + T * hidden, h.begin() + o.b0);
     std::copy(w1, w1 + T * hidden, h.begin() + o.w1);
     std::copy(b1, b1 + T, h.begin() + o.b1);
@@ -1315,7 +1341,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             for (int t = 0; t < T; ++t)
                 for (int mu = 0; mu < hidden; ++mu)
                     for (int v = 0; v < nd; ++v) {
-                        const uint16_t b = bf16(w0[((size_t)t * hidden + mu) * nd + v]);
+                        const uint16_t b = bf16(h[o.w0 + ((size_t)t * hidden + mu) * nd + v]);
                         wf[((size_t)t * hp + mu) * sf + v] = b;   // [t][mu][v]: X = Q W0^T
                         wb[((size_t)t * ndp + v) * sb + mu] = b;  // [t][v][mu]: dQ = D W0
                     }
@@ -1385,7 +1411,7 @@ int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const i
         const nep_model* o = models[k];
         if (!o) return fail(NEP_ERR_ARG, "null model in batch");
         if (o->device != m->device || o->precision != m->precision || o->nR != m->nR || o->nA != m->nA ||
-            o->KR != m->KR || o->KA != m->KA || o->L != m->L)
+            o->KR != m->KR || o->KA != m->KA || o->L != m->L || o->MBT != m->MBT)
             return fail(NEP_ERR_ARG, "batched models must share device, precision and descriptor sizes");
     }
     Guard guard(m->device);
@@ -1839,6 +1865,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.e_stride = m->T * m->KRP;
     a.phi = (real*)(base + L.phi);
     a.net_bf16 = m->precision == NEP_FP32_BF16;
+    a.many_body = m->MBT;
     a.perm = (int*)(base + L.perm);
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;

@@ -382,10 +382,50 @@ __device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off,
     __syncwarp();
 }
 
-template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0>
+// Four-body invariant of one radial channel's l = 2 moments and its gradient.
+// a[0..4] are A_n2m in the real basis of sh_eval (xy, yz, 2z^2 - x^2 - y^2, xz,
+// x^2 - y^2).  sum_m a_m Y_2m(u) = u^T M u for the traceless symmetric M built
+// below, and M = 15 / (8 pi) Q with Q = sum_j g_j (u_j u_j^T - I/3) (addition
+// theorem for l = 2).  The Wigner-coupled triple product
+// sum (2 2 2; m1 m2 m3) A_2m1 A_2m2 A_2m3 is the cubic invariant kappa tr(Q^3),
+// kappa = (2 2 2; 0 0 0) (5 / 4 pi)^(3/2) 9/2, so q4 = kQ4 tr(M^3) with
+// kQ4 = kappa (8 pi / 15)^3 = -32 sqrt(14) pi^(3/2) / 525.  d tr(M^3) / dM = 3 M^2.
+constexpr double kQ4 = -1.2699291782903164;
+constexpr double kY2xy = 1.0925484305920792;  // sqrt(15 / 4 pi): Y_2 of xy, yz, xz
+constexpr double kY2zz = 0.31539156525252005; // sqrt(5 / 16 pi): Y_2 of 2z^2 - x^2 - y^2
+constexpr double kY2xx = 0.5462742152960396;  // sqrt(15 / 16 pi): Y_2 of x^2 - y^2
+
+template <typename real>
+__device__ __forceinline__ real four_body(const real* a, real* grad)
+{
+    const real c1 = real(kY2xy), c0 = real(kY2zz), c2 = real(kY2xx);
+    const real hxy = real(0.5) * c1 * a[0], hyz = real(0.5) * c1 * a[1], hxz = real(0.5) * c1 * a[3];
+    const real mxx = c2 * a[4] - c0 * a[2], myy = -c2 * a[4] - c0 * a[2], mzz = real(2) * c0 * a[2];
+    // M^2 (symmetric)
+    const real sxx = mxx * mxx + hxy * hxy + hxz * hxz;
+    const real syy = hxy * hxy + myy * myy + hyz * hyz;
+    const real szz = hxz * hxz + hyz * hyz + mzz * mzz;
+    const real sxy = mxx * hxy + hxy * myy + hxz * hyz;
+    const real sxz = mxx * hxz + hxy * hyz + hxz * mzz;
+    const real syz = hxy * hxz + myy * hyz + hyz * mzz;
+    const real tr3 = mxx * sxx + myy * syy + mzz * szz + real(2) * (hxy * sxy + hxz * sxz + hyz * syz);
+    // dq4/da_m = kQ4 * 3 * sum_ab (M^2)_ab dM_ab/da_m
+    const real k3 = real(3 * kQ4);
+    grad[0] = k3 * c1 * sxy;
+    grad[1] = k3 * c1 * syz;
+    grad[2] = k3 * c0 * (real(2) * szz - sxx - syy);
+    grad[3] = k3 * c1 * sxz;
+    grad[4] = k3 * c2 * (sxx - syy);
+    return real(kQ4) * tr3;
+}
+
+template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0, int MBT = 0>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descriptor(EvalArgs<real> a)
 {
-    constexpr int ND = NR + NA * 4;
+    // MBT = 1: the four-body q4_n (l = 2) and five-body q5_n = q_n1^2 follow the
+    // three-body descriptors (both always; a model with one of them has zero weights
+    // on the other)
+    constexpr int ND = NR + NA * (4 + 2 * MBT);
     constexpr int KRP = (KR + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
@@ -497,6 +537,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     for (int nn = 0; nn < NA; ++nn)
 #pragma unroll
         for (int k = 0; k < kNLM; ++k) q[NR + (l_of(k) - 1) * NA + nn] += A[nn][k] * A[nn][k];
+    // four- and five-body terms; g4 keeps dq4/dA_n2m for the adjoint below
+    real g4[MBT ? NA : 1][5];
+    if constexpr (MBT == 1) {
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) {
+            q[NR + 4 * NA + nn] = four_body(&A[nn][3], g4[nn]);
+            q[NR + 5 * NA + nn] = q[NR + nn] * q[NR + nn];
+        }
+    }
 
     // ---- network (Eq. 2) and dU/dq ----
     real U;
@@ -544,11 +593,23 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     constexpr int NAP = phi_pad(NA);
     real* ph = a.phi + (size_t)i * NAP;
     const size_t kstride = (size_t)a.n * NAP;
+    if constexpr (MBT == 1) {
+        // dq5/dA_n1m = 2 q_n1 dq_n1/dA_n1m: fold into the l = 1 coefficient
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) dq[NR + nn] += real(2) * q[NR + nn] * dq[NR + 5 * NA + nn];
+    }
 #pragma unroll
     for (int k = 0; k < kNLM; ++k)
 #pragma unroll
-        for (int nn = 0; nn < NAP; ++nn)
-            ph[k * kstride + nn] = nn < NA ? real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k] : real(0);
+        for (int nn = 0; nn < NAP; ++nn) {
+            real v = real(0);
+            if (nn < NA) {
+                v = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+                if constexpr (MBT == 1)
+                    if (k >= 3 && k < 8) v += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
+            }
+            ph[k * kstride + nn] = v;
+        }
 }
 
 template <typename real>
@@ -1063,8 +1124,14 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
         cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_>,                         \
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
         if (e != cudaSuccess) return e;                                                                       \
+        e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 0, 1>,                               \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);                \
+        if (e != cudaSuccess) return e;                                                                       \
         if constexpr (sizeof(real) == 4) {                                                                    \
             e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 1>,                              \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);            \
+            if (e != cudaSuccess) return e;                                                                   \
+            e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 1, 1>,                           \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);            \
             if (e != cudaSuccess) return e;                                                                   \
         }                                                                                                     \
@@ -1088,6 +1155,20 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
     return cudaErrorInvalidValue;
 }
 
+template <typename real, int NR, int NA, int KR, int KA, int MBT>
+void launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_t st, int mb_desc)
+{
+    if constexpr (sizeof(real) == 4) {
+        if (a.net_bf16) {
+            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 1, MBT><<<nb, kBlock, smem, st>>>(a);
+            else k_descriptor<real, NR, NA, KR, KA, 3, 1, MBT><<<nb, kBlock, smem, st>>>(a);
+            return;
+        }
+    }
+    if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT><<<nb, kBlock, smem, st>>>(a);
+    else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT><<<nb, kBlock, smem, st>>>(a);
+}
+
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force)
@@ -1098,16 +1179,10 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
     }
 #define NEP_CASE(a_, b_, c_, d_)                                                                            \
     if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                     \
-        if (sizeof(real) == 4 && a.net_bf16) {                                                              \
-            if constexpr (sizeof(real) == 4) {                                                              \
-                if (mb_desc == 2) k_descriptor<real, a_, b_, c_, d_, 2, 1><<<nb, kBlock, smem_desc, st>>>(a); \
-                else k_descriptor<real, a_, b_, c_, d_, 3, 1><<<nb, kBlock, smem_desc, st>>>(a);            \
-            }                                                                                               \
-        } else if (mb_desc == 2) {                                                                          \
-            k_descriptor<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_desc, st>>>(a);                        \
-        } else {                                                                                            \
-            k_descriptor<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_desc, st>>>(a);                        \
-        }                                                                                                   \
+        if (a.many_body)                                                                                    \
+            launch_descriptor<real, a_, b_, c_, d_, 1>(a, nb, smem_desc, st, mb_desc);                      \
+        else                                                                                                \
+            launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc);                      \
         if (mid) cudaEventRecord(mid, st);                                                                  \
         if constexpr (sizeof(real) == 4) {                                                                  \
             if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \

@@ -174,6 +174,7 @@ struct EvalArgs {
     int e_stride;               // Tmax * KRP
     real* phi;                  // [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
     int net_bf16;               // 1: the hidden layer's products in BF16 on tensor cores
+    int many_body;              // 1: the four- and five-body descriptors follow the three-body ones
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null

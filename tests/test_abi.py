@@ -41,6 +41,12 @@ def test_status_strings_and_version():
     assert binding.nep_version() >= 1
     assert binding.nep_supported_shape(5, 4, 8, 8, 4)
     assert not binding.nep_supported_shape(3, 2, 5, 5, 4)
+    # four-body l = 2 and five-body l = 1 terms, alone or together
+    for l4, l5 in [(2, 0), (0, 1), (2, 1)]:
+        assert binding.nep_supported_shape(5, 4, 8, 8, 4, l4, l5)
+        assert binding.nep_supported_shape(5, 5, 9, 9, 4, l4, l5)
+    for l4, l5 in [(1, 0), (3, 0), (0, 2), (4, 1)]:
+        assert not binding.nep_supported_shape(5, 4, 8, 8, 4, l4, l5)
 
 
 def test_create_rejects_bad_arguments_without_device():
@@ -53,6 +59,14 @@ def test_create_rejects_bad_arguments_without_device():
     with pytest.raises(binding.NepError) as e:
         binding.nep_create(m)
     assert e.value.code == binding.NEP_ERR_UNSUPPORTED
+    m = inputs.random_model(l_max_4b=1)  # the four-body term exists for l = 2 only
+    with pytest.raises(binding.NepError) as e:
+        binding.nep_create(m)
+    assert e.value.code == binding.NEP_ERR_UNSUPPORTED
+    m = inputs.random_model(l_max_4b=2)
+    m.w0 = m.w0[:, :, :-1]  # w0 must hold N_des columns, four-body block included
+    with pytest.raises(ValueError):
+        binding.nep_create(m)
 
 
 def test_virial_correction_closed_form():
