@@ -43,7 +43,7 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 
 # DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
 # profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
-FORCE_TRAFFIC = {"evaluate_cu_sha1": "2ba3f727809c4627dc36cba5d47789f32d4e5184", "bytes_per_particle": 960.9,
+FORCE_TRAFFIC = {"evaluate_cu_sha1": "941eef7ada88dac38ae20a589266ca66c56ba9ae", "bytes_per_particle": 963.5,
                  "capture": "profiles/force_descriptor_water200k_ncu.md"}
 
 
@@ -405,42 +405,55 @@ def run_ours(args):
                  "how": "FP64 throughout, eager launches, same workload"}
         m64.close()
 
-    # BF16-weight network form: the same timed loop (graph replay per step, L2 flushed)
-    bf16 = None
-    if not args.quick:
-        mb = binding.Model(model, "bf16", device=local)
-        pb, vb = pos0.clone(), vel0_d.clone()
-        fb = torch.zeros_like(force)
+    def variant_leg(params, precision, dtype, how):
+        """Another model form on the same configuration, timed like the headline
+        (graph replay per step, L2 flushed between steps), plus its stage times."""
+        mv = binding.Model(params, precision, device=local)
+        pv, vv = pos0.clone(), vel0_d.clone()
+        fv_ = torch.zeros_like(force)
 
-        def step_b(k=1, fv=1):
-            binding.nep_md_step(mb.h, types, system.masses, system.box, system.pbc, pb, vb, fb, fv, k, DT_FS,
+        def step_v(k=1, fv=1):
+            binding.nep_md_step(mv.h, types, system.masses, system.box, system.pbc, pv, vv, fv_, fv, k, DT_FS,
                                 0, None, stream=sp)
-        step_b(k=0, fv=0)
+        step_v(k=0, fv=0)
         for _ in range(args.warmup):
             flush.zero_()
-            step_b()
-        kb = args.steps
-        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kb)]
+            step_v()
+        kv = args.steps
+        evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kv)]
         torch.cuda.synchronize()
-        for k in range(kb):
+        for k in range(kv):
             flush.zero_()
-            evb[k][0].record(stream)
-            step_b()
-            evb[k][1].record(stream)
+            evv[k][0].record(stream)
+            step_v()
+            evv[k][1].record(stream)
         torch.cuda.synchronize()
-        binding.nep_sync(mb.h)
-        msb = sum(x.elapsed_time(y) for x, y in evb)
-        binding.nep_set_timing(mb.h, 1)
-        for k in range(kb):
+        binding.nep_sync(mv.h)
+        msv = sum(x.elapsed_time(y) for x, y in evv)
+        binding.nep_set_timing(mv.h, 1)
+        for k in range(kv):
             flush.zero_()
-            step_b()
-        binding.nep_sync(mb.h)
-        stb, tsb = binding.nep_get_timing(mb.h)
-        binding.nep_set_timing(mb.h, 0)
-        bf16 = {"value": n * kb / (msb / 1000.0), "unit": UNIT, "steps": kb, "dtype": "f32 + bf16 W0",
-                "stages_ms_per_step": {k: v / max(1, tsb) for k, v in stb.items()},
-                "how": "BF16 hidden-layer weights, tensor-core network products; timed like the headline"}
-        mb.close()
+            step_v()
+        binding.nep_sync(mv.h)
+        stv, tsv = binding.nep_get_timing(mv.h)
+        binding.nep_set_timing(mv.h, 0)
+        mv.close()
+        return {"value": n * kv / (msv / 1000.0), "unit": UNIT, "steps": kv, "dtype": dtype,
+                "stages_ms_per_step": {k: v / max(1, tsv) for k, v in stv.items()}, "how": how}
+
+    bf16 = many_body = None
+    if not args.quick:
+        # BF16-weight network form
+        bf16 = variant_leg(model, "bf16", "f32 + bf16 W0",
+                           "BF16 hidden-layer weights, tensor-core network products; timed like the headline")
+        # the same model with the four-body (l = 2) and five-body (l = 1) descriptors added
+        mbp = inputs.ModelParams(**{k: getattr(model, k) for k in model.__dataclass_fields__})
+        mbp.l_max_4b, mbp.l_max_5b = 2, 1
+        extra = np.random.default_rng(77).standard_normal((model.n_types, model.hidden, 2 * model.n_desc_angular))
+        mbp.w0 = np.concatenate([model.w0, 0.1 * extra], axis=2)
+        many_body = variant_leg(mbp, "fp32", "f32",
+                                f"FP32 form with four- and five-body descriptors (N_des {mbp.n_des}); "
+                                "timed like the headline")
 
     m.close()
     serve = None
@@ -488,7 +501,8 @@ def run_ours(args):
                           "kernel plus its output kernel",
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
-            "steady_state_graph": steady, "plain_fp64": plain, "bf16_weights": bf16, "serving": serve}
+            "steady_state_graph": steady, "plain_fp64": plain, "bf16_weights": bf16, "many_body": many_body,
+            "serving": serve}
     print(json.dumps(line))
     return 0
 
