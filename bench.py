@@ -122,7 +122,7 @@ def algorithmic_flops(m, pairs_r, pairs_a, n):
     """
     nR, nA, KR, KA, H, T = (m.n_desc_radial, m.n_desc_angular, m.n_basis_radial, m.n_basis_angular, m.hidden,
                             m.n_types)
-    nd = nR + 4 * nA
+    nd = m.n_des
     basis = lambda K: 10 + 5 * (K - 2)  # noqa: E731
     basis_d = lambda K: 14 + 11 * (K - 2)  # noqa: E731
     d_r = 13 + basis(KR) + KR
@@ -480,6 +480,22 @@ def run_ours(args):
             "peak_note": FLOPS_PEAK_NOTE + f" ({sm_max:.0f} MHz max clock)"}
     if clk.get("sm_mhz"):
         roof["frac_at_median_clock"] = achieved / (152 * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+    # every kernel of the evaluation against its own bound, from the stage pass
+    kernels = {}
+    for k in ("descriptor_network", "force_virial"):
+        ms_k = stages[k] / max(1, tsteps)
+        kernels[k] = {"bound": "alu", "flop_per_launch": work[k], "ms_per_launch": ms_k,
+                      "achieved_tflops": work[k] / (ms_k / 1000.0) / 1e12,
+                      "frac": work[k] / (ms_k / 1000.0) / 1e12 / peak}
+    # neighbour lists: compulsory bytes = every record read once (16 B), both lists'
+    # entries written (4 B each) and the two counts (8 B) per particle
+    nb_bytes = 16 * n + 4 * (pairs_r + pairs_a) + 8 * n
+    ms_nb = stages["neighbor_lists"] / max(1, tsteps)
+    hbm = (peaks or {}).get("hbm_gbs") or 6800.0
+    kernels["neighbor_lists"] = {"bound": "hbm", "bytes_per_launch": nb_bytes, "ms_per_launch": ms_nb,
+                                 "achieved_gbs": nb_bytes / (ms_nb / 1000.0) / 1e9,
+                                 "peak_gbs": hbm, "frac": nb_bytes / (ms_nb / 1000.0) / 1e9 / hbm,
+                                 "note": "candidate distance checks (27 cells), not bytes, bound this kernel"}
 
     cpu = None
     if world == 1 and not args.no_cpu:
@@ -500,7 +516,7 @@ def run_ours(args):
                           "stages on the launch stream, L2 flushed before each step; force_virial is the force "
                           "kernel plus its output kernel",
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
-            "roofline": roof, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
             "steady_state_graph": steady, "plain_fp64": plain, "bf16_weights": bf16, "many_body": many_body,
             "serving": serve}
     print(json.dumps(line))

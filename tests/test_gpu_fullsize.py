@@ -1,7 +1,8 @@
-"""Full-size systems of the workloads (100,000-bead water, 200,000-bead four-type
-monolayer, 1,000,000-particle atom-and-bead nanowire) through the C ABI in the FP32
-form, against the oracle on sampled particles (the oracle evaluates a sample's
-neighbourhoods only), plus properties that hold at any size."""
+"""Full-size systems of the workloads (100,000-bead water, also with the four- and
+five-body terms, 200,000-bead four-type monolayer, 1,000,000-particle atom-and-bead
+nanowire) through the C ABI in the FP32 form, against the oracle on sampled
+particles (the oracle evaluates a sample's neighbourhoods only), plus properties
+that hold at any size."""
 import numpy as np
 import pytest
 
@@ -19,6 +20,10 @@ def workloads():
            lambda: inputs.monolayer(250, 200, seed=1002))
     yield ("nanowire1M", inputs.random_model(n_types=3, hidden=40, rc_radial=7.0, rc_angular=5.0, seed=4),
            lambda: inputs.nanowire(1_000_000, seed=1003))
+    # the water workload with the four-body (l = 2) and five-body (l = 1) terms added
+    yield ("water100k_4b5b", inputs.random_model(n_types=1, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=5,
+                                                 l_max_4b=2, l_max_5b=1),
+           lambda: inputs.water_box(100_000, seed=1004))
 
 
 @pytest.mark.parametrize("name,model,make", list(workloads()), ids=[w[0] for w in workloads()])
