@@ -1274,7 +1274,11 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.cR = p; p += TT * cRs;
     o.cA = p; p += TT * cAs;
     o.n_cut_coef = p;
-    o.w0 = p; p += T * hidden * m->ND;
+    // W0 rows: one type pads them to a multiple of 4 reals at a 16-byte aligned start
+    // (the descriptor kernel reads them as vectors); several types keep ND per row
+    const int w0s = T == 1 ? ((m->ND + 3) & ~3) : m->ND;
+    if (T == 1) p = (p + 3) & ~3;
+    o.w0 = p; p += T * hidden * w0s;
     o.b0 = p; p += T * hidden;
     o.w1 = p; p += T * hidden;
     o.b1 = p; p += T;
@@ -1302,7 +1306,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     for (int t = 0; t < T; ++t)
         for (int mu = 0; mu < hidden; ++mu) {
             const double* src = w0 + ((size_t)t * hidden + mu) * nd_user;
-            double* dst = h.data() + o.w0 + ((size_t)t * hidden + mu) * m->ND;
+            double* dst = h.data() + o.w0 + ((size_t)t * hidden + mu) * w0s;
             const int d3 = m->nR + m->nA * m->L;
             std::copy(src, src + d3, dst);
             int k = d3;
@@ -1341,7 +1345,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
             for (int t = 0; t < T; ++t)
                 for (int mu = 0; mu < hidden; ++mu)
                     for (int v = 0; v < nd; ++v) {
-                        const uint16_t b = bf16(h[o.w0 + ((size_t)t * hidden + mu) * nd + v]);
+                        const uint16_t b = bf16(h[o.w0 + ((size_t)t * hidden + mu) * w0s + v]);
                         wf[((size_t)t * hp + mu) * sf + v] = b;   // [t][mu][v]: X = Q W0^T
                         wb[((size_t)t * ndp + v) * sb + mu] = b;  // [t][v][mu]: dQ = D W0
                     }

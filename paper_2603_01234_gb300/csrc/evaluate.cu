@@ -170,6 +170,27 @@ __device__ __forceinline__ void walk4(const uint32_t* nl, size_t stride, int cnt
     if (s + 2 < cnt) body(q2);
 }
 
+// 4 consecutive reals (16-byte aligned) into registers
+__device__ __forceinline__ void load4(const float* p, float* o)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* o)
+{
+    const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+}
+
+template <typename real, int N>
+__device__ __forceinline__ void loadN(const real* p, real* o)
+{
+#pragma unroll
+    for (int k = 0; k + 3 < N; k += 4) load4(p + k, o + k);
+#pragma unroll
+    for (int k = N & ~3; k < N; ++k) o[k] = p[k];
+}
+
 __device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
 
@@ -556,21 +577,43 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         net_bf16<ND>(P, off, T, H, ti, q, U, dq, scratch);
         if (!live) return;
     } else {
-        const real* w0 = P + off.w0 + ti * H * ND;
         const real* b0 = P + off.b0 + ti * H;
         const real* w1 = P + off.w1 + ti * H;
         U = -P[off.b1 + ti];
 #pragma unroll
         for (int v = 0; v < ND; ++v) dq[v] = real(0);
-        for (int mu = 0; mu < H; ++mu) {
-            real x = -b0[mu];
+        if (T == 1) {
+            // one type: W0 rows padded to a multiple of 4 and 16-byte aligned, read as
+            // vectors once per hidden unit and kept for the gradient (every lane reads
+            // the same row, a broadcast)
+            constexpr int NDV = (ND + 3) & ~3;
+            const real* w0 = P + off.w0;
+            for (int mu = 0; mu < H; ++mu) {
+                real w[NDV];
+                loadN<real, NDV>(w0 + mu * NDV, w);
+                real x = -b0[mu];
 #pragma unroll
-            for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
-            const real h = tanh(x);
-            U += w1[mu] * h;
-            const real coef = w1[mu] * (real(1) - h * h);
+                for (int v = 0; v < ND; ++v) x += w[v] * q[v];
+                const real h = tanh(x);
+                U += w1[mu] * h;
+                const real coef = w1[mu] * (real(1) - h * h);
 #pragma unroll
-            for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
+                for (int v = 0; v < ND; ++v) dq[v] += coef * w[v];
+            }
+        } else {
+            // several types: unpadded rows (padded ones put the rows that lanes of
+            // different types read at once into the same shared-memory banks)
+            const real* w0 = P + off.w0 + ti * H * ND;
+            for (int mu = 0; mu < H; ++mu) {
+                real x = -b0[mu];
+#pragma unroll
+                for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
+                const real h = tanh(x);
+                U += w1[mu] * h;
+                const real coef = w1[mu] * (real(1) - h * h);
+#pragma unroll
+                for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
+            }
         }
     }
     a.U[i] = U;
@@ -671,27 +714,6 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& i
         totals[(size_t)it.req * 10 + threadIdx.x] = t;
     }
     if (threadIdx.x == 0) counter[it.req] = 0u;
-}
-
-// 4 consecutive reals (16-byte aligned) into registers
-__device__ __forceinline__ void load4(const float* p, float* o)
-{
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-__device__ __forceinline__ void load4(const double* p, double* o)
-{
-    const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
-    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
-}
-
-template <typename real, int N>
-__device__ __forceinline__ void loadN(const real* p, real* o)
-{
-#pragma unroll
-    for (int k = 0; k + 3 < N; k += 4) load4(p + k, o + k);
-#pragma unroll
-    for (int k = N & ~3; k < N; ++k) o[k] = p[k];
 }
 
 // Per-thread state of the force pass for one particle i.
