@@ -66,3 +66,16 @@ def test_static_scratch_rejects_oversize():
         _run(torch, binding.nep_compute_static, m, big, dev)
     assert e.value.code == binding.NEP_ERR_ARG and "4096" in str(e.value)
     m.close()
+
+
+def test_static_scratch_with_four_and_five_body_terms():
+    import torch
+    binding.load(build_if_missing=True)
+    dev = torch.device("cuda:0")
+    p = inputs.random_model(n_types=2, hidden=30, rc_radial=7.0, rc_angular=5.0, seed=24, l_max_4b=2, l_max_5b=1)
+    m = binding.Model(p, "fp32")
+    system = inputs.random_periodic(2500, [30.0, 30.0, 30.0], seed=25, min_dist=1.5, n_types=2)
+    ref = _run(torch, binding.nep_compute, m, system, dev)
+    got = _run(torch, binding.nep_compute_static, m, system, dev)
+    _close(got, ref)
+    m.close()
