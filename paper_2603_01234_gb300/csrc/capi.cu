@@ -463,6 +463,8 @@ int run_neighbors(nep_model* m, const Plan& p)
     a.cntR = m->cntR.as<int>();
     a.cntA = m->cntA.as<int>();
     a.maxcnt = m->flags.as<int>();
+    if ((uint64_t)std::max(a.mnR, a.mnA) * (uint64_t)a.n > (1ull << 32))
+        return fail(NEP_ERR_ARG, "neighbour lists beyond 2^32 entries (capacity x particles)");
     cudaError_t e = launch_neighbors<real>(a, (int)p.items.size(), p.smem_nbr, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     return NEP_OK;

@@ -227,9 +227,9 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         const real cR1 = cutR[0], cA1 = cutA[0];  // the one pair type of a one-type model
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
         const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
-        const size_t stride = (size_t)a.n;
-        uint32_t* outR = a.nlR + i;  // next slot of each list (column i, slot-major)
-        uint32_t* outA = a.nlA + i;
+        // slot s of particle i's list is entry s * n + i (slot-major); the launcher
+        // guarantees capacity * n <= 2^32, so the index fits 32 bits
+        const uint32_t stride = (uint32_t)a.n, col = (uint32_t)i;
         for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
             int z = cz + dz;
             if (g.pbc[2]) {  // |dz| <= 2, so at most two corrections even for one cell per axis
@@ -262,22 +262,26 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
                     // i itself (zero offset) is the one candidate at r = 0 to leave out
                     const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
                     // branch-free body: the tests predicate the stores and the counts
-#pragma unroll 2
-                    for (int k = kb; k < ke; ++k) {
-                        const PosRec<real> rj = ldg_rec(a.rec + k);
+                    auto candidate = [&](int k, const PosRec<real>& rj, real cR2, real cA2) {
                         const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
                         const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        const real cR2 = T == 1 ? cR1 : cutR[rj.t];
-                        const real cA2 = T == 1 ? cA1 : cutA[rj.t];
                         const uint32_t ent = (uint32_t)k | code;
                         const bool other = k != self;
                         const bool inR = (r2 < cR2) & other, inA = (r2 < cA2) & other;
-                        if (inR & (nr < a.mnR)) *outR = ent;
-                        if (inA & (na < a.mnA)) *outA = ent;
-                        outR += inR ? stride : 0;
-                        outA += inA ? stride : 0;
+                        if (inR & (nr < a.mnR)) a.nlR[(uint32_t)nr * stride + col] = ent;
+                        if (inA & (na < a.mnA)) a.nlA[(uint32_t)na * stride + col] = ent;
                         nr += inR;
                         na += inA;
+                    };
+                    if (T == 1) {  // one pair type: deeper unrolling (measured faster)
+#pragma unroll 4
+                        for (int k = kb; k < ke; ++k) candidate(k, ldg_rec(a.rec + k), cR1, cA1);
+                    } else {  // per-type cutoffs from shared memory (unroll 4 measured slower)
+#pragma unroll 2
+                        for (int k = kb; k < ke; ++k) {
+                            const PosRec<real> rj = ldg_rec(a.rec + k);
+                            candidate(k, rj, cutR[rj.t], cutA[rj.t]);
+                        }
                     }
                 }
             }
@@ -300,6 +304,9 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st)
 {
+    // the kernel indexes the slot-major lists with 32-bit slot * n + i
+    if ((unsigned long long)(a.mnR > a.mnA ? a.mnR : a.mnA) * (unsigned long long)a.n > (1ull << 32))
+        return cudaErrorInvalidValue;
     k_neighbors<real><<<n_items, kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
