@@ -76,6 +76,9 @@ def small_systems():
     yield "water512", water_model(), inputs.water_small()
     yield "water64_images", water_model(seed=5), inputs.water_box(64, seed=6)
     yield "water37_tiny_box", water_model(seed=7), inputs.water_box(37, seed=8)
+    # 1, 2 and 3 cells per periodic axis: every stencil row wraps and repeats cells as images
+    yield "box6x9x13_images", water_model(seed=16), inputs.random_periodic(8, [6.0, 9.0, 13.0], seed=17,
+                                                                             min_dist=1.5)
     yield "water1000", water_model(seed=9), inputs.water_box(1000, seed=10)
     yield "monolayer4types", monolayer_model(), inputs.monolayer(6, 5, seed=11)
     s = inputs.random_periodic(300, [16.0, 17.0, 18.0], seed=12, min_dist=1.4, n_types=2)
