@@ -85,6 +85,10 @@ def small_systems():
     yield "aacg300", aacg_model(), s
     w = inputs.nanowire(n_total=3000, n_cells_x=12, seed=13, margin=5.0)
     yield "nanowire3000", nanowire_model(), w
+    # six types with per-pair cutoffs (means of per-type values) and a ragged tail
+    m6 = inputs.random_model(n_types=6, hidden=24, rc_radial=inputs.pair_table(6, [5.0, 5.5, 6.0, 6.5, 7.0, 7.5]),
+                             rc_angular=inputs.pair_table(6, [4.0, 4.2, 4.4, 4.6, 4.8, 5.0]), seed=18)
+    yield "mix6types", m6, inputs.random_periodic(333, [17.0, 18.0, 19.0], seed=19, min_dist=1.5, n_types=6)
     # the second compiled shape: n_R = n_A = 5, K_R = K_A = 9 (n_A not a multiple of 4)
     m = inputs.random_model(n_types=2, n_desc_radial=5, n_desc_angular=5, n_basis_radial=9, n_basis_angular=9,
                             hidden=20, rc_radial=6.0, rc_angular=4.5, seed=14)
