@@ -344,8 +344,8 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
 
 /*
  * Autotuner.  The FP32 descriptor and force kernels are compiled in variants
- * that keep 2 or 3 thread blocks resident per SM (a register budget per
- * thread).  nep_autotune evaluates the configuration with every variant pair,
+ * that keep 2 or 3 (force: 2, 3 or 4) thread blocks resident per SM (a register
+ * budget per thread).  nep_autotune evaluates the configuration with every variant pair,
  * times them with CUDA events and keeps the fastest on the handle; the first
  * nep_md_step of a new configuration shape (n and cell grid) does the same
  * unless disabled.  All variants give identical results.  Inputs as in
@@ -354,7 +354,8 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
 int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
                  const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force);
 
-/* Set the variants (2 or 3) and whether MD calls tune automatically (1/0). */
+/* Set the variants (descriptor 2 or 3, force 2, 3 or 4) and whether MD calls tune
+ * automatically (1/0); other values give NEP_ERR_ARG. */
 int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force);
 
 /* The variants in use. */

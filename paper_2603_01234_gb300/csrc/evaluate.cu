@@ -1165,11 +1165,16 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
         if (e != cudaSuccess) return e;                                                                       \
     }
-#define NEP_CASE(a_, b_, c_, d_)                                  \
-    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {           \
-        NEP_SET(a_, b_, c_, d_, 2)                                \
-        NEP_SET(a_, b_, c_, d_, 3)                                \
-        return cudaSuccess;                                       \
+#define NEP_CASE(a_, b_, c_, d_)                                                                              \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                       \
+        NEP_SET(a_, b_, c_, d_, 2)                                                                            \
+        NEP_SET(a_, b_, c_, d_, 3)                                                                            \
+        if constexpr (sizeof(real) == 4) { /* the force kernel has a third variant, 4 blocks per SM */        \
+            cudaError_t e = cudaFuncSetAttribute(k_force_scatter<real, a_, b_, c_, d_, 4>,                   \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force); \
+            if (e != cudaSuccess) return e;                                                                   \
+        }                                                                                                     \
+        return cudaSuccess;                                                                                   \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE
@@ -1207,7 +1212,8 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
             launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc);                      \
         if (mid) cudaEventRecord(mid, st);                                                                  \
         if constexpr (sizeof(real) == 4) {                                                                  \
-            if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \
+            if (mb_force == 4) k_force_scatter<real, a_, b_, c_, d_, 4><<<nb, kBlock, smem_force, st>>>(a); \
+            else if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \
             else k_force_scatter<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);               \
             k_scatter_outputs<real><<<nb, kBlock, 0, st>>>(a);                                              \
         } else {                                                                                            \

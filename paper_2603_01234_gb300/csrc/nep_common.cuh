@@ -197,7 +197,8 @@ template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st);
 
 // Shape-dispatched evaluation; returns cudaErrorInvalidValue for an uncompiled shape.
-// mb_desc / mb_force: resident blocks per SM of the FP32 kernel variants (2 or 3).
+// mb_desc / mb_force: resident blocks per SM of the FP32 kernel variants (2 or 3; the
+// force kernel also 4).  The FP64 form has one effective variant of each.
 // The FP32 form needs a.acc (the scatter accumulators); the FP64 form ignores it.
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
