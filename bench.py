@@ -43,7 +43,7 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
 
 # DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
 # profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
-FORCE_TRAFFIC = {"evaluate_cu_sha1": "cb2be5e0300d9487fa1a9d8de7dc5b5279ba1396", "bytes_per_particle": 962.5,
+FORCE_TRAFFIC = {"evaluate_cu_sha1": "944e492b16cd527936ea261fd5fe3887b88d9b02", "bytes_per_particle": 962.7,
                  "capture": "profiles/force_descriptor_water200k_ncu.md"}
 
 

@@ -174,7 +174,7 @@ struct nep_model {
     size_t real_size = 4;
     size_t smem_desc = 0, smem_force = 0;
     int mnR = 0, mnA = 0;  // neighbour capacities
-    int mb_desc = 3, mb_force = 2;  // register-cap variants of the FP32 evaluation kernels
+    int mb_desc = 3, mb_force = 3;  // register-cap variants of the FP32 evaluation kernels
     bool autotune = true;           // tune the variants on the first MD call of a configuration shape
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
