@@ -689,8 +689,9 @@ int autotune_plan(nep_model* m, const Plan& p, double* force_d)
     if (rc == NEP_OK) {
         // leave the default (3 blocks) only for a clear win: timed back to back in
         // isolation the variants can rank a few percent differently than inside an
-        // MD step (measured on 100k-bead water: 4 blocks won here, lost in the step)
-        const float margin = 0.97f;
+        // MD step (measured on 100k-bead water: 4 blocks won here by up to 3-4% and
+        // lost 1-2% in the step; where 4 blocks win in the step they win by 7-12%)
+        const float margin = 0.95f;
         m->mb_desc = best_d[2] < margin * best_d[3] ? 2 : 3;
         int bf = 3;
         for (int v = 2; v <= 4; v += 2)
