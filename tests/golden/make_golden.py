@@ -21,6 +21,9 @@ def cases():
     yield "water64_periodic", inputs.random_model(seed=1), inputs.water_box(64, seed=2)
     m2 = inputs.random_model(n_types=2, hidden=8, rc_radial=6.0, rc_angular=4.0, seed=3)
     yield "cluster24_two_types", m2, inputs.random_cluster(24, seed=4, box_len=9.0, min_dist=1.2, n_types=2)
+    # with the four-body (l = 2) and five-body (l = 1) descriptors
+    m3 = inputs.random_model(n_types=2, hidden=8, rc_radial=6.0, rc_angular=4.5, seed=5, l_max_4b=2, l_max_5b=1)
+    yield "cluster20_many_body", m3, inputs.random_cluster(20, seed=6, box_len=8.0, min_dist=1.3, n_types=2)
 
 
 def main():
