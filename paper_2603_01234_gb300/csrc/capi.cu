@@ -645,6 +645,16 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
     return NEP_OK;
 }
 
+// Timing events of one autotuning pass, destroyed on every exit path.
+struct TuneEvents {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~TuneEvents()
+    {
+        for (cudaEvent_t x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
 // Autotuner: time the register-cap variants of the two evaluation kernels on the
 // plan's configuration (lists already built) and keep the fastest of each.  An
 // event between the two launches times each kernel on its own, so the descriptor
@@ -658,50 +668,45 @@ template <typename real>
 int autotune_plan(nep_model* m, const Plan& p, double* force_d)
 {
     if (m->precision == NEP_FP64) return NEP_OK;  // one FP64 variant only
-    cudaEvent_t e0 = nullptr, em = nullptr, e1 = nullptr;
-    NEP_CUDA(cudaEventCreate(&e0));
-    NEP_CUDA(cudaEventCreate(&em));
-    NEP_CUDA(cudaEventCreate(&e1));
+    TuneEvents ev;
+    for (cudaEvent_t& x : ev.e) NEP_CUDA(cudaEventCreate(&x));
+    cudaEvent_t e0 = ev.e[0], em = ev.e[1], e1 = ev.e[2];
     // (descriptor, force) blocks per SM; every variant of each kernel appears
     const int pairs[3][2] = {{2, 2}, {3, 3}, {3, 4}};
     float best_d[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f}, best_f[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     const int keep_d = m->mb_desc, keep_f = m->mb_force;
+    auto trial = [&](int c, bool timed) -> int {
+        m->mb_desc = pairs[c][0];
+        m->mb_force = pairs[c][1];
+        NEP_CUDA(cudaEventRecord(e0, m->cur));
+        NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>(), em));
+        NEP_CUDA(cudaEventRecord(e1, m->cur));
+        NEP_CUDA(cudaEventSynchronize(e1));
+        if (!timed) return NEP_OK;
+        float td = 0.f, tf = 0.f;
+        NEP_CUDA(cudaEventElapsedTime(&td, e0, em));
+        NEP_CUDA(cudaEventElapsedTime(&tf, em, e1));
+        best_d[pairs[c][0]] = std::min(best_d[pairs[c][0]], td);
+        best_f[pairs[c][1]] = std::min(best_f[pairs[c][1]], tf);
+        return NEP_OK;
+    };
     int rc = NEP_OK;
-    for (int round = -1; round < 4 && rc == NEP_OK; ++round) {  // round -1 warms up
-        for (int c = 0; c < 3 && rc == NEP_OK; ++c) {
-            m->mb_desc = pairs[c][0];
-            m->mb_force = pairs[c][1];
-            cudaEventRecord(e0, m->cur);
-            rc = run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>(), em);
-            cudaEventRecord(e1, m->cur);
-            if (rc != NEP_OK) break;
-            cudaEventSynchronize(e1);
-            if (round < 0) continue;
-            float td = 0.f, tf = 0.f;
-            cudaEventElapsedTime(&td, e0, em);
-            cudaEventElapsedTime(&tf, em, e1);
-            best_d[pairs[c][0]] = std::min(best_d[pairs[c][0]], td);
-            best_f[pairs[c][1]] = std::min(best_f[pairs[c][1]], tf);
-        }
-    }
+    for (int round = -1; round < 4 && rc == NEP_OK; ++round)  // round -1 warms up
+        for (int c = 0; c < 3 && rc == NEP_OK; ++c) rc = trial(c, round >= 0);
     m->mb_desc = keep_d;
     m->mb_force = keep_f;
-    if (rc == NEP_OK) {
-        // leave the default (3 blocks) only for a clear win: timed back to back in
-        // isolation the variants can rank a few percent differently than inside an
-        // MD step (measured on 100k-bead water: 4 blocks won here by up to 3-4% and
-        // lost 1-2% in the step; where 4 blocks win in the step they win by 7-12%)
-        const float margin = 0.95f;
-        m->mb_desc = best_d[2] < margin * best_d[3] ? 2 : 3;
-        int bf = 3;
-        for (int v = 2; v <= 4; v += 2)
-            if (best_f[v] < margin * best_f[3] && best_f[v] < best_f[bf]) bf = v;
-        m->mb_force = bf;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(em);
-    cudaEventDestroy(e1);
-    return rc;
+    if (rc != NEP_OK) return rc;
+    // leave the default (3 blocks) only for a clear win: timed back to back in
+    // isolation the variants can rank a few percent differently than inside an
+    // MD step (measured on 100k-bead water: 4 blocks won here by up to 3-4% and
+    // lost 1-2% in the step; where 4 blocks win in the step they win by 7-12%)
+    const float margin = 0.95f;
+    m->mb_desc = best_d[2] < margin * best_d[3] ? 2 : 3;
+    int bf = 3;
+    for (int v = 2; v <= 4; v += 2)
+        if (best_f[v] < margin * best_f[3] && best_f[v] < best_f[bf]) bf = v;
+    m->mb_force = bf;
+    return NEP_OK;
 }
 
 // Stochastic-velocity-rescaling thermostat of an MD call (inactive when noise is null).
