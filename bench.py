@@ -91,6 +91,8 @@ def config_dict(system, name=None):
             "integrator": "velocity-Verlet NVE (FP64)",
             "precision": "FP32 descriptors/network/forces, FP64 reductions+integration",
             "l2": "flushed between timed steps (256 MiB write)",
+            "state": "every timed step starts from the same configuration (positions, velocities and forces "
+                     "restored before the step, outside the timed events)",
             "data": "synthetic (seeded lattice, Maxwell-Boltzmann 300 K)"}
 
 
@@ -135,6 +137,39 @@ def algorithmic_flops(m, pairs_r, pairs_a, n):
 
 
 # ---- clocks sampler ------------------------------------------------------------
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def summarize_clocks(samples, t0=None, t1=None):
+    """Clock samples [(host time, nvidia-smi CSV line)] to the bench's clocks record.
+    The statistics use the samples taken in [t0, t1] (the timed region); when none
+    fell inside it, the nearest sample on each side stands in, and the record says
+    so."""
+    rows = []
+    for t, ln in samples:
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm, smax, pw = float(f[1]), float(f[2]), float(f[3])
+        except ValueError:
+            continue
+        act = [name for k, name in enumerate(CLOCK_REASONS) if f[5 + k].lower().startswith("active")]
+        rows.append((t, sm, smax, pw, act))
+    inside = rows if t0 is None else [r for r in rows if t0 <= r[0] <= t1]
+    window = "timed region"
+    if not inside and rows:
+        before = [r for r in rows if r[0] < t0]
+        after = [r for r in rows if r[0] > t1]
+        inside = before[-1:] + after[:1]
+        window = "nearest samples around the timed region (none fell inside it)"
+    if not inside:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"], "samples": 0}
+    return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+            "reasons": sorted({a for r in inside for a in r[4]}), "samples": len(inside),
+            "power_w_max": max(r[3] for r in inside), "window": window}
+
+
 class Clocks:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -143,12 +178,15 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.samples = []  # (host time, CSV line)
+        self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling every 100 ms (call before the warm-up, so that sampling runs
+        by the time the timed region starts)."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -157,35 +195,22 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.samples.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        """The timed region, in time.perf_counter() seconds."""
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.15)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-                power.append(float(f[3]))
-            except ValueError:
-                continue
-            for k, name in enumerate(names):
-                if f[5 + k].lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(power) if power else None}
+        return summarize_clocks(list(self.samples), self.t0, self.t1)
 
 
 def measured_peaks():
@@ -284,11 +309,20 @@ def run_ours(args):
     sp = stream.cuda_stream
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB
 
-    pos0, vel0_d = pos.clone(), vel.clone()  # every leg starts from this state
+    # Every timed step starts from the same state (positions, velocities and the
+    # forces at those positions), restored before the step outside the timed events
+    # like the L2 flush.  The random-weight potential is not a physical water model:
+    # run on, it drives the configuration away from the water structure (over 1000
+    # steps the pair counts, and the force stage with them, about triple), and the
+    # number would then depend on how many steps are timed.
+    pos0, vel0_d = pos.clone(), vel.clone()
+    force0 = None
 
     def restore():
         pos.copy_(pos0)
         vel.copy_(vel0_d)
+        if force0 is not None:
+            force.copy_(force0)
 
     def step(k=1, fv=1, sample=0, thermo=None):
         binding.nep_md_step(m.h, types, system.masses, system.box, system.pbc, pos, vel, force, fv, k, DT_FS,
@@ -300,26 +334,33 @@ def run_ours(args):
     pairs_r, pairs_a = int(cnt_r.sum()), int(cnt_a.sum())
 
     step(k=0, fv=0)  # initial forces
+    force0 = force.clone()
     # timed steps: each one nep_md_step call of one step, which replays the
-    # handle's captured graph of the step's kernels; L2 flushed before each
+    # handle's captured graph of the step's kernels; state restored and L2 flushed
+    # before each.  The clock sampler starts before the warm-up and keeps the samples
+    # of the timed region.
+    clocks = Clocks(local)
+    clocks.start()
     binding.nep_set_timing(m.h, 0)
     for _ in range(args.warmup):
+        restore()
         flush.zero_()
         step()
     binding.nep_sync(m.h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = Clocks(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    t_start = time.perf_counter()
     for k in range(args.steps):
+        restore()
         flush.zero_()
         ev[k][0].record(stream)
         step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     binding.nep_sync(m.h)
+    clocks.mark(t_start, time.perf_counter())
     if dist:
         dist.barrier()
     clk = clocks.stop()
@@ -328,6 +369,7 @@ def run_ours(args):
     # events between the stages on the launch stream (L2 flushed before each step)
     binding.nep_set_timing(m.h, 1)
     for k in range(args.steps):
+        restore()
         flush.zero_()
         step()
     binding.nep_sync(m.h)
@@ -336,15 +378,14 @@ def run_ours(args):
     value, ms = replica_throughput(ms, n * args.steps, dist, dev)
     ms_step = ms / args.steps
 
-    # steady state: the same steps back to back through the graph-captured loop
+    # steady state: 100 steps back to back through the graph-captured loop, from the
+    # same state (a fixed count: a longer run drifts away from the water structure)
     steady = None
     if not args.quick:
-        k2 = max(args.steps, 20)
+        k2 = 100
         restore()
-        step(k=0, fv=0)
         step(k=k2)  # captures the chunk graph
         restore()
-        step(k=0, fv=0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -360,14 +401,14 @@ def run_ours(args):
     if not args.quick:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         restore()
-        step(k=0, fv=0)
         torch.cuda.synchronize()
         h_types, h_pos = pin(system.types), pin(pos.cpu().numpy())
         h_vel, h_force = pin(vel.cpu().numpy()), pin(force.cpu().numpy())
         thermo = pin(np.zeros((1, 12)))
         binding.nep_md_step(m.h, h_types, system.masses, system.box, system.pbc, h_pos, h_vel, h_force, 1, 1, DT_FS,
                             1, thermo)
-        ke = max(3, args.steps // 2)
+        h_pos[:], h_vel[:], h_force[:] = pos0.cpu().numpy(), vel0_d.cpu().numpy(), force0.cpu().numpy()
+        ke = 100  # from the same state, a fixed count (host buffers cannot be restored untimed)
         t0 = time.perf_counter()
         for _ in range(ke):
             binding.nep_md_step(m.h, h_types, system.masses, system.box, system.pbc, h_pos, h_vel, h_force, 1, 1,
@@ -416,13 +457,21 @@ def run_ours(args):
             binding.nep_md_step(mv.h, types, system.masses, system.box, system.pbc, pv, vv, fv_, fv, k, DT_FS,
                                 0, None, stream=sp)
         step_v(k=0, fv=0)
+        fv0 = fv_.clone()
+
+        def restore_v():  # every step from the same state, as in the headline loop
+            pv.copy_(pos0)
+            vv.copy_(vel0_d)
+            fv_.copy_(fv0)
         for _ in range(args.warmup):
+            restore_v()
             flush.zero_()
             step_v()
         kv = args.steps
         evv = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kv)]
         torch.cuda.synchronize()
         for k in range(kv):
+            restore_v()
             flush.zero_()
             evv[k][0].record(stream)
             step_v()
@@ -432,6 +481,7 @@ def run_ours(args):
         msv = sum(x.elapsed_time(y) for x, y in evv)
         binding.nep_set_timing(mv.h, 1)
         for k in range(kv):
+            restore_v()
             flush.zero_()
             step_v()
         binding.nep_sync(mv.h)
@@ -613,7 +663,7 @@ def run_drift(args, n_steps=1000, every=10):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the steady-state, e2e and FP64 legs")
