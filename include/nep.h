@@ -345,10 +345,11 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
 /*
  * Autotuner.  The FP32 descriptor and force kernels are compiled in variants
  * that keep 2 or 3 (force: 2, 3 or 4) thread blocks resident per SM (a register
- * budget per thread).  nep_autotune evaluates the configuration with every variant pair,
- * times them with CUDA events and keeps the fastest on the handle; the first
- * nep_md_step of a new configuration shape (n and cell grid) does the same
- * unless disabled.  All variants give identical results.  Inputs as in
+ * budget per thread).  nep_autotune evaluates the configuration several times with
+ * each variant, times the two kernels separately with CUDA events, and keeps for
+ * each kernel the 3-block default unless another variant is at least 5% faster;
+ * the first nep_md_step of a new configuration shape (n and cell grid) does the
+ * same unless disabled.  All variants give identical results.  Inputs as in
  * nep_compute; the chosen variants are returned (may be NULL).
  */
 int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
@@ -364,7 +365,8 @@ int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force);
 /* Current neighbour-list capacities (entries per particle). */
 int nep_get_capacity(nep_model* m, int* radial, int* angular);
 
-/* Set the neighbour-list capacities (entries per particle, >= 1). */
+/* Set the neighbour-list capacities (entries per particle, >= 1).  A list holds
+ * capacity x n entries, at most 2^32 (larger lists give NEP_ERR_ARG when built). */
 int nep_set_capacity(nep_model* m, int radial, int angular);
 
 #ifdef __cplusplus
