@@ -196,10 +196,11 @@ int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const i
  * returns when the steps are done.
  * Neighbour-list capacity is probed synchronously once per configuration shape
  * (n and cell grid) and set to 1.5 times the largest count plus 8; it is raised
- * the same way when a chunk of steps sees counts above 80% of it.  That check runs
- * between chunks and lags one chunk behind the GPU, so the counts must not grow by
- * more than about a quarter over two chunks: a structure that changes fast needs
- * short chunks (a small sample_every).  NEP_ERR_NEIGHBOR_OVERFLOW means a list
+ * the same way when the counts, projected two chunks ahead at the last chunk's
+ * growth, pass 80% of it.  That check runs between chunks and lags one chunk behind
+ * the GPU, so a sudden jump in the counts (beyond the projection and the 1.5x
+ * headroom within two chunks) can still overflow; short chunks (a small
+ * sample_every) shrink that window.  NEP_ERR_NEIGHBOR_OVERFLOW means a list
  * outgrew its capacity: the state of that call is undefined and the capacity is
  * raised for the next, so the caller retries from its saved state.
  */

@@ -972,6 +972,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         NEP_TRY(capture());
         const bool check = n_steps >= 2 * chunk;
         bool pending = false;
+        int prevR = -1, prevA = -1;  // the counts' running maxima one chunk earlier
         for (; done + chunk <= n_steps; done += chunk) {
             NEP_CUDA(cudaGraphLaunch(m->graph.exec, m->cur));
             if (!check) continue;
@@ -991,12 +992,19 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
                     m->graph.reset();
                     return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "a neighbour list outgrew its capacity during MD");
                 }
-                if (needR * 5 > m->mnR * 4 || needA * 5 > m->mnA * 4) {
+                // the counts two chunks ahead (the chunk in flight and the next) at the
+                // last chunk's growth, so that a structure whose neighbour counts grow
+                // steadily gets room before it overflows
+                const int projR = needR + (prevR >= 0 ? 2 * std::max(0, needR - prevR) : 0);
+                const int projA = needA + (prevA >= 0 ? 2 * std::max(0, needA - prevA) : 0);
+                prevR = needR;
+                prevA = needA;
+                if (projR * 5 > m->mnR * 4 || projA * 5 > m->mnA * 4) {
                     // grow before the lists overflow: finish the chunk in flight, then
                     // resize and capture again
                     NEP_CUDA(cudaStreamSynchronize(m->cur));
-                    m->mnR = std::max(m->mnR, ((int)(needR * 1.5) + 8 + 7) & ~7);
-                    m->mnA = std::max(m->mnA, ((int)(needA * 1.5) + 8 + 7) & ~7);
+                    m->mnR = std::max(m->mnR, ((int)(projR * 1.5) + 8 + 7) & ~7);
+                    m->mnA = std::max(m->mnA, ((int)(projA * 1.5) + 8 + 7) & ~7);
                     NEP_TRY(ensure_lists(m, n));
                     NEP_TRY(capture());
                 }
