@@ -39,12 +39,13 @@ from paper_2603_01234_gb300 import inputs  # noqa: E402
 METRIC = "bead-steps/s (100k-bead CG water MD step)"
 UNIT = "bead-steps/s"
 DT_FS = 10.0
-FLOPS_PEAK_NOTE = "FP32 ALU peak = 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock"
+FLOPS_PEAK_NOTE = "FP32 ALU peak = SMs (device-reported) x 128 FP32 lanes x 2 flop/FMA x clock"
 
-# DRAM bytes per particle of one force-kernel launch, from the ncu capture summarised in
-# profiles/force_descriptor_water200k_ncu.md; valid only for the source it was taken on.
-FORCE_TRAFFIC = {"evaluate_cu_sha1": "944e492b16cd527936ea261fd5fe3887b88d9b02", "bytes_per_particle": 962.7,
-                 "capture": "profiles/force_descriptor_water200k_ncu.md"}
+# DRAM bytes per particle of one launch of the dominant kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the evaluate.cu
+# source it was taken on, otherwise the bench reports traffic as null.
+KERNEL_TRAFFIC = {"evaluate_cu_sha1": None, "bytes_per_particle": None,
+                  "capture": "ncu, 200,000-bead water, cold caches"}
 
 
 N_BEADS = 100_000
@@ -296,6 +297,7 @@ def run_ours(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     binding.load(build_if_missing=True)
 
     model, system, vel0 = workload()
@@ -518,18 +520,20 @@ def run_ours(args):
     dom_ms = stages[dom] / max(1, tsteps)
     achieved = work[dom] / (dom_ms / 1000.0) / 1e12
     sm_max = (clk.get("sm_max_mhz") or (peaks or {}).get("sm_max_mhz") or 2070.0)
-    peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    sms = n_sms
+    peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
     traffic = None
-    if dom == "force_virial":
-        import hashlib
-        src = os.path.join(ROOT, "paper_2603_01234_gb300", "csrc", "evaluate.cu")
-        if hashlib.sha1(open(src, "rb").read()).hexdigest() == FORCE_TRAFFIC["evaluate_cu_sha1"]:
-            traffic = FORCE_TRAFFIC["bytes_per_particle"] * n
+    import hashlib
+    src = os.path.join(ROOT, "paper_2603_01234_gb300", "csrc", "evaluate.cu")
+    if KERNEL_TRAFFIC["bytes_per_particle"] and \
+            hashlib.sha1(open(src, "rb").read()).hexdigest() == KERNEL_TRAFFIC["evaluate_cu_sha1"]:
+        traffic = KERNEL_TRAFFIC["bytes_per_particle"] * n
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": traffic, "traffic_source": FORCE_TRAFFIC["capture"], "kernel": dom, "flop_per_launch": work[dom], "ms_per_launch": dom_ms,
-            "peak_note": FLOPS_PEAK_NOTE + f" ({sm_max:.0f} MHz max clock)"}
+            "traffic": traffic, "traffic_source": KERNEL_TRAFFIC["capture"], "kernel": dom,
+            "flop_per_launch": work[dom], "ms_per_launch": dom_ms, "sms": sms,
+            "peak_note": FLOPS_PEAK_NOTE + f" ({sms} SMs, {sm_max:.0f} MHz max clock)"}
     if clk.get("sm_mhz"):
-        roof["frac_at_median_clock"] = achieved / (152 * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
+        roof["frac_at_median_clock"] = achieved / (sms * 128 * 2 * clk["sm_mhz"] * 1e6 / 1e12)
     # every kernel of the evaluation against its own bound, from the stage pass
     kernels = {}
     for k in ("descriptor_network", "force_virial"):

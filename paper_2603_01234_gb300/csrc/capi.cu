@@ -302,7 +302,7 @@ void set_models(Plan& p, nep_model* const* models, int n_models)
     }
 }
 
-size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Upload the plan's tables (through pinned staging) unless they are unchanged.
 int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
@@ -1305,6 +1305,8 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.rcA2 = p; p += TT;
     o.rcRi = p; p += TT;
     o.rcAi = p; p += TT;
+    o.rcRl = p; p += TT;
+    o.rcAl = p; p += TT;
     const int cRs = coef_stride(m->nR, m->KR), cAs = coef_stride(m->nA, m->KA);
     o.cR = p; p += TT * cRs;
     o.cA = p; p += TT * cAs;
@@ -1317,6 +1319,19 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.b0 = p; p += T * hidden;
     o.w1 = p; p += T * hidden;
     o.b1 = p; p += T;
+    // FP32 form: each network parameter and radial coefficient also as its rounding
+    // residual, so that the kernels evaluate the caller's FP64 model to ~1e-14 rather
+    // than a model rounded to FP32 (the rounding is the same for every particle and
+    // would otherwise add a consistent offset to every site energy)
+    o.w0l = o.b0l = o.w1l = o.b1l = o.cRl = -1;
+    if (precision != NEP_FP64) {
+        if (T == 1) p = (p + 3) & ~3;
+        o.w0l = p; p += T * hidden * w0s;
+        o.b0l = p; p += T * hidden;
+        o.w1l = p; p += T * hidden;
+        o.b1l = p; p += T;
+        o.cRl = p; p += TT * cRs;
+    }
     o.w0f = o.w0b = -1;
     const int nd = m->ND, hp = net_hp(hidden);
     if (precision == NEP_FP32_BF16) {  // BF16 copies of W0 laid out as MMA B operands
@@ -1331,6 +1346,11 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
         h[o.rcA2 + k] = m->rcA[k] * m->rcA[k];
         h[o.rcRi + k] = 1.0 / m->rcR[k];
         h[o.rcAi + k] = 1.0 / m->rcA[k];
+        // the FP32 kernels form r / r_c as r (hi + lo): FP32 1/r_c alone is off by up
+        // to 6e-8 relative, the same for every pair of a type pair, which would shift
+        // every cutoff value one way
+        h[o.rcRl + k] = precision == NEP_FP64 ? 0.0 : 1.0 / m->rcR[k] - (double)(float)(1.0 / m->rcR[k]);
+        h[o.rcAl + k] = precision == NEP_FP64 ? 0.0 : 1.0 / m->rcA[k] - (double)(float)(1.0 / m->rcA[k]);
     }
     for (int k = 0; k < TT; ++k) {  // pair tables at odd strides
         std::copy(c_radial + (size_t)k * m->nR * m->KR, c_radial + (size_t)(k + 1) * m->nR * m->KR,
@@ -1354,6 +1374,16 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     std::copy(b0, b0 + T * hidden, h.begin() + o.b0);
     std::copy(w1, w1 + T * hidden, h.begin() + o.w1);
     std::copy(b1, b1 + T, h.begin() + o.b1);
+    if (o.w0l >= 0) {  // rounding residuals of the FP32 tables
+        auto residual = [&](int hi, int lo, int count) {
+            for (int k = 0; k < count; ++k) h[lo + k] = h[hi + k] - (double)(float)h[hi + k];
+        };
+        residual(o.w0, o.w0l, T * hidden * w0s);
+        residual(o.b0, o.b0l, T * hidden);
+        residual(o.w1, o.w1l, T * hidden);
+        residual(o.b1, o.b1l, T);
+        residual(o.cR, o.cRl, TT * cRs);
+    }
 
     auto cleanup = [&](int code) {
         nep_destroy(m);
@@ -1751,6 +1781,10 @@ constexpr int kStaticMaxKRP = 12;        // padded K_R
 constexpr int kStaticMaxItems = (kStaticMaxN + kBlock - 1) / kBlock;
 constexpr size_t kStaticTableBytes = 2048;  // one request, its work items, one model
 constexpr int kStaticMaxDevices = 64;
+// the request, its work items and one model table must fit the table region
+static_assert(align16(sizeof(ReqInfo)) + align16(sizeof(WorkItem) * kStaticMaxItems) +
+                      sizeof(ModelDesc<double>) <= kStaticTableBytes,
+              "static table region too small for the request, its work items and the model table");
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 

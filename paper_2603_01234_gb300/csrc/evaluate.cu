@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include "nep_common.cuh"
+#include "poly32.cuh"
 #include "sh_poly.cuh"
 
 namespace nep {
@@ -39,25 +40,46 @@ constexpr int kNLM = 24;
 // The FP32 kernels are compiled for 2 and for 3 resident blocks per SM (which caps
 // registers per thread); the runtime picks one per handle (autotuned).
 
-// sin(pi x), cos(pi x) for x = r / r_c in [0, 1].  FP32 uses the hardware
-// approximations (absolute error below 4e-7 on [0, pi]); FP64 the accurate routine.
-__device__ __forceinline__ void sincospi_r(float x, float* s, float* c)
+// The cutoff of Eq. 8 halved, f_c / 2, and its derivative halved, f_c' / 2, at
+// x = r / r_c in [0, 1].  FP32 evaluates the polynomials of poly32.cuh
+// (the hardware sine and cosine err by about 1e-7 with a consistent sign, which
+// summed over pairs biases the energy); FP64 uses the accurate sincospi.
+__device__ __forceinline__ float cut_half(float x)
 {
-    const float t = 3.14159265358979f * x;
-    *s = __sinf(t);
-    *c = __cosf(t);
+    const float y = x - 0.5f;
+    return fmaf(-y, cut_p(y * y), 0.25f);
 }
-__device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ double cut_half(double x)
+{
+    return 0.25 + 0.25 * cospi(x);
+}
+__device__ __forceinline__ void cut_half_d(float x, float inv_rc, float* hf, float* hdf)
+{
+    const float y = x - 0.5f;
+    const float z = y * y;
+    *hf = fmaf(-y, cut_p(z), 0.25f);
+    *hdf = -cut_q(z) * inv_rc;
+}
+__device__ __forceinline__ void cut_half_d(double x, double inv_rc, double* hf, double* hdf)
+{
+    double s, c;
+    sincospi(x, &s, &c);
+    *hf = 0.25 + 0.25 * c;
+    *hdf = (-0.25 * 3.14159265358979323846) * inv_rc * s;
+}
 
 // Chebyshev basis f_k(r) of Eq. 7 with the cutoff of Eq. 8, k = 0..K-1, by the
 // three-term recurrence T_{k+1} = 2 x T_k - T_{k-1}.
+// x = r / r_c from the inverse cutoff and its FP32 rounding residual (FP64: exact enough)
+__device__ __forceinline__ float scaled_r(float r, float inv_rc, float inv_lo) { return fmaf(r, inv_lo, r * inv_rc); }
+__device__ __forceinline__ double scaled_r(double r, double inv_rc, double) { return r * inv_rc; }
+
 template <typename real, int K>
-__device__ __forceinline__ void basis(real r, real inv_rc, real* f)
+__device__ __forceinline__ void basis(real r, real inv_rc, real inv_lo, real* f)
 {
-    real sn, cs;
-    sincospi_r(r * inv_rc, &sn, &cs);
-    const real hf = real(0.25) + real(0.25) * cs;  // f_c / 2
-    const real s = r * inv_rc - real(1);
+    const real xr = scaled_r(r, inv_rc, inv_lo);
+    const real hf = cut_half(xr);  // f_c / 2
+    const real s = xr - real(1);
     const real x = real(2) * s * s - real(1);
     const real x2 = x + x;
     real t0 = real(1), t1 = x;
@@ -75,13 +97,12 @@ __device__ __forceinline__ void basis(real r, real inv_rc, real* f)
 // f_k and df_k/dr:  df_k = 1/2 [T_k'(x) x'(r) f_c + (T_k + 1) f_c'],
 // with T'_{k+1} = 2 T_k + 2 x T'_k - T'_{k-1}.
 template <typename real, int K>
-__device__ __forceinline__ void basis_d(real r, real inv_rc, real* f, real* df)
+__device__ __forceinline__ void basis_d(real r, real inv_rc, real inv_lo, real* f, real* df)
 {
-    real sn, cs;
-    sincospi_r(r * inv_rc, &sn, &cs);
-    const real hf = real(0.25) + real(0.25) * cs;                           // f_c / 2
-    const real hdf = real(-0.25 * 3.14159265358979323846) * inv_rc * sn;    // f_c' / 2
-    const real s = r * inv_rc - real(1);
+    const real xr = scaled_r(r, inv_rc, inv_lo);
+    real hf, hdf;  // f_c / 2, f_c' / 2
+    cut_half_d(xr, inv_rc, &hf, &hdf);
+    const real s = xr - real(1);
     const real x = real(2) * s * s - real(1);
     const real hdx = real(4) * s * inv_rc * hf;                             // x'(r) f_c / 2
     const real x2 = x + x;
@@ -170,6 +191,32 @@ __device__ __forceinline__ void walk4(const uint32_t* nl, size_t stride, int cnt
     if (s + 2 < cnt) body(q2);
 }
 
+// walk4 with the entry's position in its group of four passed as the second
+// argument (0..3, a constant after unrolling), so that a body can keep four
+// partial sums: each then grows to a quarter of the total, which cuts the FP32
+// rounding of a long accumulation about four-fold at no extra instructions.
+template <typename Body>
+__device__ __forceinline__ void walk4p(const uint32_t* nl, size_t stride, int cnt, Body&& body)
+{
+    auto ld = [&](int s) { return s < cnt ? nl[(size_t)s * stride] : 0u; };
+    uint32_t q0 = ld(0), q1 = ld(1), q2 = ld(2), q3 = ld(3);
+    int s = 0;
+    for (; s + 4 <= cnt; s += 4) {
+        const uint32_t a0 = q0, a1 = q1, a2 = q2, a3 = q3;
+        q0 = ld(s + 4);
+        q1 = ld(s + 5);
+        q2 = ld(s + 6);
+        q3 = ld(s + 7);
+        body(a0, 0);
+        body(a1, 1);
+        body(a2, 2);
+        body(a3, 3);
+    }
+    if (s < cnt) body(q0, 0);
+    if (s + 1 < cnt) body(q1, 1);
+    if (s + 2 < cnt) body(q2, 2);
+}
+
 // 4 consecutive reals (16-byte aligned) into registers
 __device__ __forceinline__ void load4(const float* p, float* o)
 {
@@ -191,8 +238,40 @@ __device__ __forceinline__ void loadN(const real* p, real* o)
     for (int k = N & ~3; k < N; ++k) o[k] = p[k];
 }
 
-__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+// 1/sqrt(x): the hardware estimate refined by one Newton-Raphson step on
+// f(y) = y^-2 - x, y' = y + y (1 - x y^2) / 2.  The estimate's error has a small
+// consistent sign, which through |u| = |r| / r and the homogeneous harmonics would
+// bias the angular descriptors; after the step the quadratic term is ~1e-14 and
+// what remains is the (unsigned) rounding of y^2.
+__device__ __forceinline__ float rsqrt_r(float x)
+{
+    const float y = rsqrtf(x);
+    const float e = fmaf(-x, y * y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+}
 __device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
+// tanh in FP32.  Each hidden unit's pre-activation keeps one sign over most
+// particles, so an activation whose rounding error leans one way on part of its
+// range biases every particle's energy alike; CUDA's tanhf does (about -9e-9 on
+// [1/4, 1/2]).  Here: on |x| < 1 the odd polynomial of poly32.cuh (mean error below
+// 2e-10 on every eighth of the range); beyond, (1 - e) / (1 + e) with
+// e = exp(-2|x|), where no cancellation remains, divided through a reciprocal
+// refined by one Newton-Raphson step.
+__device__ __forceinline__ float tanh_r(float x)
+{
+    const float a = fabsf(x);
+    if (a < 1.0f) {
+        const float z = x * x;
+        return fmaf(x * z, tanh_r_poly(z), x);
+    }
+    const float e = expf(-2.0f * a);
+    const float d = 1.0f + e;
+    float r = __fdividef(1.0f, d);
+    r = fmaf(r, fmaf(-d, r, 1.0f), r);
+    return copysignf((1.0f - e) * r, x);
+}
+__device__ __forceinline__ double tanh_r(double x) { return tanh(x); }
 
 template <typename real>
 __device__ __forceinline__ void stage_params(const real* __restrict__ src, real* dst, int count)
@@ -279,6 +358,8 @@ __device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off,
     const uint16_t* W0b = reinterpret_cast<const uint16_t*>(P + off.w0b);
     const float* b0 = P + off.b0;
     const float* w1 = P + off.w1;
+    const float* b0l = P + off.b0l;  // FP32 rounding residuals of b0, w1 (b1 below)
+    const float* w1l = P + off.w1l;
     float up[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
     float dacc[2][NB][4];
 #pragma unroll
@@ -334,9 +415,9 @@ __device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off,
                     const int t = rt[mt][e >> 1];
                     float coef = 0.f;
                     if (col < H) {
-                        const float h = tanhf(x[mt][nl][e] - b0[t * H + col]);
+                        const float h = tanh_r(x[mt][nl][e] - b0[t * H + col] - b0l[t * H + col]);
                         const float w = w1[t * H + col];
-                        up[mt][e >> 1] += w * h;
+                        up[mt][e >> 1] += w * h + w1l[t * H + col] * h;
                         coef = w * (1.f - h * h);
                     }
                     d[nl][e] = coef;
@@ -387,7 +468,7 @@ __device__ __forceinline__ void net_bf16(const float* P, const ParamLayout& off,
         const float v = __shfl_sync(FULL, rs[k], 4 * (lane & 7));
         if ((lane >> 3) == k) mine = v;
     }
-    U = mine - P[off.b1 + ti];
+    U = mine - P[off.b1 + ti] - P[off.b1l + ti];
     // dQ back to one row per lane
     float* Dw = reinterpret_cast<float*>(scratch);  // [32][NDP + 1]
 #pragma unroll
@@ -476,32 +557,50 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     // ---- radial descriptors (Eq. 3, 6-8) ----
     const int cR = min(a.cntR[i], a.mnR);
     if (T == 1) {
-        // one pair type: q_n = sum_k c_nk (sum_j f_k(r_ij)), contracted once per bead
-        real fs[KR];
+        // one pair type: q_n = sum_k c_nk (sum_j f_k(r_ij)), contracted once per bead;
+        // the pair sums are kept as four partial sums (see walk4p)
+        real fp[4][KR];
 #pragma unroll
-        for (int k = 0; k < KR; ++k) fs[k] = real(0);
-        const real inv_rc = P[off.rcRi];
-        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int k = 0; k < KR; ++k) fp[p][k] = real(0);
+        const real inv_rc = P[off.rcRi], inv_lo = P[off.rcRl];
+        walk4p(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e, int p) {
             const PosRec<real> rj = a.rec[e & kJMask];
             real dx, dy, dz;
             pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real r = r2 * rsqrt_r(r2);
             real f[KR];
-            basis<real, KR>(r, inv_rc, f);
+            basis<real, KR>(r, inv_rc, inv_lo, f);
 #pragma unroll
-            for (int k = 0; k < KR; ++k) fs[k] += f[k];
+            for (int k = 0; k < KR; ++k) fp[p][k] += f[k];
         });
+        real fs[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) fs[k] = (fp[0][k] + fp[1][k]) + (fp[2][k] + fp[3][k]);
         const real* c = P + off.cR;
 #pragma unroll
         for (int nn = 0; nn < NR; ++nn) {
             real g = real(0);
 #pragma unroll
             for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * fs[k];
+            if constexpr (sizeof(real) == 4) {  // plus the coefficients' FP32 rounding residuals
+                const real* cl = P + off.cRl;
+                real gl = real(0);
+#pragma unroll
+                for (int k = 0; k < KR; ++k) gl += cl[nn * KR + k] * fs[k];
+                g += gl;
+            }
             q[nn] = g;
         }
     } else {
-        walk4(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e) {
+        real qp[4][NR];  // four partial sums (see walk4p)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int nn = 0; nn < NR; ++nn) qp[p][nn] = real(0);
+        walk4p(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e, int p) {
             const PosRec<real> rj = a.rec[e & kJMask];
             real dx, dy, dz;
             pair_vec(len, ri, rj, e, dx, dy, dz);
@@ -509,16 +608,18 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             const real r = r2 * rsqrt_r(r2);
             const int tp = ti * T + rj.t;
             real f[KR];
-            basis<real, KR>(r, P[off.rcRi + tp], f);
+            basis<real, KR>(r, P[off.rcRi + tp], P[off.rcRl + tp], f);
             const real* c = P + off.cR + tp * coef_stride(NR, KR);
 #pragma unroll
             for (int nn = 0; nn < NR; ++nn) {
                 real g = real(0);
 #pragma unroll
                 for (int k = 0; k < KR; ++k) g += c[nn * KR + k] * f[k];
-                q[nn] += g;
+                qp[p][nn] += g;
             }
         });
+#pragma unroll
+        for (int nn = 0; nn < NR; ++nn) q[nn] = (qp[0][nn] + qp[1][nn]) + (qp[2][nn] + qp[3][nn]);
     }
 
     // ---- angular moments A_nlm (Eq. 5) ----
@@ -540,7 +641,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         const real r = r2 * inv_r;
         const int tp = ti * T + rj.t;
         real f[KA];
-        basis<real, KA>(r, P[off.rcAi + tp], f);
+        basis<real, KA>(r, P[off.rcAi + tp], P[off.rcAl + tp], f);
         const real* c = P + off.cA + tp * coef_stride(NA, KA);
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
@@ -577,9 +678,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
         net_bf16<ND>(P, off, T, H, ti, q, U, dq, scratch);
         if (!live) return;
     } else {
+        // The FP32 form adds the parameters' rounding residuals (tables ...l) in
+        // separate accumulators, so the energy is that of the caller's FP64 weights;
+        // the gradient (forces, whose tolerance is far looser) uses the FP32 weights.
+        constexpr bool kRes = sizeof(real) == 4;
         const real* b0 = P + off.b0 + ti * H;
         const real* w1 = P + off.w1 + ti * H;
+        const real* b0l = P + (kRes ? off.b0l : off.b0) + ti * H;
+        const real* w1l = P + (kRes ? off.w1l : off.w1) + ti * H;
         U = -P[off.b1 + ti];
+        real Ul = kRes ? -P[off.b1l + ti] : real(0);
 #pragma unroll
         for (int v = 0; v < ND; ++v) dq[v] = real(0);
         if (T == 1) {
@@ -588,14 +696,22 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             // the same row, a broadcast)
             constexpr int NDV = (ND + 3) & ~3;
             const real* w0 = P + off.w0;
+            const real* w0l = P + (kRes ? off.w0l : off.w0);
             for (int mu = 0; mu < H; ++mu) {
                 real w[NDV];
                 loadN<real, NDV>(w0 + mu * NDV, w);
                 real x = -b0[mu];
 #pragma unroll
                 for (int v = 0; v < ND; ++v) x += w[v] * q[v];
-                const real h = tanh(x);
+                if constexpr (kRes) {  // residual row straight from shared memory (no register copy)
+                    real xl = -b0l[mu];
+#pragma unroll
+                    for (int v = 0; v < ND; ++v) xl += w0l[mu * NDV + v] * q[v];
+                    x += xl;
+                }
+                const real h = tanh_r(x);
                 U += w1[mu] * h;
+                if constexpr (kRes) Ul += w1l[mu] * h;
                 const real coef = w1[mu] * (real(1) - h * h);
 #pragma unroll
                 for (int v = 0; v < ND; ++v) dq[v] += coef * w[v];
@@ -604,17 +720,26 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             // several types: unpadded rows (padded ones put the rows that lanes of
             // different types read at once into the same shared-memory banks)
             const real* w0 = P + off.w0 + ti * H * ND;
+            const real* w0l = P + (kRes ? off.w0l : off.w0) + ti * H * ND;
             for (int mu = 0; mu < H; ++mu) {
                 real x = -b0[mu];
 #pragma unroll
                 for (int v = 0; v < ND; ++v) x += w0[mu * ND + v] * q[v];
-                const real h = tanh(x);
+                if constexpr (kRes) {
+                    real xl = -b0l[mu];
+#pragma unroll
+                    for (int v = 0; v < ND; ++v) xl += w0l[mu * ND + v] * q[v];
+                    x += xl;
+                }
+                const real h = tanh_r(x);
                 U += w1[mu] * h;
+                if constexpr (kRes) Ul += w1l[mu] * h;
                 const real coef = w1[mu] * (real(1) - h * h);
 #pragma unroll
                 for (int v = 0; v < ND; ++v) dq[v] += coef * w0[mu * ND + v];
             }
         }
+        if constexpr (kRes) U += Ul;
     }
     a.U[i] = U;
     // e_i^t[k] = sum_n dU/dq_n c^{t_i t}_{nk}
@@ -750,7 +875,7 @@ __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real
         const real inv_r = rsqrt_r(r2);
         const real r = r2 * inv_r;
         real f[KR], df[KR];
-        basis_d<real, KR>(r, P[off.rcRi + ti * T + rj.t], f, df);
+        basis_d<real, KR>(r, P[off.rcRi + ti * T + rj.t], P[off.rcRl + ti * T + rj.t], f, df);
         real ai = real(0), bj = real(0);
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
@@ -810,7 +935,7 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
         const real r = r2 * inv_r;
         const int tij = ti * T + rj.t, tji = rj.t * T + ti;
         real f[KA], df[KA];
-        basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
+        basis_d<real, KA>(r, P[off.rcAi + tij], P[off.rcAl + tij], f, df);
         real gi[NA], dgi[NA], gj[NA], dgj[NA];
         {
             const real* cc = P + off.cA + tij * coef_stride(NA, KA);
@@ -995,7 +1120,7 @@ __device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, c
         const real r = r2 * inv_r;
         const int tij = ti * T + rj.t;
         real f[KA], df[KA];
-        basis_d<real, KA>(r, P[off.rcAi + tij], f, df);
+        basis_d<real, KA>(r, P[off.rcAi + tij], P[off.rcAl + tij], f, df);
         real g[NA], dg[NA];
         const real* cc = P + off.cA + tij * coef_stride(NA, KA);
 #pragma unroll

@@ -112,8 +112,13 @@ __host__ __device__ inline double wrap_periodic(double x, double L)
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
+    int rcRl, rcAl;             // [T][T] each: rounding residuals of the inverse cutoffs
+                                // (1/r_c - rcRi in FP32; zero in FP64)
     int cR, cA;                 // [T][T] tables of [nR][KR] and [nA][KA], coef_stride apart
     int w0, b0, w1, b1;         // [T][H][ND], [T][H], [T][H], [T]
+    int w0l, b0l, w1l, b1l;     // FP32 form: the rounding residuals x - (float)x of w0, b0, w1, b1
+                                // (same layouts; -1 in the FP64 form)
+    int cRl;                    // FP32 form: residuals of the cR tables (-1 in the FP64 form)
     int w0f, w0b;               // BF16-weight network form: W0 as BF16 MMA operands (-1 when absent),
                                 // [T][net_hp(H)][net_sf(ND)] and [T][net_ndp(ND)][net_hp(H) + 8]
     int n_cut_coef;             // elements of the cutoff + coefficient prefix
