@@ -190,7 +190,8 @@ struct nep_model {
     Buf cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
-    Buf acc;  // FP32 force scatter accumulators [n][16] (64-bit fixed point)
+    Buf acc;  // FP32 form: force and virial fixed-point lines, thread virial sums (acc_bytes)
+    bool eval_per_bead = false;  // the evaluation in progress returns per-particle virials
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
     Buf noise_d, bussi;  // thermostat: random numbers of the call; [step, alpha] words
     Buf md_virial, md_site, heat, heat_rows;  // HNEMD: per-particle W_i and U_i; acc[6] + counter; rows
@@ -361,6 +362,13 @@ int single_plan(nep_model* m, int n, const CellGrid& g)
 }
 
 // ---- workspace ---------------------------------------------------------------
+// The FP32 form's accumulators for n particles in one buffer: force lines, virial
+// lines, thread virial sums.
+size_t acc_bytes(size_t n) { return 32 * n + 96 * n + 36 * n; }
+unsigned long long* acc_force(void* base) { return (unsigned long long*)base; }
+unsigned long long* acc_virial(void* base, size_t n) { return (unsigned long long*)((char*)base + 32 * n); }
+float* acc_wsum(void* base, size_t n) { return (float*)((char*)base + 128 * n); }
+
 int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
 {
     const size_t rs = m->real_size;
@@ -375,9 +383,10 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->cntA.ensure(sizeof(int) * n));
     NEP_TRY(m->U.ensure(rs * n));
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
-    NEP_TRY(m->phi.ensure(rs * 24 * phi_pad(m->nA) * (size_t)n));
+    if (m->precision == NEP_FP64) NEP_TRY(m->phi.ensure(rs * 24 * phi_pad(m->nA) * (size_t)n));  // FP32 keeps Phi in registers
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
-    if (m->precision != NEP_FP64) NEP_TRY(m->acc.ensure(sizeof(unsigned long long) * 16 * (size_t)n));
+    // FP32 form: force lines [n][4] u64, virial lines [n][12] u64, thread virial sums [9][n] float
+    if (m->precision != NEP_FP64) NEP_TRY(m->acc.ensure(acc_bytes(n)));
     NEP_TRY(m->partial2.ensure(sizeof(double) * 6 * ((n + kBlock - 1) / kBlock)));
     NEP_TRY(m->force_tmp.ensure(sizeof(double) * 3 * (size_t)n));
     const size_t old_req = m->counters.cap / sizeof(unsigned int);
@@ -463,6 +472,10 @@ int run_neighbors(nep_model* m, const Plan& p)
     a.cntR = m->cntR.as<int>();
     a.cntA = m->cntA.as<int>();
     a.maxcnt = m->flags.as<int>();
+    // the FP32 form's fixed-point lines are zeroed by the neighbour kernel (virial
+    // lines only when this evaluation returns per-particle virials)
+    a.accF = m->precision != NEP_FP64 ? acc_force(m->acc.p) : nullptr;
+    a.accW = m->precision != NEP_FP64 && m->eval_per_bead ? acc_virial(m->acc.p, p.n) : nullptr;
     if ((uint64_t)std::max(a.mnR, a.mnA) * (uint64_t)a.n > (1ull << 32))
         return fail(NEP_ERR_ARG, "neighbour lists beyond 2^32 entries (capacity x particles)");
     cudaError_t e = launch_neighbors<real>(a, (int)p.items.size(), p.smem_nbr, m->cur);
@@ -496,7 +509,9 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.force = force;
     a.virial = virial;
     a.site = site;
-    a.acc = m->acc.as<unsigned long long>();
+    a.accF = acc_force(m->acc.p);
+    a.accW = acc_virial(m->acc.p, p.n);
+    a.wsum = acc_wsum(m->acc.p, p.n);
     a.partial = m->partial.as<double>();
     a.counter = m->counters.as<unsigned int>() + 2;
     a.totals = totals;
@@ -532,6 +547,7 @@ int evaluate_plan(nep_model* m, const Plan& p, const int* types_d, const double*
                   double* virial, double* site, double* totals)
 {
     NEP_TRY(ensure_plan_workspace(m, p));
+    m->eval_per_bead = virial != nullptr;
     NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
     NEP_TRY(run_cells<real>(m, p, types_d, pos_d));
     NEP_TRY(run_neighbors<real>(m, p));
@@ -874,6 +890,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         dr.acc = m->heat.as<double>();
         dr.rows = m->heat_rows.as<double>();
     }
+    m->eval_per_bead = dr.on != 0;
 
     // Size the neighbour lists (one synchronous probe) only for a new
     // configuration shape; continuation calls rely on the deferred status.
@@ -899,6 +916,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         }
         if (!forces_valid) NEP_TRY(md_forces<real>(m, p, n, force_d, dr));
     }
+    m->eval_per_bead = dr.on != 0;
     Thermostat th;
     if (noise) {
         NEP_TRY(m->noise_d.ensure(sizeof(double) * 2 * std::max(1, n_steps)));
@@ -1051,6 +1069,7 @@ int neighbors_impl(nep_model* m, int n, const int32_t* types, const double* pos,
     NEP_CUDA(cudaMemcpyAsync(m->types_d.p, types, sizeof(int) * n, cudaMemcpyHostToDevice, m->cur));
     NEP_CUDA(cudaMemcpyAsync(m->pos_d.p, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, m->cur));
     NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+    m->eval_per_bead = false;
     NEP_TRY(run_cells<real>(m, p, m->types_d.as<int>(), m->pos_d.as<double>()));
     NEP_TRY(run_neighbors<real>(m, p));
     NEP_TRY(check_lists<real>(m, p));
@@ -1823,7 +1842,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     L.totals = p; p = align256(p + 8 * 10);
     L.flags = p; p = align256(p + 16);
     L.tables = p; p = align256(p + kStaticTableBytes);
-    L.acc = p; p = align256(p + (rs == 4 ? 8 * 16 * n : 0));  // FP32 force scatter accumulators
+    L.acc = p; p = align256(p + (rs == 4 ? (32 + 96 + 36) * n : 0));  // FP32 force / virial lines, virial sums
     L.end = p;
     return L;
 }
@@ -1919,6 +1938,8 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     na.cntR = (int*)(base + L.cntR);
     na.cntA = (int*)(base + L.cntA);
     na.maxcnt = flags;
+    na.accF = sizeof(real) == 4 ? acc_force(base + L.acc) : nullptr;
+    na.accW = sizeof(real) == 4 && virial ? acc_virial(base + L.acc, n) : nullptr;
     e = launch_neighbors<real>(na, n_items, 2 * sizeof(real) * m->T * m->T, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     EvalArgs<real> a;
@@ -1943,7 +1964,9 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.force = force ? force : (double*)(base + L.force);
     a.virial = virial;
     a.site = site_energy;
-    a.acc = sizeof(real) == 4 ? (unsigned long long*)(base + L.acc) : nullptr;
+    a.accF = sizeof(real) == 4 ? acc_force(base + L.acc) : nullptr;
+    a.accW = sizeof(real) == 4 ? acc_virial(base + L.acc, n) : nullptr;
+    a.wsum = sizeof(real) == 4 ? acc_wsum(base + L.acc, n) : nullptr;
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
     a.totals = totals;

@@ -14,13 +14,15 @@
 //   F_i = sum_j (f_ij - f_ji),   W_i = sum_j r_ij (x) f_ji   (Eq. 15),
 // f_ij = dU_i/dr_ij, and E = sum U_i, W = sum W_i reduced in FP64 (Eq. 1, 16) by
 // a deterministic last-block pass:
-//   k_force_scatter (FP32)  radial pairs in gather form (f_ij and f_ji from i's
-//                           and j's stored gradient vectors); angular pairs
-//                           evaluated once, by i, contracting Phi_i only, with
-//                           -f_ij (and W_j's term) sent to j through 64-bit
-//                           fixed-point atomic adds (order-independent sums);
-//                           k_scatter_outputs converts the sums to FP64 outputs
-//   k_force (FP64)          gather form for both kinds of pair, no atomics
+//   FP32  k_descriptor also evaluates the angular pairs, in scatter form, from
+//         Phi_i while it is in registers (Phi never reaches memory): F_i keeps
+//         f_ij, and -f_ij (and W_j's term) go to j through 64-bit fixed-point
+//         atomic adds (order-independent sums); k_force_radial then takes the
+//         radial pairs in gather form (f_ij and f_ji from i's and j's stored
+//         gradient vectors), adds the accumulated angular part and writes the
+//         outputs
+//   FP64  k_descriptor stores Phi; k_force takes both kinds of pair in gather
+//         form, no atomics
 //
 // Angular pair gradient.  For A = g(r) Y(u), u = r/|r|, with Y a homogeneous
 // polynomial of degree l:  dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
@@ -521,7 +523,36 @@ __device__ __forceinline__ real four_body(const real* a, real* grad)
     return real(kQ4) * tr3;
 }
 
-template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0, int MBT = 0>
+// Per-thread state of the force pass for one particle i.
+template <typename real, int KRP>
+struct ForceCtx {
+    PosRec<real> ri;
+    int i, ti, T;
+    real len[3];
+    real F[3];
+    real W[9];
+};
+
+// 64-bit fixed-point accumulation (2^-32 units): integer sums do not depend on the
+// order in which atomic adds arrive, so scattered forces stay bitwise reproducible.
+constexpr float kFixScale = 4294967296.0f;  // 2^32 fixed-point units per eV/A (or eV)
+constexpr double kFixUnit = 1.0 / 4294967296.0;
+
+__device__ __forceinline__ void fix_add(unsigned long long* p, float v)
+{
+    atomicAdd(p, (unsigned long long)__float2ll_rn(v * kFixScale));
+}
+
+__device__ __forceinline__ double fix_value(unsigned long long v) { return (double)(long long)v * kFixUnit; }
+
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+
+template <typename real, int NA, int KA, typename Ctx>
+__device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                                      const real (&Phi)[NA][24], Ctx& c, bool per_bead);
+
+template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0, int MBT = 0, int FUSE = 0>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descriptor(EvalArgs<real> a)
 {
     // MBT = 1: the four-body q4_n (l = 2) and five-body q5_n = q_n1^2 follow the
@@ -541,11 +572,6 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
     const bool live = NET == 0 || it.begin + (int)threadIdx.x < it.end;
     const int i = live ? it.begin + threadIdx.x : it.end - 1;
     if (NET == 0 && i >= it.end) return;
-    if (live && a.acc) {  // the scatter accumulators of i start the force pass at zero
-        ulonglong2* z = reinterpret_cast<ulonglong2*>(a.acc + (size_t)i * 16);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) z[k] = make_ulonglong2(0ull, 0ull);
-    }
     const int T = md.T, H = md.H;
     const real len[3] = {(real)rq.g.len[0], (real)rq.g.len[1], (real)rq.g.len[2]};
     const PosRec<real> ri = a.rec[i];
@@ -756,28 +782,62 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descript
             ei[t * KRP + k] = v;
         }
     }
-    // Phi is stored component-major, [24][n][NAP]: for one component the rows of
-    // consecutive particles are adjacent, so a warp's row loads are contiguous
-    constexpr int NAP = phi_pad(NA);
-    real* ph = a.phi + (size_t)i * NAP;
-    const size_t kstride = (size_t)a.n * NAP;
     if constexpr (MBT == 1) {
         // dq5/dA_n1m = 2 q_n1 dq_n1/dA_n1m: fold into the l = 1 coefficient
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) dq[NR + nn] += real(2) * q[NR + nn] * dq[NR + 5 * NA + nn];
     }
+    if constexpr (FUSE == 1) {
+        // Phi_nlm in place of A_nlm, in registers; then the angular pairs' forces
+        // in scatter form (f_ij from Phi_i alone) while Phi_i is still here
 #pragma unroll
-    for (int k = 0; k < kNLM; ++k)
+        for (int k = 0; k < kNLM; ++k)
 #pragma unroll
-        for (int nn = 0; nn < NAP; ++nn) {
-            real v = real(0);
-            if (nn < NA) {
-                v = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+            for (int nn = 0; nn < NA; ++nn) {
+                real v = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
                 if constexpr (MBT == 1)
                     if (k >= 3 && k < 8) v += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
+                A[nn][k] = v;
             }
-            ph[k * kstride + nn] = v;
-        }
+        ForceCtx<real, KRP> c;
+        c.i = i;
+        c.T = T;
+        c.ri = ri;
+        c.ti = ti;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.len[k] = len[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.F[k] = real(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c.W[k] = real(0);
+        const bool per_bead = a.virial != nullptr;
+        force_angular_phi_reg<real, NA, KA>(a, P, off, A, c, per_bead);
+        // F_i's angular part into i's line; the thread's angular virial sum (what
+        // the totals use, with or without per-particle virials) as plain stores
+        unsigned long long* acc_i = a.accF + (size_t)i * 4;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) fix_add(acc_i + p, c.F[p]);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a.wsum[(size_t)k * a.n + i] = c.W[k];
+    } else {
+        // Phi is stored component-major, [24][n][NAP]: for one component the rows of
+        // consecutive particles are adjacent, so a warp's row loads are contiguous
+        constexpr int NAP = phi_pad(NA);
+        real* ph = a.phi + (size_t)i * NAP;
+        const size_t kstride = (size_t)a.n * NAP;
+#pragma unroll
+        for (int k = 0; k < kNLM; ++k)
+#pragma unroll
+            for (int nn = 0; nn < NAP; ++nn) {
+                real v = real(0);
+                if (nn < NA) {
+                    v = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+                    if constexpr (MBT == 1)
+                        if (k >= 3 && k < 8) v += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
+                }
+                ph[k * kstride + nn] = v;
+            }
+    }
 }
 
 template <typename real>
@@ -841,15 +901,6 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& i
     if (threadIdx.x == 0) counter[it.req] = 0u;
 }
 
-// Per-thread state of the force pass for one particle i.
-template <typename real, int KRP>
-struct ForceCtx {
-    PosRec<real> ri;
-    int i, ti, T;
-    real len[3];
-    real F[3];
-    real W[9];
-};
 
 // Radial pairs of slots s0, s0 + ds, ... :
 //   f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u,  F_i += f_ij - f_ji,
@@ -1078,34 +1129,17 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
     reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
 }
 
-// ---- FP32 scatter form -----------------------------------------------------------
-// Each ordered angular pair is evaluated once, by the thread of its centre i, which
-// contracts only Phi_i: f_ij = dU_i/dr_ij.  F_i gains f_ij in registers; F_j loses
-// it and W_j gains r_ji (x) f_ij through 64-bit fixed-point atomic adds.  Integer
-// sums do not depend on the order in which the adds arrive, so the results stay
-// bitwise reproducible.  The radial pairs stay in gather form (their reverse term
-// needs only j's 8-entry gradient vector).
-constexpr float kFixScale = 4294967296.0f;  // 2^32 fixed-point units per eV/A (or eV)
-constexpr double kFixUnit = 1.0 / 4294967296.0;
-
-__device__ __forceinline__ void fix_add(unsigned long long* p, float v)
-{
-    atomicAdd(p, (unsigned long long)__float2ll_rn(v * kFixScale));
-}
-
-__device__ __forceinline__ double fix_value(unsigned long long v) { return (double)(long long)v * kFixUnit; }
-
-__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
-__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
-
+// ---- FP32 form: angular pairs in scatter form inside the descriptor kernel ------
+// Each ordered angular pair is evaluated once, by the thread of its centre i, from
+// Phi_i alone while it is still in registers: f_ij = dU_i/dr_ij.  F_i gains f_ij
+// in registers; F_j loses it (and W_j gains r_ji (x) f_ij) through the fixed-point
+// atomic adds.  For A = g(r) Y(u) with Y homogeneous of degree l:
+//   dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
 template <typename real, int NA, int KA, typename Ctx>
-__device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
-                                                      Ctx& c, bool per_bead)
+__device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                                      const real (&Phi)[NA][24], Ctx& c, bool per_bead)
 {
     const int T = c.T, ti = c.ti;
-    constexpr int NAP = phi_pad(NA);
-    const size_t kstride = (size_t)a.n * NAP;
-    const real* phi_i = a.phi + (size_t)c.i * NAP;
     const int cA = min(a.cntA[c.i], a.mnA);
     NbrWalk<real> wa(a.nlA, a.n, c.i, cA, a.rec);
     for (int s = 0; s < cA; ++s) {
@@ -1140,13 +1174,11 @@ __device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, c
         real ga[3] = {real(0), real(0), real(0)};
 #pragma unroll
         for (int k = 0; k < kNLM; ++k) {
-            real pi_[NA];
-            loadN<real, NA>(phi_i + k * kstride, pi_);
             real G = real(0), dG = real(0);
 #pragma unroll
             for (int nn = 0; nn < NA; ++nn) {
-                G += pi_[nn] * g[nn];
-                dG += pi_[nn] * dg[nn];
+                G += Phi[nn][k] * g[nn];
+                dG += Phi[nn][k] * dg[nn];
             }
             real y, gx, gy, gz;
             sh_val_grad(k, mono, y, gx, gy, gz);
@@ -1156,31 +1188,35 @@ __device__ __forceinline__ void force_angular_scatter(const EvalArgs<real>& a, c
             ga[2] += G * gz;
         }
         const real fij[3] = {sr * ux + ga[0] * inv_r, sr * uy + ga[1] * inv_r, sr * uz + ga[2] * inv_r};
-        unsigned long long* acc_j = a.acc + (size_t)j * 16;
+        unsigned long long* acc_j = a.accF + (size_t)j * 4;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
             c.F[p] += fij[p];
             fix_add(acc_j + p, -fij[p]);
         }
+        // W_j += r_ji (x) f_ij; each product is rounded on its own, so the thread's
+        // sum (the totals) is the same whether or not it is also scattered
         const real d[3] = {dx, dy, dz};
+        unsigned long long* accw_j = per_bead ? a.accW + (size_t)j * 12 : nullptr;
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                // W_j += r_ji (x) f_ij; the product is rounded on its own so that the
-                // totals do not depend on whether it is also scattered
                 const real w = mul_rn(-d[p], fij[q]);
-                c.W[3 * p + q] += w;  // c.W feeds only the totals here
-                if (per_bead) fix_add(acc_j + 3 + 3 * p + q, w);
+                c.W[3 * p + q] += w;
+                if (per_bead) fix_add(accw_j + 3 * p + q, w);
             }
     }
 }
 
-// One thread per particle: radial pairs in gather form, angular pairs scattered.
-// Without per-particle virial output only the force is scattered; the virial
-// contributions of a thread's pairs go straight into the FP64 totals.
-template <typename real, int NR, int NA, int KR, int KA, int MB>
-__global__ void __launch_bounds__(kBlock, MB) k_force_scatter(EvalArgs<real> a)
+// Radial pairs in gather form, then i's outputs.  By the time this kernel runs the
+// descriptor kernel has finished every scatter, so i's fixed-point line holds the
+// angular part of F_i (its own and what its neighbours sent) and of W_i (per-particle
+// virials), or the thread's angular virial sum (totals only).  The kernel adds the
+// radial part, writes the caller-order FP64 outputs, clears the line for the next
+// evaluation, and reduces E and W in FP64 (Eq. 1, 16).
+template <typename real, int NR, int KR, int MB>
+__global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
 {
     constexpr int KRP = (KR + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1206,48 +1242,33 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_scatter(EvalArgs<real> a)
 #pragma unroll
         for (int k = 0; k < 9; ++k) c.W[k] = real(0);
         force_radial<real, NR, KR>(a, P, off, c, 0, 1);
-        unsigned long long* acc_i = a.acc + (size_t)i * 16;
-        const bool per_bead = a.virial != nullptr;
-        if (per_bead)  // W_i's radial part is complete here
+        ulonglong2* line = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
+        const ulonglong2 f01 = line[0], f2x = line[1];
+        line[0] = line[1] = make_ulonglong2(0ull, 0ull);
+        const int ui = a.perm[i];
+        const int lu = ui - rq.begin;
+        double* fo = a.force + (size_t)3 * rq.begin + lu;
+        fo[0] = fix_value(f01.x) + (double)c.F[0];
+        fo[rq.n] = fix_value(f01.y) + (double)c.F[1];
+        fo[(size_t)2 * rq.n] = fix_value(f2x.x) + (double)c.F[2];
+        if (a.virial) {  // W_i: the angular terms its neighbours sent, plus its radial terms
+            ulonglong2* wl = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
+            double* vo = a.virial + (size_t)9 * rq.begin + lu;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) fix_add(acc_i + 3 + k, c.W[k]);
-        force_angular_scatter<real, NA, KA>(a, P, off, c, per_bead);
-#pragma unroll
-        for (int p = 0; p < 3; ++p) fix_add(acc_i + p, c.F[p]);
+            for (int q = 0; q < 5; ++q) {
+                const ulonglong2 v = wl[q];
+                wl[q] = make_ulonglong2(0ull, 0ull);
+                vo[(size_t)(2 * q) * rq.n] = fix_value(v.x) + (double)c.W[2 * q];
+                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = fix_value(v.y) + (double)c.W[2 * q + 1];
+            }
+        }
         const real Ui = a.U[i];
-        if (a.site) a.site[a.perm[i]] = (double)Ui;
+        if (a.site) a.site[ui] = (double)Ui;
         tot[0] = (double)Ui;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)c.W[k];
+        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)a.wsum[(size_t)k * a.n + i] + (double)c.W[k];
     }
     reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
-}
-
-// The accumulated F_i (and W_i) to the caller-order FP64 outputs.
-template <typename real>
-__global__ void __launch_bounds__(kBlock) k_scatter_outputs(EvalArgs<real> a)
-{
-    const WorkItem it = a.items[blockIdx.x];
-    const ReqInfo& rq = a.reqs[it.req];
-    const int i = it.begin + threadIdx.x;
-    if (i >= it.end) return;
-    const ulonglong2* acc = reinterpret_cast<const ulonglong2*>(a.acc + (size_t)i * 16);
-    const int lu = a.perm[i] - rq.begin;
-    const ulonglong2 w01 = acc[0], w23 = acc[1];
-    double* fo = a.force + (size_t)3 * rq.begin + lu;
-    fo[0] = fix_value(w01.x);
-    fo[rq.n] = fix_value(w01.y);
-    fo[(size_t)2 * rq.n] = fix_value(w23.x);
-    if (a.virial) {
-        double* vo = a.virial + (size_t)9 * rq.begin + lu;
-        vo[0] = fix_value(w23.y);
-#pragma unroll
-        for (int q = 2; q < 6; ++q) {  // words 2q, 2q + 1 are W[2q - 3], W[2q - 2]
-            const ulonglong2 w = acc[q];
-            vo[(size_t)(2 * q - 3) * rq.n] = fix_value(w.x);
-            vo[(size_t)(2 * q - 2) * rq.n] = fix_value(w.y);
-        }
-    }
 }
 
 // ---- shape dispatch -----------------------------------------------------------
@@ -1263,47 +1284,57 @@ bool evaluate_shape_supported(int nR, int nA, int KR, int KA)
     return false;
 }
 
+// FP32: the descriptor kernel with the angular forces fused (K1) and the radial /
+// output kernel (K2); FP64: the descriptor kernel storing Phi and the gather-form
+// force kernel.  Variants: resident blocks per SM (register caps), and for the
+// descriptor the network form (NET) and the many-body terms (MBT).
+template <typename real, int A_, int B_, int C_, int D_, int MB>
+cudaError_t set_smem_desc(size_t smem)
+{
+    constexpr int FU = sizeof(real) == 4 ? 1 : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, A_, B_, C_, D_, MB, 0, 0, FU>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_descriptor<real, A_, B_, C_, D_, MB, 0, 1, FU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(real) == 4) {
+        e = cudaFuncSetAttribute(k_descriptor<real, A_, B_, C_, D_, MB, 1, 0, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_descriptor<real, A_, B_, C_, D_, MB, 1, 1, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    return e;
+}
+
+template <typename real, int A_, int B_, int C_, int D_, int MB>
+cudaError_t set_smem_force(size_t smem)
+{
+    if constexpr (sizeof(real) == 4)
+        return cudaFuncSetAttribute(k_force_radial<real, A_, C_, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    else
+        return cudaFuncSetAttribute(k_force<real, A_, B_, C_, D_, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+}
+
 template <typename real>
 cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, size_t smem_force)
 {
-#define NEP_SET(a_, b_, c_, d_, mb_)                                                                          \
-    {                                                                                                         \
-        cudaError_t e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_>,                         \
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);    \
-        if (e != cudaSuccess) return e;                                                                       \
-        e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 0, 1>,                               \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);                \
-        if (e != cudaSuccess) return e;                                                                       \
-        if constexpr (sizeof(real) == 4) {                                                                    \
-            e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 1>,                              \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);            \
-            if (e != cudaSuccess) return e;                                                                   \
-            e = cudaFuncSetAttribute(k_descriptor<real, a_, b_, c_, d_, mb_, 1, 1>,                           \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_desc);            \
-            if (e != cudaSuccess) return e;                                                                   \
-        }                                                                                                     \
-        if constexpr (sizeof(real) == 4)                                                                      \
-            e = cudaFuncSetAttribute(k_force_scatter<real, a_, b_, c_, d_, mb_>,                              \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
-        else                                                                                                  \
-            e = cudaFuncSetAttribute(k_force<real, a_, b_, c_, d_, mb_>,                                      \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force);           \
-        if (e != cudaSuccess) return e;                                                                       \
-    }
-#define NEP_CASE(a_, b_, c_, d_)                                                                              \
-    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                       \
-        NEP_SET(a_, b_, c_, d_, 2)                                                                            \
-        NEP_SET(a_, b_, c_, d_, 3)                                                                            \
-        if constexpr (sizeof(real) == 4) { /* the force kernel has a third variant, 4 blocks per SM */        \
-            cudaError_t e = cudaFuncSetAttribute(k_force_scatter<real, a_, b_, c_, d_, 4>,                   \
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_force); \
-            if (e != cudaSuccess) return e;                                                                   \
-        }                                                                                                     \
-        return cudaSuccess;                                                                                   \
+#define NEP_CASE(a_, b_, c_, d_)                                                                 \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                          \
+        cudaError_t e;                                                                           \
+        if ((e = set_smem_desc<real, a_, b_, c_, d_, 2>(smem_desc)) != cudaSuccess) return e;    \
+        if ((e = set_smem_desc<real, a_, b_, c_, d_, 3>(smem_desc)) != cudaSuccess) return e;    \
+        if ((e = set_smem_force<real, a_, b_, c_, d_, 2>(smem_force)) != cudaSuccess) return e;  \
+        if ((e = set_smem_force<real, a_, b_, c_, d_, 3>(smem_force)) != cudaSuccess) return e;  \
+        if constexpr (sizeof(real) == 4) /* K2 also at 4 blocks per SM */                        \
+            if ((e = set_smem_force<real, a_, b_, c_, d_, 4>(smem_force)) != cudaSuccess) return e; \
+        return cudaSuccess;                                                                      \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE
-#undef NEP_SET
     return cudaErrorInvalidValue;
 }
 
@@ -1312,13 +1343,16 @@ void launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_
 {
     if constexpr (sizeof(real) == 4) {
         if (a.net_bf16) {
-            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 1, MBT><<<nb, kBlock, smem, st>>>(a);
-            else k_descriptor<real, NR, NA, KR, KA, 3, 1, MBT><<<nb, kBlock, smem, st>>>(a);
-            return;
+            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 1, MBT, 1><<<nb, kBlock, smem, st>>>(a);
+            else k_descriptor<real, NR, NA, KR, KA, 3, 1, MBT, 1><<<nb, kBlock, smem, st>>>(a);
+        } else {
+            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 1><<<nb, kBlock, smem, st>>>(a);
+            else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 1><<<nb, kBlock, smem, st>>>(a);
         }
+    } else {
+        if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 0><<<nb, kBlock, smem, st>>>(a);
+        else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 0><<<nb, kBlock, smem, st>>>(a);
     }
-    if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT><<<nb, kBlock, smem, st>>>(a);
-    else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT><<<nb, kBlock, smem, st>>>(a);
 }
 
 template <typename real>
@@ -1327,25 +1361,24 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
 {
     const int nb = n_items;
     if constexpr (sizeof(real) == 4) {
-        if (!a.acc) return cudaErrorInvalidValue;  // the FP32 form scatters into a.acc
+        if (!a.accF || !a.wsum) return cudaErrorInvalidValue;  // the FP32 form scatters into a.accF
     }
-#define NEP_CASE(a_, b_, c_, d_)                                                                            \
-    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                     \
-        if (a.many_body)                                                                                    \
-            launch_descriptor<real, a_, b_, c_, d_, 1>(a, nb, smem_desc, st, mb_desc);                      \
-        else                                                                                                \
-            launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc);                      \
-        if (mid) cudaEventRecord(mid, st);                                                                  \
-        if constexpr (sizeof(real) == 4) {                                                                  \
-            if (mb_force == 4) k_force_scatter<real, a_, b_, c_, d_, 4><<<nb, kBlock, smem_force, st>>>(a); \
-            else if (mb_force == 3) k_force_scatter<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a); \
-            else k_force_scatter<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);               \
-            k_scatter_outputs<real><<<nb, kBlock, 0, st>>>(a);                                              \
-        } else {                                                                                            \
-            if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);         \
-            else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                       \
-        }                                                                                                   \
-        return cudaGetLastError();                                                                          \
+#define NEP_CASE(a_, b_, c_, d_)                                                                          \
+    if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                   \
+        if (a.many_body)                                                                                  \
+            launch_descriptor<real, a_, b_, c_, d_, 1>(a, nb, smem_desc, st, mb_desc);                    \
+        else                                                                                              \
+            launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc);                    \
+        if (mid) cudaEventRecord(mid, st);                                                                \
+        if constexpr (sizeof(real) == 4) {                                                                \
+            if (mb_force == 4) k_force_radial<real, a_, c_, 4><<<nb, kBlock, smem_force, st>>>(a);        \
+            else if (mb_force == 3) k_force_radial<real, a_, c_, 3><<<nb, kBlock, smem_force, st>>>(a);   \
+            else k_force_radial<real, a_, c_, 2><<<nb, kBlock, smem_force, st>>>(a);                      \
+        } else {                                                                                          \
+            if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);       \
+            else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                     \
+        }                                                                                                 \
+        return cudaGetLastError();                                                                        \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE

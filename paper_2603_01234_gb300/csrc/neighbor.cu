@@ -288,6 +288,15 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         }
         a.cntR[i] = nr;
         a.cntA[i] = na;
+        if (a.accF) {  // i's fixed-point lines start the evaluation at zero
+            ulonglong2* z = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
+            z[0] = z[1] = make_ulonglong2(0ull, 0ull);
+        }
+        if (a.accW) {
+            ulonglong2* z = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) z[k] = make_ulonglong2(0ull, 0ull);
+        }
     }
     // warp maxima, then one atomic per warp
 #pragma unroll

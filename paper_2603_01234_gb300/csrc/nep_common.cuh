@@ -161,6 +161,8 @@ struct NeighborArgs {
     int* cntR;                  // [n]
     int* cntA;                  // [n]
     int* maxcnt;                // [2]
+    unsigned long long* accF;   // FP32 form: [n][4] fixed-point force lines, zeroed here for the evaluation (or null)
+    unsigned long long* accW;   // FP32 form with per-particle virials: [n][12] fixed-point virial lines (or null)
 };
 
 template <typename real>
@@ -177,14 +179,18 @@ struct EvalArgs {
     real* U;                    // [n] sorted site energies
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
-    real* phi;                  // [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
+    real* phi;                  // FP64 form: [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
     int net_bf16;               // 1: the hidden layer's products in BF16 on tensor cores
     int many_body;              // 1: the four- and five-body descriptors follow the three-body ones
     const int* perm;            // sorted slot -> caller index
     double* force;              // per request [3][n_r] blocks (required)
     double* virial;             // per request [9][n_r] blocks, or null
     double* site;               // [n] or null
-    unsigned long long* acc;    // FP32 scatter form: [n][16] fixed-point F[3], W[9] (2^-32 units)
+    unsigned long long* accF;   // FP32 form: [n][4] fixed-point F[3] (2^-32 eV/A units); zero on entry,
+                                // left zero by the radial/output kernel
+    unsigned long long* accW;   // FP32 form with per-particle virials: [n][12] fixed-point W[9] (2^-32 eV),
+                                // same rules; used only when virial is non-null
+    float* wsum;                // FP32 form: [9][n] each thread's angular virial sum (for the totals)
     double* partial;            // [items][10] per-block (E, W[9])
     unsigned int* counter;      // [requests] last-block counters (self-resetting)
     double* totals;             // [requests][10]: E, W[9]
