@@ -144,20 +144,55 @@ struct GraphCache {
         key.clear();
     }
 };
+constexpr size_t kEvalGraphs = 8;  // evaluation graphs kept per handle
 
 
-// Host copy of one batch layout and its device tables (requests, work items, models).
+// Host copy of one batch layout and its device tables (counts, requests, work
+// items, models).  Launch shapes and workspace strides follow the capacities
+// (n_cap, items_cap, ncell_cap >= the counts): equal to the counts for a single
+// configuration, rounded up to a size class for batches, so that batches of
+// similar size replay one captured graph.
 struct Plan {
     std::vector<ReqInfo> reqs;
     std::vector<WorkItem> items;
     std::vector<unsigned char> models;  // ModelDesc<real> entries, raw bytes
     int n = 0, ncell = 0, n_models = 0;
+    int n_cap = 0, items_cap = 0, ncell_cap = 0, req_cap = 0;
     int Tmax = 1;
     size_t smem_desc = 0, smem_force = 0, smem_nbr = 0;
     std::vector<unsigned char> key;     // identity of the uploaded tables
-    Buf dev;                            // [reqs | items | models] on the device
-    size_t off_items = 0, off_models = 0;
+    Buf dev;                            // [counts | reqs | items | models] on the device
+    size_t off_reqs = 0, off_items = 0, off_models = 0;
 };
+
+// Size class of a batch dimension: x rounded up to a multiple of 1/8 of the power
+// of two below it (at least `quantum`), so a class wastes at most 1/8.
+int size_class(int x, int quantum)
+{
+    if (x <= quantum) return quantum;
+    int p2 = 1;
+    while (p2 * 2 <= x) p2 *= 2;
+    const int step = std::max(quantum, p2 / 8);
+    return (int)(((long long)x + step - 1) / step * step);
+}
+
+// Capacities equal to the counts (single configurations, MD) or rounded to size
+// classes (batches).
+void set_caps(Plan& p, bool classes)
+{
+    const int n_items = (int)p.items.size();
+    if (!classes) {
+        p.n_cap = p.n;
+        p.items_cap = n_items;
+        p.ncell_cap = p.ncell;
+        p.req_cap = (int)p.reqs.size();
+        return;
+    }
+    p.n_cap = size_class(p.n, kBlock);
+    p.items_cap = size_class(n_items, 8);
+    p.ncell_cap = size_class(p.ncell, 64);
+    p.req_cap = size_class((int)p.reqs.size(), 8);
+}
 
 }  // namespace
 
@@ -192,6 +227,7 @@ struct nep_model {
     Buf partial, partial2, counters, totals, flags, thermo, sample_index;
     Buf acc;  // FP32 form: force and virial fixed-point lines, thread virial sums (acc_bytes)
     bool eval_per_bead = false;  // the evaluation in progress returns per-particle virials
+    bool cells_dirty = true;     // the cell counters may be non-zero (new buffer, or a build that failed)
     Buf types_d, pos_d, vel_d, force_d, virial_d, site_d, force_tmp, totals_tmp;
     Buf noise_d, bussi;  // thermostat: random numbers of the call; [step, alpha] words
     Buf md_virial, md_site, heat, heat_rows;  // HNEMD: per-particle W_i and U_i; acc[6] + counter; rows
@@ -202,7 +238,8 @@ struct nep_model {
     size_t h_stage_cap = 0;
     size_t n_lists = 0;  // particles the lists were sized for
     Plan plan;
-    GraphCache graph;
+    GraphCache graph;                    // MD step chunk
+    std::vector<GraphCache> eval_graphs;  // nep_compute / nep_compute_batch evaluations
     StageTimer timer;
 };
 
@@ -313,12 +350,17 @@ int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
         const unsigned char* b = (const unsigned char*)q;
         key.insert(key.end(), b, b + s);
     };
+    const PlanCounts counts{p.n, (int)p.items.size(), p.ncell, (int)p.reqs.size()};
+    put(&counts, sizeof counts);
     put(p.reqs.data(), sizeof(ReqInfo) * p.reqs.size());
     put(p.items.data(), sizeof(WorkItem) * p.items.size());
     put(p.models.data(), p.models.size());
     if (!force_upload && key == p.key && p.dev.p) return NEP_OK;
-    p.off_items = align16(sizeof(ReqInfo) * p.reqs.size());
-    p.off_models = p.off_items + align16(sizeof(WorkItem) * p.items.size());
+    // the regions are laid out by capacity, so their offsets (which the kernels'
+    // arguments carry, and a captured graph keeps) depend only on the capacities
+    p.off_reqs = align16(sizeof(PlanCounts));
+    p.off_items = p.off_reqs + align16(sizeof(ReqInfo) * std::max<size_t>(p.req_cap, p.reqs.size()));
+    p.off_models = p.off_items + align16(sizeof(WorkItem) * std::max<size_t>(p.items_cap, p.items.size()));
     const size_t bytes = p.off_models + p.models.size();
     NEP_TRY(p.dev.ensure(bytes));
     if (m->plan_pending) NEP_CUDA(cudaEventSynchronize(m->ev_plan));  // staging free again
@@ -330,7 +372,8 @@ int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
         NEP_CUDA(cudaMallocHost((void**)&m->h_stage, bytes + bytes / 2));
         m->h_stage_cap = bytes + bytes / 2;
     }
-    memcpy(m->h_stage, p.reqs.data(), sizeof(ReqInfo) * p.reqs.size());
+    memcpy(m->h_stage, &counts, sizeof counts);
+    memcpy(m->h_stage + p.off_reqs, p.reqs.data(), sizeof(ReqInfo) * p.reqs.size());
     memcpy(m->h_stage + p.off_items, p.items.data(), sizeof(WorkItem) * p.items.size());
     memcpy(m->h_stage + p.off_models, p.models.data(), p.models.size());
     NEP_CUDA(cudaMemcpyAsync(p.dev.p, m->h_stage, bytes, cudaMemcpyHostToDevice, m->cur));
@@ -340,7 +383,8 @@ int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
     return NEP_OK;
 }
 
-const ReqInfo* d_reqs(const Plan& p) { return p.dev.as<ReqInfo>(); }
+const PlanCounts* d_counts(const Plan& p) { return p.dev.as<PlanCounts>(); }
+const ReqInfo* d_reqs(const Plan& p) { return (const ReqInfo*)((const unsigned char*)p.dev.p + p.off_reqs); }
 const WorkItem* d_items(const Plan& p) { return (const WorkItem*)((const unsigned char*)p.dev.p + p.off_items); }
 template <typename real>
 const ModelDesc<real>* d_models(const Plan& p)
@@ -356,6 +400,7 @@ int single_plan(nep_model* m, int n, const CellGrid& g)
     p.items.clear();
     p.n = p.ncell = 0;
     add_request(p, g, n, 0);
+    set_caps(p, false);
     nep_model* one[1] = {m};
     set_models<real>(p, one, 1);
     return upload_plan(m, p);
@@ -407,19 +452,24 @@ int ensure_lists(nep_model* m, int n)
 
 int ensure_cells(nep_model* m, int ncell)
 {
+    // the scan leaves the cell and fill counters zero for the next build; a new
+    // buffer starts with anything in it, so the next build clears them first
+    const void* c0 = m->cell_count.p;
+    const void* f0 = m->cell_fill.p;
     NEP_TRY(m->cell_count.ensure(sizeof(int) * ncell));
     NEP_TRY(m->cell_local.ensure(sizeof(int) * ncell));
     NEP_TRY(m->block_off.ensure(sizeof(int) * (kScanItems + 1)));
     NEP_TRY(m->cell_fill.ensure(sizeof(int) * ncell));
     NEP_TRY(m->cell_start.ensure(sizeof(int) * (ncell + 1)));
+    if (m->cell_count.p != c0 || m->cell_fill.p != f0) m->cells_dirty = true;
     return NEP_OK;
 }
 
 int ensure_plan_workspace(nep_model* m, const Plan& p)
 {
-    NEP_TRY(ensure_particles(m, p.n, (int)p.items.size(), (int)p.reqs.size(), p.Tmax));
-    NEP_TRY(ensure_cells(m, p.ncell));
-    if ((size_t)p.n > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, p.n));
+    NEP_TRY(ensure_particles(m, p.n_cap, p.items_cap, (int)p.reqs.size(), p.Tmax));
+    NEP_TRY(ensure_cells(m, p.ncell_cap));
+    if ((size_t)p.n_cap > m->n_lists || !m->nlR.p) NEP_TRY(ensure_lists(m, p.n_cap));
     return NEP_OK;
 }
 
@@ -446,11 +496,16 @@ template <typename real>
 int run_cells(nep_model* m, const Plan& p, const int* types_d, const double* pos_d)
 {
     cudaError_t e = launch_cell_build<real>(
-        p.n, (int)p.items.size(), p.ncell, d_items(p), d_reqs(p), d_models<real>(p), pos_d, types_d,
-        m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(), m->cell_count.as<int>(), m->cell_local.as<int>(),
-        m->block_off.as<int>(), m->cell_fill.as<int>(), m->perm_tmp.as<int>(), m->perm.as<int>(),
-        m->cell_start.as<int>(), m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(), m->flags.as<int>() + 2, m->cur);
-    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
+        d_counts(p), p.n_cap, p.items_cap, p.ncell_cap, m->cells_dirty, d_items(p), d_reqs(p), d_models<real>(p),
+        pos_d, types_d, m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(), m->cell_count.as<int>(),
+        m->cell_local.as<int>(), m->block_off.as<int>(), m->cell_fill.as<int>(), m->perm_tmp.as<int>(),
+        m->perm.as<int>(), m->cell_start.as<int>(), m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(),
+        m->flags.as<int>() + 2, m->cur);
+    if (e != cudaSuccess) {
+        m->cells_dirty = true;
+        return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
+    }
+    m->cells_dirty = false;
     return NEP_OK;
 }
 
@@ -458,9 +513,10 @@ template <typename real>
 int run_neighbors(nep_model* m, const Plan& p)
 {
     NeighborArgs<real> a;
-    a.n = p.n;
+    a.n = p.n_cap;
     a.mnR = m->mnR;
     a.mnA = m->mnA;
+    a.counts = d_counts(p);
     a.items = d_items(p);
     a.reqs = d_reqs(p);
     a.models = d_models<real>(p);
@@ -475,10 +531,10 @@ int run_neighbors(nep_model* m, const Plan& p)
     // the FP32 form's fixed-point lines are zeroed by the neighbour kernel (virial
     // lines only when this evaluation returns per-particle virials)
     a.accF = m->precision != NEP_FP64 ? acc_force(m->acc.p) : nullptr;
-    a.accW = m->precision != NEP_FP64 && m->eval_per_bead ? acc_virial(m->acc.p, p.n) : nullptr;
+    a.accW = m->precision != NEP_FP64 && m->eval_per_bead ? acc_virial(m->acc.p, p.n_cap) : nullptr;
     if ((uint64_t)std::max(a.mnR, a.mnA) * (uint64_t)a.n > (1ull << 32))
         return fail(NEP_ERR_ARG, "neighbour lists beyond 2^32 entries (capacity x particles)");
-    cudaError_t e = launch_neighbors<real>(a, (int)p.items.size(), p.smem_nbr, m->cur);
+    cudaError_t e = launch_neighbors<real>(a, p.items_cap, p.smem_nbr, m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
@@ -488,9 +544,10 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
                  cudaEvent_t mid = nullptr)
 {
     EvalArgs<real> a;
-    a.n = p.n;
+    a.n = p.n_cap;
     a.mnR = m->mnR;
     a.mnA = m->mnA;
+    a.counts = d_counts(p);
     a.items = d_items(p);
     a.reqs = d_reqs(p);
     a.models = d_models<real>(p);
@@ -510,12 +567,12 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.virial = virial;
     a.site = site;
     a.accF = acc_force(m->acc.p);
-    a.accW = acc_virial(m->acc.p, p.n);
-    a.wsum = acc_wsum(m->acc.p, p.n);
+    a.accW = acc_virial(m->acc.p, p.n_cap);
+    a.wsum = acc_wsum(m->acc.p, p.n_cap);
     a.partial = m->partial.as<double>();
     a.counter = m->counters.as<unsigned int>() + 2;
     a.totals = totals;
-    cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, (int)p.items.size(), p.smem_desc,
+    cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, p.items_cap, p.smem_desc,
                                           p.smem_force, m->cur, mid, m->mb_desc, m->mb_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     return NEP_OK;
@@ -534,14 +591,16 @@ int check_lists(nep_model* m, const Plan& p)
         if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
         if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
         if (needA > m->mnA) m->mnA = ((int)(needA * 1.25) + 8 + 7) & ~7;
-        NEP_TRY(ensure_lists(m, p.n));
+        NEP_TRY(ensure_lists(m, p.n_cap));
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 2 * sizeof(int), m->cur));
         NEP_TRY(run_neighbors<real>(m, p));
     }
     return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity did not converge");
 }
 
-// Full evaluation of the uploaded plan on device arrays.  force must be non-null.
+// Full evaluation of the uploaded plan on device arrays, with a synchronous check of
+// the list sizes before the evaluation (used where the call synchronises anyway).
+// force must be non-null.
 template <typename real>
 int evaluate_plan(nep_model* m, const Plan& p, const int* types_d, const double* pos_d, double* force,
                   double* virial, double* site, double* totals)
@@ -553,6 +612,104 @@ int evaluate_plan(nep_model* m, const Plan& p, const int* types_d, const double*
     NEP_TRY(run_neighbors<real>(m, p));
     NEP_TRY(check_lists<real>(m, p));
     NEP_TRY(run_evaluate<real>(m, p, force, virial, site, totals));
+    return NEP_OK;
+}
+
+// The evaluation pipeline of the uploaded plan with no host synchronisation: status
+// words cleared, cell build, neighbour lists, descriptor + forces.  List overflow
+// and bad inputs are read afterwards from the status words (eval_status).
+template <typename real>
+int eval_pipeline(nep_model* m, const Plan& p, const int* types_d, const double* pos_d, double* force,
+                  double* virial, double* site, double* totals)
+{
+    NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
+    NEP_TRY(run_cells<real>(m, p, types_d, pos_d));
+    NEP_TRY(run_neighbors<real>(m, p));
+    NEP_TRY(run_evaluate<real>(m, p, force, virial, site, totals));
+    return NEP_OK;
+}
+
+// Everything a captured evaluation graph bakes in: launch shapes, shared-memory
+// sizes, kernel variants, list capacities and every device pointer.
+template <typename real>
+std::vector<unsigned char> eval_graph_key(const nep_model* m, const Plan& p, const void* const* io, int n_io)
+{
+    std::vector<unsigned char> key;
+    auto put = [&](const void* q, size_t sz) {
+        const unsigned char* b = (const unsigned char*)q;
+        key.insert(key.end(), b, b + sz);
+    };
+    const int ints[] = {p.n_cap, p.items_cap, p.ncell_cap, p.Tmax, m->mnR, m->mnA, m->mb_desc, m->mb_force,
+                        m->eval_per_bead ? 1 : 0, m->precision, m->MBT, (int)sizeof(real)};
+    put(ints, sizeof ints);
+    const size_t sm[] = {p.smem_desc, p.smem_force, p.smem_nbr, p.off_reqs, p.off_items, p.off_models};
+    put(sm, sizeof sm);
+    const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
+                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
+                         &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->counters, &m->flags,
+                         &m->acc, &p.dev};
+    for (const Buf* b : bufs) put(&b->p, sizeof(void*));
+    put(io, sizeof(void*) * n_io);
+    return key;
+}
+
+// The evaluation pipeline, replayed from a captured CUDA graph when one matches
+// (cached on the handle, a few at a time).  Batches are planned with rounded
+// capacities and the kernels read the actual sizes from the device, so batches of
+// similar size share one graph.  A build whose cell counters may be dirty runs
+// eagerly (it clears them first).
+template <typename real>
+int eval_launch(nep_model* m, const Plan& p, const int* types_d, const double* pos_d, double* force,
+                double* virial, double* site, double* totals)
+{
+    NEP_TRY(ensure_plan_workspace(m, p));
+    m->eval_per_bead = virial != nullptr;
+    if (m->cells_dirty) return eval_pipeline<real>(m, p, types_d, pos_d, force, virial, site, totals);
+    const void* io[] = {types_d, pos_d, force, virial, site, totals};
+    std::vector<unsigned char> key = eval_graph_key<real>(m, p, io, 6);
+    for (size_t k = 0; k < m->eval_graphs.size(); ++k)
+        if (m->eval_graphs[k].key == key) {
+            NEP_CUDA(cudaGraphLaunch(m->eval_graphs[k].exec, m->cur));
+            return NEP_OK;
+        }
+    NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
+    const int rc = eval_pipeline<real>(m, p, types_d, pos_d, force, virial, site, totals);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
+    if (rc != NEP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        m->cells_dirty = true;
+        return rc;
+    }
+    if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+    GraphCache gc;
+    ec = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ec));
+    gc.key = key;
+    if (m->eval_graphs.size() >= kEvalGraphs) {  // drop the oldest
+        m->eval_graphs.front().reset();
+        m->eval_graphs.erase(m->eval_graphs.begin());
+    }
+    m->eval_graphs.push_back(gc);
+    NEP_CUDA(cudaGraphLaunch(m->eval_graphs.back().exec, m->cur));
+    return NEP_OK;
+}
+
+// Deferred status of an evaluation, read from h_flags after the call synchronised:
+// a bad input fails the call; lists that outgrew their capacity are grown and the
+// caller runs the evaluation again (retry = true).
+int eval_status(nep_model* m, bool& retry)
+{
+    retry = false;
+    if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
+    if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+    const int needR = m->h_flags[0], needA = m->h_flags[1];
+    if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
+    if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
+    if (needA > m->mnA) m->mnA = ((int)(needA * 1.25) + 8 + 7) & ~7;
+    m->n_lists = 0;  // reallocate at the new capacity
+    retry = true;
     return NEP_OK;
 }
 
@@ -639,24 +796,37 @@ int compute_impl(nep_model* m, int n, const int32_t* types, const double* pos, c
         force_d = m->force_tmp.as<double>();
     }
     double* totals = m->totals.as<double>();
-    NEP_TRY(evaluate_plan<real>(m, m->plan, types_d, pos_d, force_d, virial_d, site_d, totals));
-    if (mem == NEP_HOST) {
-        NEP_TRY(ensure_host_totals(m, 10));
-        if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
-        if (virial) NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
-        if (site_energy)
-            NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
-        NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
+    NEP_TRY(ensure_host_totals(m, 10));
+    // one synchronisation per call: the evaluation, its outputs and its status words
+    // are enqueued together; lists that overflowed are grown and the call runs again
+    for (int attempt = 0;; ++attempt) {
+        NEP_TRY(eval_launch<real>(m, m->plan, types_d, pos_d, force_d, virial_d, site_d, totals));
+        if (mem == NEP_HOST) {
+            if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+            if (virial)
+                NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
+            if (site_energy)
+                NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
+            NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10, cudaMemcpyDeviceToHost, m->cur));
+        } else {
+            if (energy_total)
+                NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
+            if (virial_total)
+                NEP_CUDA(cudaMemcpyAsync(virial_total, totals + 1, sizeof(double) * 9, cudaMemcpyDeviceToDevice,
+                                         m->cur));
+        }
+        NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
         NEP_TRY(leave(m, stream));
+        bool retry = false;
+        NEP_TRY(eval_status(m, retry));
+        if (!retry) break;
+        if (attempt == 2) return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity did not converge");
+        NEP_TRY(enter(m, stream));
+    }
+    if (mem == NEP_HOST) {
         if (energy_total) *energy_total = m->h_totals[0];
         if (virial_total)
             for (int k = 0; k < 9; ++k) virial_total[k] = m->h_totals[1 + k];
-    } else {
-        if (energy_total)
-            NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
-        if (virial_total)
-            NEP_CUDA(cudaMemcpyAsync(virial_total, totals + 1, sizeof(double) * 9, cudaMemcpyDeviceToDevice, m->cur));
-        NEP_TRY(leave(m, stream));
     }
     return NEP_OK;
 }
@@ -962,6 +1132,8 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&th, sizeof th);
         put(&m->mb_desc, sizeof m->mb_desc);
         put(&m->mb_force, sizeof m->mb_force);
+        const size_t offs[] = {p.off_reqs, p.off_items, p.off_models};
+        put(offs, sizeof offs);
         const void* tptr[] = {m->bussi.p, dr.virial, dr.site, dr.acc, dr.rows};
         put(tptr, sizeof tptr);
         put(&dr.on, sizeof dr.on);
@@ -1135,6 +1307,7 @@ int batch_impl(nep_model* const* models, int n_models, int n_req, const int32_t*
             return fail(NEP_ERR_ARG, "batch cell grids too large");
         add_request(p, g, req_n[r], req_model[r]);
     }
+    set_caps(p, true);  // size classes: batches of similar size replay one graph
     set_models<real>(p, models, n_models);
     (void)rc_max;
     NEP_TRY(enter(m, stream));
@@ -1174,30 +1347,41 @@ int batch_impl(nep_model* const* models, int n_models, int n_req, const int32_t*
         force_d = m->force_tmp.as<double>();
     }
     double* totals = m->totals.as<double>();
-    NEP_TRY(evaluate_plan<real>(m, p, types_d, pos_d, force_d, virial_d, site_d, totals));
-    if (mem == NEP_HOST) {
-        NEP_TRY(ensure_host_totals(m, 10 * (size_t)n_req));
-        if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
-        if (virial) NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
-        if (site_energy)
-            NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
-        NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10 * n_req, cudaMemcpyDeviceToHost, m->cur));
+    NEP_TRY(ensure_host_totals(m, 10 * (size_t)n_req));
+    // one synchronisation per batch (see compute_impl)
+    for (int attempt = 0;; ++attempt) {
+        NEP_TRY(eval_launch<real>(m, p, types_d, pos_d, force_d, virial_d, site_d, totals));
+        if (mem == NEP_HOST) {
+            if (force) NEP_CUDA(cudaMemcpyAsync(force, force_d, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, m->cur));
+            if (virial)
+                NEP_CUDA(cudaMemcpyAsync(virial, virial_d, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, m->cur));
+            if (site_energy)
+                NEP_CUDA(cudaMemcpyAsync(site_energy, site_d, sizeof(double) * n, cudaMemcpyDeviceToHost, m->cur));
+            NEP_CUDA(cudaMemcpyAsync(m->h_totals, totals, sizeof(double) * 10 * n_req, cudaMemcpyDeviceToHost,
+                                     m->cur));
+        } else {
+            // totals [req][10] -> energy[req], virial_total[req][9] on the device
+            if (energy)
+                NEP_CUDA(cudaMemcpy2DAsync(energy, sizeof(double), totals, 10 * sizeof(double), sizeof(double), n_req,
+                                           cudaMemcpyDeviceToDevice, m->cur));
+            if (virial_total)
+                NEP_CUDA(cudaMemcpy2DAsync(virial_total, 9 * sizeof(double), totals + 1, 10 * sizeof(double),
+                                           9 * sizeof(double), n_req, cudaMemcpyDeviceToDevice, m->cur));
+        }
+        NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
         NEP_TRY(leave(m, stream));
+        bool retry = false;
+        NEP_TRY(eval_status(m, retry));
+        if (!retry) break;
+        if (attempt == 2) return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "neighbour capacity did not converge");
+        NEP_TRY(enter(m, stream));
+    }
+    if (mem == NEP_HOST)
         for (int r = 0; r < n_req; ++r) {
             if (energy) energy[r] = m->h_totals[10 * r];
             if (virial_total)
                 for (int k = 0; k < 9; ++k) virial_total[9 * r + k] = m->h_totals[10 * r + 1 + k];
         }
-    } else {
-        // totals [req][10] -> energy[req], virial_total[req][9] on the device
-        if (energy)
-            NEP_CUDA(cudaMemcpy2DAsync(energy, sizeof(double), totals, 10 * sizeof(double), sizeof(double), n_req,
-                                       cudaMemcpyDeviceToDevice, m->cur));
-        if (virial_total)
-            NEP_CUDA(cudaMemcpy2DAsync(virial_total, 9 * sizeof(double), totals + 1, 10 * sizeof(double),
-                                       9 * sizeof(double), n_req, cudaMemcpyDeviceToDevice, m->cur));
-        NEP_TRY(leave(m, stream));
-    }
     return NEP_OK;
 }
 
@@ -1239,6 +1423,8 @@ int nep_destroy(nep_model* m)
     if (m->async_pending && m->ev_flags) cudaEventSynchronize(m->ev_flags);
     if (m->plan_pending && m->ev_plan) cudaEventSynchronize(m->ev_plan);
     m->graph.reset();
+    for (GraphCache& g : m->eval_graphs) g.reset();
+    m->eval_graphs.clear();
     m->timer.destroy();
     Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
                    &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
@@ -1800,10 +1986,10 @@ constexpr int kStaticMaxKRP = 12;        // padded K_R
 constexpr int kStaticMaxItems = (kStaticMaxN + kBlock - 1) / kBlock;
 constexpr size_t kStaticTableBytes = 2048;  // one request, its work items, one model
 constexpr int kStaticMaxDevices = 64;
-// the request, its work items and one model table must fit the table region
-static_assert(align16(sizeof(ReqInfo)) + align16(sizeof(WorkItem) * kStaticMaxItems) +
+// the counts, the request, its work items and one model table must fit the table region
+static_assert(align16(sizeof(PlanCounts)) + align16(sizeof(ReqInfo)) + align16(sizeof(WorkItem) * kStaticMaxItems) +
                       sizeof(ModelDesc<double>) <= kStaticTableBytes,
-              "static table region too small for the request, its work items and the model table");
+              "static table region too small for the counts, the request, its work items and the model table");
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -1897,16 +2083,20 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     for (int b = 0; b < n; b += kBlock) items[n_items++] = WorkItem{0, b, std::min(n, b + kBlock)};
     rq.item_end = n_items;
     const ModelDesc<real> md = model_desc<real>(m);
-    const size_t off_items = align16(sizeof(ReqInfo)), off_models = off_items + align16(sizeof(WorkItem) * n_items);
+    const PlanCounts counts{n, n_items, g.ncell, 1};
+    const size_t off_rq = align16(sizeof(PlanCounts)), off_items = off_rq + align16(sizeof(ReqInfo)),
+                 off_models = off_items + align16(sizeof(WorkItem) * n_items);
     if (m->plan_pending) NEP_CUDA(cudaEventSynchronize(m->ev_plan));
-    memcpy(m->h_stage, &rq, sizeof rq);
+    memcpy(m->h_stage, &counts, sizeof counts);
+    memcpy(m->h_stage + off_rq, &rq, sizeof rq);
     memcpy(m->h_stage + off_items, items, sizeof(WorkItem) * n_items);
     memcpy(m->h_stage + off_models, &md, sizeof md);
     unsigned char* tables = base + L.tables;
     NEP_CUDA(cudaMemcpyAsync(tables, m->h_stage, off_models + sizeof md, cudaMemcpyHostToDevice, m->cur));
     NEP_CUDA(cudaEventRecord(m->ev_plan, m->cur));
     m->plan_pending = true;
-    const ReqInfo* d_rq = (const ReqInfo*)tables;
+    const PlanCounts* d_cnt = (const PlanCounts*)tables;
+    const ReqInfo* d_rq = (const ReqInfo*)(tables + off_rq);
     const WorkItem* d_it = (const WorkItem*)(tables + off_items);
     const ModelDesc<real>* d_md = (const ModelDesc<real>*)(tables + off_models);
 
@@ -1917,8 +2107,9 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     // (the cell counters are cleared by the cell build itself)
     NEP_CUDA(cudaMemsetAsync(flags, 0, 16, m->cur));
     NEP_CUDA(cudaMemsetAsync(counters, 0, 16, m->cur));
+    // the scratch's regions move with n, so the cell counters are cleared here
     cudaError_t e = launch_cell_build<real>(
-        n, n_items, g.ncell, d_it, d_rq, d_md, pos, types, (int*)(base + L.cell_of),
+        d_cnt, n, n_items, g.ncell, true, d_it, d_rq, d_md, pos, types, (int*)(base + L.cell_of),
         (PosRec<real>*)(base + L.rec_user), (int*)(base + L.cell_count), (int*)(base + L.cell_local),
         (int*)(base + L.block_off), (int*)(base + L.cell_fill), (int*)(base + L.perm_tmp), (int*)(base + L.perm),
         (int*)(base + L.cell_start), (int*)(base + L.cell_s), (PosRec<real>*)(base + L.rec_s), flags + 2, m->cur);
@@ -1927,6 +2118,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     na.n = n;
     na.mnR = kStaticMNR;
     na.mnA = kStaticMNA;
+    na.counts = d_cnt;
     na.items = d_it;
     na.reqs = d_rq;
     na.models = d_md;
@@ -1946,6 +2138,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.n = n;
     a.mnR = kStaticMNR;
     a.mnA = kStaticMNA;
+    a.counts = d_cnt;
     a.items = d_it;
     a.reqs = d_rq;
     a.models = d_md;

@@ -552,21 +552,35 @@ template <typename real, int NA, int KA, typename Ctx>
 __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
                                                       const real (&Phi)[NA][24], Ctx& c, bool per_bead);
 
+template <typename real, int NR, int NA, int KR, int KA, int NET, int MBT, int FUSE>
+__device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const WorkItem it, unsigned char* smem_raw);
+
+// One work item per block (launch grids cover the item capacity; blocks past the
+// batch's item count exit): the block stages its model's tables, then one thread
+// per particle runs descriptor_item.
 template <typename real, int NR, int NA, int KR, int KA, int MB, int NET = 0, int MBT = 0, int FUSE = 0>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_descriptor(EvalArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if ((int)blockIdx.x >= a.counts->n_items) return;
+    const WorkItem it = a.items[blockIdx.x];
+    const ModelDesc<real>& md = a.models[a.reqs[it.req].model];
+    stage_params(md.params, reinterpret_cast<real*>(smem_raw), md.off.total);
+    descriptor_item<real, NR, NA, KR, KA, NET, MBT, FUSE>(a, it, smem_raw);
+}
+
+template <typename real, int NR, int NA, int KR, int KA, int NET, int MBT, int FUSE>
+__device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const WorkItem it, unsigned char* smem_raw)
 {
     // MBT = 1: the four-body q4_n (l = 2) and five-body q5_n = q_n1^2 follow the
     // three-body descriptors (both always; a model with one of them has zero weights
     // on the other)
     constexpr int ND = NR + NA * (4 + 2 * MBT);
     constexpr int KRP = (KR + 3) & ~3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
-    const WorkItem it = a.items[blockIdx.x];
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
-    stage_params(md.params, P, off.total);
     // NET = 1 evaluates the network warp-wide: a lane past the item's end follows
     // the item's last particle and writes nothing
     const bool live = NET == 0 || it.begin + (int)threadIdx.x < it.end;
@@ -853,7 +867,7 @@ __device__ __forceinline__ real warp_sum(real v)
 // (counted from the request's first, so a request sums alike alone or in a batch),
 // then a fixed tree combines the threads, so the result does not depend on timing.
 template <int BS>
-__device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& it, const ReqInfo& rq,
+__device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const WorkItem& it, const ReqInfo& rq,
                                               double* partial, unsigned int* counter, double* totals)
 {
     __shared__ double red[BS / 32][10];
@@ -869,7 +883,7 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], const WorkItem& i
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
-        partial[(size_t)blockIdx.x * 10 + threadIdx.x] = s;
+        partial[(size_t)item * 10 + threadIdx.x] = s;
     }
     __threadfence();
     __syncthreads();
@@ -1102,7 +1116,9 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
     // the neighbours' records and gradients need more)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
-    const WorkItem it = a.items[blockIdx.x];
+    const int w = blockIdx.x;  // one work item per block (see k_descriptor)
+    if (w >= a.counts->n_items) return;
+    const WorkItem it = a.items[w];
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
@@ -1126,7 +1142,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
         force_angular_k<real, NA, KA, 0, kNLM>(a, P, off, c);
         force_outputs(a, rq, i, c.F, c.W, tot);
     }
-    reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
+    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.counter, a.totals);
 }
 
 // ---- FP32 form: angular pairs in scatter form inside the descriptor kernel ------
@@ -1221,7 +1237,9 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
     constexpr int KRP = (KR + 3) & ~3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
-    const WorkItem it = a.items[blockIdx.x];
+    const int w = blockIdx.x;  // one work item per block (see k_descriptor)
+    if (w >= a.counts->n_items) return;
+    const WorkItem it = a.items[w];
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
@@ -1268,7 +1286,7 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
 #pragma unroll
         for (int k = 0; k < 9; ++k) tot[1 + k] = (double)a.wsum[(size_t)k * a.n + i] + (double)c.W[k];
     }
-    reduce_totals<kBlock>(tot, it, rq, a.partial, a.counter, a.totals);
+    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.counter, a.totals);
 }
 
 // ---- shape dispatch -----------------------------------------------------------
@@ -1356,10 +1374,10 @@ void launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_
 }
 
 template <typename real>
-cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
+cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int items_cap, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force)
 {
-    const int nb = n_items;
+    const int nb = items_cap;
     if constexpr (sizeof(real) == 4) {
         if (!a.accF || !a.wsum) return cudaErrorInvalidValue;  // the FP32 form scatters into a.accF
     }

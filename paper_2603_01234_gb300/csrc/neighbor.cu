@@ -14,94 +14,112 @@
 namespace nep {
 
 template <typename real>
-__global__ void __launch_bounds__(kBlock) k_bin(const WorkItem* __restrict__ items, const ReqInfo* __restrict__ reqs,
+__global__ void __launch_bounds__(kBlock) k_bin(const PlanCounts* __restrict__ pc, const WorkItem* __restrict__ items,
+                                                const ReqInfo* __restrict__ reqs,
                                                 const ModelDesc<real>* __restrict__ models,
                                                 const double* __restrict__ pos, const int* __restrict__ types,
                                                 int* __restrict__ cell_of, PosRec<real>* __restrict__ rec,
                                                 int* __restrict__ cell_count, int* __restrict__ err)
 {
-    const WorkItem it = items[blockIdx.x];
-    const int i = it.begin + threadIdx.x;
-    if (i >= it.end) return;
-    const ReqInfo& q = reqs[it.req];
-    const CellGrid& g = q.g;
-    const int local = i - q.begin;
-    int c3[3];
-    real xr[3];
+    const int n_items = pc->n_items;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+        const WorkItem it = items[w];
+        const int i = it.begin + threadIdx.x;
+        if (i >= it.end) continue;
+        const ReqInfo& q = reqs[it.req];
+        const CellGrid& g = q.g;
+        const int local = i - q.begin;
+        int c3[3];
+        real xr[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double x = pos[(size_t)3 * q.begin + (size_t)a * q.n + local];
-        if (!isfinite(x)) {
-            atomicOr(err, 1);
-            x = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[(size_t)3 * q.begin + (size_t)a * q.n + local];
+            if (!isfinite(x)) {
+                atomicOr(err, 1);
+                x = 0.0;
+            }
+            if (g.pbc[a]) x = wrap_periodic(x, g.box[a]);
+            const double cf = floor(x * g.inv_len[a]);
+            int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
+            c3[a] = c;
+            xr[a] = (real)(x - (double)c * g.len[a]);
         }
-        if (g.pbc[a]) x = wrap_periodic(x, g.box[a]);
-        const double cf = floor(x * g.inv_len[a]);
-        int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
-        c3[a] = c;
-        xr[a] = (real)(x - (double)c * g.len[a]);
+        int t = types[i];
+        if (t < 0 || t >= models[q.model].T) {
+            atomicOr(err, 2);
+            t = 0;
+        }
+        const int cell = q.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+        cell_of[i] = cell;
+        PosRec<real> r;
+        r.x = xr[0];
+        r.y = xr[1];
+        r.z = xr[2];
+        r.t = t;
+        rec[i] = r;
+        atomicAdd(&cell_count[cell], 1);
     }
-    int t = types[i];
-    if (t < 0 || t >= models[q.model].T) {
-        atomicOr(err, 2);
-        t = 0;
-    }
-    const int cell = q.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
-    cell_of[i] = cell;
-    PosRec<real> r;
-    r.x = xr[0];
-    r.y = xr[1];
-    r.z = xr[2];
-    r.t = t;
-    rec[i] = r;
-    atomicAdd(&cell_count[cell], 1);
 }
 
-// Block-local exclusive scan of kScanItems counts (4 per thread, 1024 threads).
-__global__ void __launch_bounds__(1024) k_scan_local(int ncell, const int* __restrict__ count,
-                                                     int* __restrict__ local, int* __restrict__ block_sum)
+// Block-local exclusive scan of kScanItems counts (4 per thread, 1024 threads),
+// blocks striding over the cells.  The counters it reads (cell counts and the
+// scatter's fill counters) are cleared here for the next build.
+__global__ void __launch_bounds__(1024) k_scan_local(const PlanCounts* __restrict__ pc, int* __restrict__ count,
+                                                     int* __restrict__ local, int* __restrict__ block_sum,
+                                                     int* __restrict__ fill)
 {
     __shared__ int warp_tot[32];
-    const int base = blockIdx.x * kScanItems + threadIdx.x * 4;
-    int v[4], s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = (base + k < ncell) ? count[base + k] : 0;
-        s += v[k];
-    }
+    const int ncell = pc->ncell;
+    const int nb = (ncell + kScanItems - 1) / kScanItems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = s;
+    for (int blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int base = blk * kScanItems + threadIdx.x * 4;
+        int v[4], s = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_tot[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = warp_tot[lane];
-        int wi = w;
+        for (int k = 0; k < 4; ++k) {
+            v[k] = 0;
+            if (base + k < ncell) {
+                v[k] = count[base + k];
+                count[base + k] = 0;
+                fill[base + k] = 0;
+            }
+            s += v[k];
+        }
+        int incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += y;
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
-        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
-        if (lane == 31) block_sum[blockIdx.x] = wi;
-    }
-    __syncthreads();
-    int run = warp_tot[warp] + incl - s;
+        if (lane == 31) warp_tot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_tot[lane];
+            int wi = w;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (base + k < ncell) local[base + k] = run;
-        run += v[k];
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+            if (lane == 31) block_sum[blk] = wi;
+        }
+        __syncthreads();
+        int run = warp_tot[warp] + incl - s;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < ncell) local[base + k] = run;
+            run += v[k];
+        }
+        __syncthreads();  // warp_tot is reused by the next block of cells
     }
 }
 
 // Exclusive scan of the block sums in place (one block; nb <= 4096).
-__global__ void __launch_bounds__(1024) k_scan_top(int nb, int* __restrict__ block_sum)
+__global__ void __launch_bounds__(1024) k_scan_top(const PlanCounts* __restrict__ pc, int* __restrict__ block_sum)
 {
     __shared__ int warp_tot[32];
+    const int nb = (pc->ncell + kScanItems - 1) / kScanItems;
     const int base = threadIdx.x * 4;
     int v[4], s = 0;
 #pragma unroll
@@ -139,74 +157,99 @@ __global__ void __launch_bounds__(1024) k_scan_top(int nb, int* __restrict__ blo
 
 // Counting-sort scatter (thread per particle, arbitrary order within a cell) and the
 // cell start offsets (thread per cell).
-__global__ void __launch_bounds__(kBlock) k_scatter(int n, int ncell, const int* __restrict__ cell_of,
+__global__ void __launch_bounds__(kBlock) k_scatter(const PlanCounts* __restrict__ pc, const int* __restrict__ cell_of,
                                                     const int* __restrict__ local, const int* __restrict__ block_off,
                                                     int* __restrict__ fill, int* __restrict__ perm_tmp,
                                                     int* __restrict__ cell_start)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) {
-        const int c = cell_of[t];
-        const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
-        perm_tmp[slot] = t;
+    const int n = pc->n, ncell = pc->ncell;
+    const int total = n > ncell + 1 ? n : ncell + 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        if (t < n) {
+            const int c = cell_of[t];
+            const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
+            perm_tmp[slot] = t;
+        }
+        if (t < ncell) cell_start[t] = local[t] + block_off[t / kScanItems];
+        if (t == ncell) cell_start[ncell] = n;
     }
-    if (t < ncell) cell_start[t] = local[t] + block_off[t / kScanItems];
-    if (t == ncell) cell_start[ncell] = n;
 }
 
 // Deterministic order within each cell (by caller index): thread per slot, rank =
 // number of the cell's members with a smaller caller index; gathers the records.
 template <typename real>
-__global__ void __launch_bounds__(kBlock) k_cell_rank(int n, const int* __restrict__ cell_of,
+__global__ void __launch_bounds__(kBlock) k_cell_rank(const PlanCounts* __restrict__ pc,
+                                                      const int* __restrict__ cell_of,
                                                       const int* __restrict__ cell_start,
                                                       const int* __restrict__ perm_tmp, int* __restrict__ perm,
                                                       int* __restrict__ cell_s, const PosRec<real>* __restrict__ rec,
                                                       PosRec<real>* __restrict__ rec_s)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int v = perm_tmp[k];
-    const int c = cell_of[v];
-    const int b = cell_start[c], e = cell_start[c + 1];
-    int rank = 0;
-    for (int q = b; q < e; ++q) rank += perm_tmp[q] < v;
-    const int dst = b + rank;
-    perm[dst] = v;
-    cell_s[dst] = c;
-    rec_s[dst] = rec[v];
+    const int n = pc->n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int v = perm_tmp[k];
+        const int c = cell_of[v];
+        const int b = cell_start[c], e = cell_start[c + 1];
+        int rank = 0;
+        for (int q = b; q < e; ++q) rank += perm_tmp[q] < v;
+        const int dst = b + rank;
+        perm[dst] = v;
+        cell_s[dst] = c;
+        rec_s[dst] = rec[v];
+    }
 }
 
 template <typename real>
-cudaError_t launch_cell_build(int n, int n_items, int ncell_total, const WorkItem* items, const ReqInfo* reqs,
-                              const ModelDesc<real>* models, const double* pos, const int* types, int* cell_of,
-                              PosRec<real>* rec_user, int* cell_count, int* cell_start_local, int* block_off,
-                              int* cell_fill, int* perm_tmp, int* perm, int* cell_start, int* cell_s,
-                              PosRec<real>* rec_sorted, int* err, cudaStream_t st)
+cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap, int ncell_cap, bool zero_counts,
+                              const WorkItem* items, const ReqInfo* reqs, const ModelDesc<real>* models,
+                              const double* pos, const int* types, int* cell_of, PosRec<real>* rec_user,
+                              int* cell_count, int* cell_start_local, int* block_off, int* cell_fill, int* perm_tmp,
+                              int* perm, int* cell_start, int* cell_s, PosRec<real>* rec_sorted, int* err,
+                              cudaStream_t st)
 {
-    const int nb_scan = (ncell_total + kScanItems - 1) / kScanItems;
-    if (nb_scan > kScanItems) return cudaErrorInvalidValue;
+    const int nb_scan = (ncell_cap + kScanItems - 1) / kScanItems;
+    if (nb_scan > kScanItems || n_cap < 1 || items_cap < 1) return cudaErrorInvalidValue;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell_total, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell_total, st)) != cudaSuccess) return e;
-    k_bin<real><<<n_items, kBlock, 0, st>>>(items, reqs, models, pos, types, cell_of, rec_user, cell_count, err);
-    k_scan_local<<<nb_scan, 1024, 0, st>>>(ncell_total, cell_count, cell_start_local, block_off);
-    k_scan_top<<<1, 1024, 0, st>>>(nb_scan, block_off);
-    const int nt = (n > ncell_total + 1 ? n : ncell_total + 1);
-    k_scatter<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, ncell_total, cell_of, cell_start_local, block_off,
-                                                              cell_fill, perm_tmp, cell_start);
-    k_cell_rank<real><<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, cell_of, cell_start, perm_tmp, perm, cell_s,
-                                                                    rec_user, rec_sorted);
+    if (zero_counts) {
+        if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
+    }
+    k_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, pos, types, cell_of, rec_user, cell_count,
+                                              err);
+    k_scan_local<<<nb_scan, 1024, 0, st>>>(counts, cell_count, cell_start_local, block_off, cell_fill);
+    k_scan_top<<<1, 1024, 0, st>>>(counts, block_off);
+    const int nt = (n_cap > ncell_cap + 1 ? n_cap : ncell_cap + 1);
+    k_scatter<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(counts, cell_of, cell_start_local, block_off, cell_fill,
+                                                              perm_tmp, cell_start);
+    k_cell_rank<real><<<(n_cap + kBlock - 1) / kBlock, kBlock, 0, st>>>(counts, cell_of, cell_start, perm_tmp, perm,
+                                                                        cell_s, rec_user, rec_sorted);
     return cudaGetLastError();
 }
 
 // One thread per sorted particle i: scan the cells at offsets [-S, S]^3 from i's
 // cell in its request's grid and keep every (j, offset) with r^2 < r_c^2(t_i, t_j).
+// A warp's particles are consecutive in cell order (about two cells of a water
+// box), so in SIMT the warp tests the union of their neighbourhoods whatever the
+// per-thread scheme; the candidate body is therefore kept branch-free, with the
+// tests predicating the stores (masks with store loops afterwards, and skipping
+// cells out of reach, were measured slower: both make the lanes diverge).
+template <typename real>
+__device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, const WorkItem it, real* cut);
+
 template <typename real>
 __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* cut = reinterpret_cast<real*>(smem_raw);  // rcR2[T*T], rcA2[T*T]
-    const WorkItem it = a.items[blockIdx.x];
+    // one work item per block: launch grids cover the item capacity, blocks past the
+    // batch's item count exit
+    if ((int)blockIdx.x >= a.counts->n_items) return;
+    neighbors_item(a, a.items[blockIdx.x], cut);
+}
+
+template <typename real>
+__device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, const WorkItem it, real* cut)
+{
     const ReqInfo& q = a.reqs[it.req];
     const ModelDesc<real> md = a.models[q.model];
     const int T = md.T, TT = T * T;
@@ -289,13 +332,13 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
         a.cntR[i] = nr;
         a.cntA[i] = na;
         if (a.accF) {  // i's fixed-point lines start the evaluation at zero
-            ulonglong2* z = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
-            z[0] = z[1] = make_ulonglong2(0ull, 0ull);
+            ulonglong2* zl = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
+            zl[0] = zl[1] = make_ulonglong2(0ull, 0ull);
         }
         if (a.accW) {
-            ulonglong2* z = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
+            ulonglong2* zl = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) z[k] = make_ulonglong2(0ull, 0ull);
+            for (int k = 0; k < 6; ++k) zl[k] = make_ulonglong2(0ull, 0ull);
         }
     }
     // warp maxima, then one atomic per warp
@@ -311,20 +354,20 @@ __global__ void __launch_bounds__(kBlock) k_neighbors(NeighborArgs<real> a)
 }
 
 template <typename real>
-cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st)
+cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st)
 {
     // the kernel indexes the slot-major lists with 32-bit slot * n + i
     if ((unsigned long long)(a.mnR > a.mnA ? a.mnR : a.mnA) * (unsigned long long)a.n > (1ull << 32))
         return cudaErrorInvalidValue;
-    k_neighbors<real><<<n_items, kBlock, smem, st>>>(a);
+    k_neighbors<real><<<items_cap, kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 #define NEP_INSTANTIATE(real)                                                                                   \
-    template cudaError_t launch_cell_build<real>(int, int, int, const WorkItem*, const ReqInfo*,                \
-                                                 const ModelDesc<real>*, const double*, const int*, int*,         \
-                                                 PosRec<real>*, int*, int*, int*, int*, int*, int*, int*, int*,   \
-                                                 PosRec<real>*, int*, cudaStream_t);                              \
+    template cudaError_t launch_cell_build<real>(const PlanCounts*, int, int, int, bool, const WorkItem*,      \
+                                                 const ReqInfo*, const ModelDesc<real>*, const double*,           \
+                                                 const int*, int*, PosRec<real>*, int*, int*, int*, int*, int*,   \
+                                                 int*, int*, int*, PosRec<real>*, int*, cudaStream_t);            \
     template cudaError_t launch_neighbors<real>(const NeighborArgs<real>&, int, size_t, cudaStream_t);
 NEP_INSTANTIATE(float)
 NEP_INSTANTIATE(double)

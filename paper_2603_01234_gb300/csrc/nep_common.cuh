@@ -147,9 +147,18 @@ struct WorkItem {
     int req, begin, end;
 };
 
+// Sizes of the batch in progress, in device memory ahead of its tables.  The
+// kernels take their loop bounds from here and loop over work items with a grid
+// stride, so launch shapes depend only on capacities: one captured CUDA graph then
+// serves every batch that fits them.
+struct PlanCounts {
+    int n, n_items, ncell, n_req;
+};
+
 template <typename real>
 struct NeighborArgs {
-    int n, mnR, mnA;
+    int n, mnR, mnA;            // n: the list stride (particle capacity)
+    const PlanCounts* counts;
     const WorkItem* items;
     const ReqInfo* reqs;
     const ModelDesc<real>* models;
@@ -167,7 +176,8 @@ struct NeighborArgs {
 
 template <typename real>
 struct EvalArgs {
-    int n, mnR, mnA;
+    int n, mnR, mnA;            // n: the list / array stride (particle capacity)
+    const PlanCounts* counts;
     const WorkItem* items;
     const ReqInfo* reqs;
     const ModelDesc<real>* models;
@@ -191,28 +201,33 @@ struct EvalArgs {
     unsigned long long* accW;   // FP32 form with per-particle virials: [n][12] fixed-point W[9] (2^-32 eV),
                                 // same rules; used only when virial is non-null
     float* wsum;                // FP32 form: [9][n] each thread's angular virial sum (for the totals)
-    double* partial;            // [items][10] per-block (E, W[9])
+    double* partial;            // [items][10] per work item (E, W[9])
     unsigned int* counter;      // [requests] last-block counters (self-resetting)
     double* totals;             // [requests][10]: E, W[9]
 };
 
 // ---- host-side launchers (defined in the .cu files) ----
+// Grids are sized by the capacities (n_cap particles, items_cap work items,
+// ncell_cap cells); the sizes in effect come from *counts.  The cell counters must
+// be zero on entry (the scan clears them for the next build); zero_counts clears
+// them first for callers whose buffers may hold anything.
 template <typename real>
-cudaError_t launch_cell_build(int n, int n_items, int ncell_total, const WorkItem* items, const ReqInfo* reqs,
-                              const ModelDesc<real>* models, const double* pos, const int* types, int* cell_of,
-                              PosRec<real>* rec_user, int* cell_count, int* cell_start_local, int* block_off,
-                              int* cell_fill, int* perm_tmp, int* perm, int* cell_start, int* cell_s,
-                              PosRec<real>* rec_sorted, int* err, cudaStream_t st);
+cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap, int ncell_cap, bool zero_counts,
+                              const WorkItem* items, const ReqInfo* reqs, const ModelDesc<real>* models,
+                              const double* pos, const int* types, int* cell_of, PosRec<real>* rec_user,
+                              int* cell_count, int* cell_start_local, int* block_off, int* cell_fill, int* perm_tmp,
+                              int* perm, int* cell_start, int* cell_s, PosRec<real>* rec_sorted, int* err,
+                              cudaStream_t st);
 
 template <typename real>
-cudaError_t launch_neighbors(const NeighborArgs<real>& a, int n_items, size_t smem, cudaStream_t st);
+cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st);
 
 // Shape-dispatched evaluation; returns cudaErrorInvalidValue for an uncompiled shape.
 // mb_desc / mb_force: resident blocks per SM of the FP32 kernel variants (2 or 3; the
 // force kernel also 4).  The FP64 form has one effective variant of each.
 // The FP32 form needs a.acc (the scatter accumulators); the FP64 form ignores it.
 template <typename real>
-cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int n_items, size_t smem_desc,
+cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int items_cap, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr, int mb_desc = 3,
                             int mb_force = 2);
 

@@ -112,3 +112,30 @@ def test_batch_rejects_mismatched_models(nep_lib):
     assert e.value.code == binding.NEP_ERR_ARG
     a.close()
     b.close()
+
+
+def test_batches_of_one_size_class_share_a_graph(nep_lib):
+    """Consecutive batches whose sizes fall in one size class replay one captured
+    graph (the kernels read the batch's sizes from the device); every request of
+    every batch still equals its evaluation alone, bitwise.  The batches differ in
+    their number of requests, so the tables' offsets would differ if they were laid
+    out by count rather than by capacity."""
+    models = [water_model(), monolayer_model()]
+    batch_handles = [binding.Model(p, "fp32") for p in models]
+    alone_handles = [binding.Model(p, "fp32") for p in models]
+    rng = np.random.default_rng(71)
+    for b in range(6):
+        k = int(rng.integers(3, 9))
+        reqs = []
+        for r in range(k):
+            n = int(rng.integers(80, 160))
+            reqs.append((0, inputs.water_box(n, seed=1000 * b + r)) if r % 2 == 0 else
+                        (1, inputs.monolayer(3, 2, seed=1000 * b + r)))
+        got = run_batch([h.h for h in batch_handles], reqs)
+        for (mi, s), g in zip(reqs, got):
+            alone = alone_handles[mi].compute(s)
+            assert g["energy"] == alone["energy"]
+            np.testing.assert_array_equal(g["force"], alone["force"])
+            np.testing.assert_array_equal(g["virial"], alone["virial"])
+    for h in batch_handles + alone_handles:
+        h.close()
