@@ -169,6 +169,12 @@ int nep_compute(nep_model* m, int n, const int32_t* types, const double* pos, co
  *   virial             blocks [9][n_r] at virial + 9 o_r, or NULL
  * Results equal those of one nep_compute per request.  Synchronous like
  * nep_compute; at most 2^23 particles in total.
+ * The call synchronises once: the whole pipeline, the output copies and the status
+ * words are enqueued together, and a neighbour list that outgrew its capacity is
+ * grown and the batch run again (the capacity then stays).  Capacities are
+ * rounded up to size classes (at most 1/8 more than the batch) and the pipeline is
+ * captured as a CUDA graph cached on models[0] by its launch shapes and pointers,
+ * so later batches of a similar size (and the same buffers) replay it.
  */
 int nep_compute_batch(nep_model* const* models, int n_models, int n_req, const int32_t* req_n,
                       const int32_t* req_model, const double* req_box, const int32_t* req_pbc,
@@ -373,6 +379,29 @@ int nep_get_capacity(nep_model* m, int* radial, int* angular);
 /* Set the neighbour-list capacities (entries per particle, >= 1).  A list holds
  * capacity x n entries, at most 2^32 (larger lists give NEP_ERR_ARG when built). */
 int nep_set_capacity(nep_model* m, int radial, int angular);
+
+/*
+ * Device workspace bytes that one request adds to a batch of nep_compute_batch on
+ * models[0]'s workspace (the same models[n_models] as the batch; the request uses
+ * models[model], n particles, box and pbc as in the batch): particle arrays
+ * (strided by the batch's largest type count), neighbour lists at models[0]'s
+ * current capacities (or, before it has evaluated anything, the first-call
+ * estimate from this request's density), cell arrays, work items and the request's
+ * own entries, plus the staging of host-memory calls.  A batch allocates at most
+ * 9/8 of the sum over its requests (size classes).  For admission of requests by
+ * memory; computes on the host only.
+ */
+int nep_request_workspace(nep_model* const* models, int n_models, int model, int n, const double box[3],
+                          const int32_t pbc[3], size_t* bytes);
+
+/* Device bytes m's workspace holds now (every buffer the library allocated for
+ * evaluations and MD on m; the model parameters are not counted). */
+int nep_workspace_bytes(nep_model* m, size_t* bytes);
+
+/* Page-locked host memory (cudaMallocHost) for request and result buffers: copies
+ * between it and the device run at full link speed.  Free with nep_host_free. */
+int nep_host_alloc(size_t bytes, void** out);
+int nep_host_free(void* p);
 
 #ifdef __cplusplus
 }

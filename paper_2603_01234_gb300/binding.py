@@ -36,7 +36,8 @@ EXPORTED = ["nep_version", "nep_error_string", "nep_last_error", "nep_create", "
             "nep_destroy", "nep_compute", "nep_md_step", "nep_scale_positions", "nep_neighbors",
             "nep_get_capacity", "nep_set_capacity", "nep_sync", "nep_set_timing", "nep_get_timing",
             "nep_compute_static", "nep_compute_batch", "nep_md_step_nvt", "nep_cg_map",
-            "nep_virial_correction", "nep_autotune", "nep_set_tuning", "nep_get_tuning", "nep_md_step_hnemd"]
+            "nep_virial_correction", "nep_autotune", "nep_set_tuning", "nep_get_tuning", "nep_md_step_hnemd",
+            "nep_request_workspace", "nep_workspace_bytes", "nep_host_alloc", "nep_host_free"]
 
 _lib = None
 
@@ -113,6 +114,14 @@ def load(build_if_missing: bool = False):
     lib.nep_set_tuning.restype = i
     lib.nep_get_tuning.argtypes = [p, C.POINTER(i), C.POINTER(i)]
     lib.nep_get_tuning.restype = i
+    lib.nep_request_workspace.argtypes = [p, i, i, i, p, p, C.POINTER(C.c_size_t)]
+    lib.nep_request_workspace.restype = i
+    lib.nep_workspace_bytes.argtypes = [p, C.POINTER(C.c_size_t)]
+    lib.nep_workspace_bytes.restype = i
+    lib.nep_host_alloc.argtypes = [C.c_size_t, C.POINTER(p)]
+    lib.nep_host_alloc.restype = i
+    lib.nep_host_free.argtypes = [p]
+    lib.nep_host_free.restype = i
     _lib = lib
     return lib
 
@@ -361,6 +370,50 @@ def nep_get_tuning(h):
     a, b = C.c_int(), C.c_int()
     _check(load().nep_get_tuning(h, C.byref(a), C.byref(b)), "nep_get_tuning")
     return a.value, b.value
+
+
+def nep_request_workspace(handles, model, n, box, pbc):
+    """Device bytes one request (of handles[model], n particles in box) adds to a
+    batch evaluated on handles[0]'s workspace."""
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    out = C.c_size_t()
+    _check(load().nep_request_workspace(C.cast(arr, C.c_void_p), len(handles), int(model), int(n),
+                                        _ptr(_host(box, np.float64)), _ptr(_host(pbc, np.int32)), C.byref(out)),
+           "nep_request_workspace")
+    return out.value
+
+
+def nep_workspace_bytes(h):
+    out = C.c_size_t()
+    _check(load().nep_workspace_bytes(h, C.byref(out)), "nep_workspace_bytes")
+    return out.value
+
+
+class PinnedBuffer:
+    """Page-locked host memory from nep_host_alloc, viewed as numpy arrays."""
+
+    def __init__(self, nbytes):
+        self.nbytes = int(nbytes)
+        ptr = C.c_void_p()
+        _check(load().nep_host_alloc(self.nbytes, C.byref(ptr)), "nep_host_alloc")
+        self.ptr = ptr.value
+        self._raw = (C.c_ubyte * self.nbytes).from_address(self.ptr)
+
+    def view(self, offset, count, dtype):
+        dtype = np.dtype(dtype)
+        return np.frombuffer(self._raw, dtype=dtype, count=count, offset=offset)
+
+    def close(self):
+        if self.ptr:
+            self._raw = None
+            load().nep_host_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def nep_sync(h):

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -144,7 +145,7 @@ struct GraphCache {
         key.clear();
     }
 };
-constexpr size_t kEvalGraphs = 8;  // evaluation graphs kept per handle
+constexpr size_t kEvalGraphs = 16;  // evaluation graphs kept per handle
 
 
 // Host copy of one batch layout and its device tables (counts, requests, work
@@ -190,8 +191,8 @@ void set_caps(Plan& p, bool classes)
     }
     p.n_cap = size_class(p.n, kBlock);
     p.items_cap = size_class(n_items, 8);
-    p.ncell_cap = size_class(p.ncell, 64);
-    p.req_cap = size_class((int)p.reqs.size(), 8);
+    p.ncell_cap = (p.ncell + kScanItems - 1) / kScanItems * kScanItems;  // whole scan tiles
+    p.req_cap = (int)p.reqs.size();
 }
 
 }  // namespace
@@ -240,6 +241,7 @@ struct nep_model {
     Plan plan;
     GraphCache graph;                    // MD step chunk
     std::vector<GraphCache> eval_graphs;  // nep_compute / nep_compute_batch evaluations
+    std::vector<size_t> eval_seen;        // hashes of evaluation shapes seen once (captured on the next)
     StageTimer timer;
 };
 
@@ -356,12 +358,13 @@ int upload_plan(nep_model* m, Plan& p, bool force_upload = false)
     put(p.items.data(), sizeof(WorkItem) * p.items.size());
     put(p.models.data(), p.models.size());
     if (!force_upload && key == p.key && p.dev.p) return NEP_OK;
-    // the regions are laid out by capacity, so their offsets (which the kernels'
-    // arguments carry, and a captured graph keeps) depend only on the capacities
-    p.off_reqs = align16(sizeof(PlanCounts));
-    p.off_items = p.off_reqs + align16(sizeof(ReqInfo) * std::max<size_t>(p.req_cap, p.reqs.size()));
-    p.off_models = p.off_items + align16(sizeof(WorkItem) * std::max<size_t>(p.items_cap, p.items.size()));
-    const size_t bytes = p.off_models + p.models.size();
+    // [counts | models | items | requests]: the items region is laid out by
+    // capacity, so the offsets (which the kernels' arguments carry, and a captured
+    // graph keeps) depend only on the model count and the item capacity
+    p.off_models = align16(sizeof(PlanCounts));
+    p.off_items = p.off_models + align16(p.models.size());
+    p.off_reqs = p.off_items + align16(sizeof(WorkItem) * std::max<size_t>(p.items_cap, p.items.size()));
+    const size_t bytes = p.off_reqs + sizeof(ReqInfo) * p.reqs.size();
     NEP_TRY(p.dev.ensure(bytes));
     if (m->plan_pending) NEP_CUDA(cudaEventSynchronize(m->ev_plan));  // staging free again
     m->plan_pending = false;
@@ -672,6 +675,15 @@ int eval_launch(nep_model* m, const Plan& p, const int* types_d, const double* p
             NEP_CUDA(cudaGraphLaunch(m->eval_graphs[k].exec, m->cur));
             return NEP_OK;
         }
+    // a shape seen for the first time runs eagerly (capturing and instantiating a
+    // graph costs more than launching its nodes once); the second time it is
+    // captured, and replayed from then on
+    const size_t h = std::hash<std::string>()(std::string(key.begin(), key.end()));
+    if (std::find(m->eval_seen.begin(), m->eval_seen.end(), h) == m->eval_seen.end()) {
+        m->eval_seen.push_back(h);
+        if (m->eval_seen.size() > 4 * kEvalGraphs) m->eval_seen.erase(m->eval_seen.begin());
+        return eval_pipeline<real>(m, p, types_d, pos_d, force, virial, site, totals);
+    }
     NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
     const int rc = eval_pipeline<real>(m, p, types_d, pos_d, force, virial, site, totals);
     cudaGraph_t graph = nullptr;
@@ -1944,6 +1956,82 @@ int nep_get_capacity(nep_model* m, int* radial, int* angular)
     if (!m) return fail(NEP_ERR_ARG, "null model");
     if (radial) *radial = m->mnR;
     if (angular) *angular = m->mnA;
+    return NEP_OK;
+}
+
+// Device bytes one request adds to a batch on models[0]'s workspace: the sizes
+// ensure_plan_workspace, ensure_lists and the host-call staging of batch_impl
+// allocate, per particle, per cell, per work item and per request, with the
+// batch's largest type count (the gradient array's stride) and models[0]'s list
+// capacities.
+int nep_request_workspace(nep_model* const* models, int n_models, int model, int n, const double box[3],
+                          const int32_t pbc[3], size_t* bytes)
+{
+    if (!models || n_models < 1 || model < 0 || model >= n_models || n < 1 || !box || !pbc || !bytes)
+        return fail(NEP_ERR_ARG, "bad argument");
+    const nep_model* m = models[0];
+    int Tmax = 1;
+    for (int k = 0; k < n_models; ++k) {
+        if (!models[k]) return fail(NEP_ERR_ARG, "null model");
+        Tmax = std::max(Tmax, models[k]->T);
+    }
+    CellGrid g;
+    NEP_TRY(make_grid(models[model], models[model]->rc_max, box, pbc, g));
+    int mnR = m->mnR, mnA = m->mnA;
+    if (mnR <= 0 || mnA <= 0) {  // not sized yet: the first-call estimate from the density
+        const double rho = n / (box[0] * box[1] * box[2]);
+        double rR = 0, rA = 0;
+        for (double v : m->rcR) rR = std::max(rR, v);
+        for (double v : m->rcA) rA = std::max(rA, v);
+        auto est = [&](double rc) { return (std::min((int)(4.18879 * rc * rc * rc * rho * 1.3 + 16), 4096) + 7) & ~7; };
+        if (mnR <= 0) mnR = est(rR);
+        if (mnA <= 0) mnA = est(rA);
+    }
+    const size_t rs = m->real_size;
+    // cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, U, e, force_tmp, partial2
+    size_t per_particle = 4 + 4 * rs + 4 + 4 + 4 * rs + 4 + 4 + 4 + rs + rs * Tmax * m->KRP + 24 + 1;
+    if (m->precision == NEP_FP64) per_particle += rs * 24 * phi_pad(m->nA);
+    else per_particle += acc_bytes(1);            // fixed-point lines, thread virial sums
+    per_particle += 4 * (size_t)(mnR + mnA);      // neighbour lists
+    per_particle += 4 + 24 + 24 + 72 + 8;          // host-call staging: types, positions, F, W, U
+    const size_t per_cell = 16;                    // count, local prefix, fill, start
+    const size_t items = ((size_t)n + kBlock - 1) / kBlock;
+    const size_t per_item = 10 * sizeof(double) + sizeof(WorkItem);
+    const size_t per_req = sizeof(ReqInfo) + 10 * sizeof(double) + sizeof(unsigned int);
+    *bytes = per_particle * n + per_cell * g.ncell + per_item * items + per_req;
+    return NEP_OK;
+}
+
+int nep_workspace_bytes(nep_model* m, size_t* bytes)
+{
+    if (!m || !bytes) return fail(NEP_ERR_ARG, "bad argument");
+    const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
+                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
+                         &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters,
+                         &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d,
+                         &m->force_d, &m->virial_d, &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev,
+                         &m->noise_d, &m->bussi, &m->md_virial, &m->md_site, &m->heat, &m->heat_rows, &m->acc};
+    size_t t = 0;
+    for (const Buf* b : bufs) t += b->p ? b->cap : 0;
+    *bytes = t;
+    return NEP_OK;
+}
+
+int nep_host_alloc(size_t bytes, void** out)
+{
+    if (!out) return fail(NEP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (bytes == 0) return fail(NEP_ERR_ARG, "zero bytes");
+    cudaError_t e = cudaMallocHost(out, bytes);
+    if (e != cudaSuccess) return fail(NEP_ERR_OOM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    return NEP_OK;
+}
+
+int nep_host_free(void* p)
+{
+    if (!p) return NEP_OK;
+    cudaError_t e = cudaFreeHost(p);
+    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("cudaFreeHost: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
 

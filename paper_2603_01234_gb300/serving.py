@@ -3,12 +3,18 @@
 Requests (a model index and a configuration) arrive over time.  `lanes` worker
 threads each own a set of model handles -- and therefore a device workspace -- and
 repeatedly admit the requests that have arrived, in arrival order, until the
-batch's particle budget is reached, then evaluate them with one nep_compute_batch
-call.  The call releases the GIL, so while one lane's batch runs on the GPU another
-lane admits the requests that arrived meanwhile and launches its own batch: work of
-different batches overlaps on the device, and a request never waits for a batch
-that is already running.  Admission is by memory: the particle budget per batch is
-derived from a byte budget per lane and the workspace bytes a particle needs.
+lane's memory budget is reached, then evaluate them with one nep_compute_batch
+call.  The call releases the GIL, so while one lane's batch runs on the GPU the
+other lanes admit the requests that arrived meanwhile and launch their own
+batches: work of different batches overlaps on the device, and a request never
+waits for a batch that is already running.
+
+Admission is by memory: every request carries the device workspace bytes the
+library reports for it (nep_request_workspace: particle arrays, neighbour lists at
+the handle's capacities, cells, work items), and a lane admits requests while their
+sum stays within its budget (less the 1/8 by which a batch's size classes may round
+up).  Each lane packs its batches into page-locked host buffers, so the copies to
+and from the device run at link speed.
 
 With lanes=1 and max_requests=1 the same server evaluates one request per launch
 sequence (the plain, unbatched form).
@@ -24,13 +30,8 @@ import numpy as np
 
 from . import binding
 
-
-# Device workspace bytes per particle of a batch (FP32 form): cell-relative records,
-# neighbour lists at their usual capacity, radial and angular gradients, outputs.
-def bytes_per_particle(params, list_capacity=160):
-    rs = 4
-    return (2 * 16 + 6 * 4 + 4 * list_capacity + rs * (1 + params.n_types * 8 + 24 * params.n_desc_angular)
-            + 8 * (1 + 3 + 9) + 8 * 4)
+# a batch's capacities round up to size classes: at most 9/8 of the sum over requests
+CLASS_MARGIN = 9.0 / 8.0
 
 
 @dataclass
@@ -42,6 +43,7 @@ class Request:
     done: float = 0.0
     result: dict | None = None
     batch_size: int = 0
+    ws: int = 0  # device workspace bytes this request adds to a batch
 
 
 @dataclass
@@ -63,17 +65,59 @@ class ServeStats:
         return float(np.percentile(self.latencies_s, q))
 
 
+class Staging:
+    """One lane's host buffers for a batch (inputs and outputs), grown as needed:
+    page-locked (nep_host_alloc) or, with pinned=False, ordinary numpy memory."""
+
+    # bytes per particle: types int32, positions 3 f64, forces 3 f64, virials 9 f64
+    _LAYOUT = (("types", 4, 1, np.int32), ("pos", 8, 3, np.float64), ("force", 8, 3, np.float64),
+               ("virial", 8, 9, np.float64))
+
+    def __init__(self, pinned=True):
+        self.pinned = pinned
+        self.n_cap = 0
+        self.k_cap = 0
+        self.buf = None
+        self.arrays = {}
+
+    def ensure(self, n, k):
+        if n <= self.n_cap and k <= self.k_cap:
+            return self.arrays
+        self.close()
+        self.n_cap = max(n, int(self.n_cap * 1.25))
+        self.k_cap = max(k, int(self.k_cap * 1.25))
+        sizes = [(name, w * self.n_cap, dt) for name, _, w, dt in self._LAYOUT]
+        sizes += [("energy", self.k_cap, np.float64), ("virial_total", 9 * self.k_cap, np.float64)]
+        if self.pinned:
+            total = sum(((c * np.dtype(dt).itemsize + 255) // 256) * 256 for _, c, dt in sizes)
+            self.buf = binding.PinnedBuffer(total)
+            off = 0
+            for name, c, dt in sizes:
+                self.arrays[name] = self.buf.view(off, c, dt)
+                off += ((c * np.dtype(dt).itemsize + 255) // 256) * 256
+        else:
+            self.arrays = {name: np.zeros(c, dt) for name, c, dt in sizes}
+        return self.arrays
+
+    def close(self):
+        self.arrays = {}
+        if self.buf is not None:
+            self.buf.close()
+            self.buf = None
+
+
 class Server:
     def __init__(self, params_list, precision="fp32", lanes=2, lane_bytes=2 << 30, max_requests=4096, device=0,
-                 keep_results=True):
+                 keep_results=True, pinned=True):
         self.params_list = params_list
         self.lanes = []
         for _ in range(lanes):
             self.lanes.append([binding.Model(p, precision, device) for p in params_list])
-        bpp = max(bytes_per_particle(p) for p in params_list)
-        self.max_particles = max(1, int(lane_bytes // bpp))
+        # admission budget: the lane's bytes less the size classes' rounding
+        self.max_bytes = max(1, int(lane_bytes / CLASS_MARGIN))
         self.max_requests = max_requests
         self.keep_results = keep_results
+        self.pinned = pinned
         self._cv = threading.Condition()
         self._pending = deque()
         self._closed = False
@@ -86,39 +130,59 @@ class Server:
                 m.close()
         self.lanes = []
 
+    def workspace_bytes(self, r):
+        """Device workspace the request adds to a batch, as the library reports it
+        for the lane workspace (models[0] of a lane) that would evaluate it."""
+        return binding.nep_request_workspace([m.h for m in self.lanes[0]], r.model, r.system.n, r.system.box,
+                                             r.system.pbc)
+
     # -- admission --------------------------------------------------------------
     def _admit(self):
-        """Take arrived requests in order until the particle or request budget."""
-        batch, beads = [], 0
+        """Take arrived requests in order until the memory or request budget; a
+        request larger than the whole budget goes alone."""
+        batch, used = [], 0
         while self._pending and len(batch) < self.max_requests:
             r = self._pending[0]
-            if batch and beads + r.system.n > self.max_particles:
+            if batch and used + r.ws > self.max_bytes:
                 break
             batch.append(self._pending.popleft())
-            beads += r.system.n
+            used += r.ws
         return batch
 
     def _lane(self, handles):
         hs = [m.h for m in handles]
-        while True:
-            with self._cv:
-                while not self._pending and not self._closed:
-                    self._cv.wait()
-                if not self._pending and self._closed:
-                    return
-                batch = self._admit()
-            self._run_batch(hs, batch)
+        staging = Staging(self.pinned)
+        try:
+            while True:
+                with self._cv:
+                    while not self._pending and not self._closed:
+                        self._cv.wait()
+                    if not self._pending and self._closed:
+                        return
+                    batch = self._admit()
+                self._run_batch(hs, batch, staging)
+        finally:
+            staging.close()
 
-    def _run_batch(self, hs, batch):
-        systems = [r.system for r in batch]
-        req_n, req_box, req_pbc, types, pos = binding.pack_requests(systems)
-        n = int(req_n.sum())
+    def _run_batch(self, hs, batch, staging):
         k = len(batch)
-        e = np.zeros(k)
-        wt = np.zeros((k, 9))
-        F = np.zeros(3 * n)
-        W = np.zeros(9 * n) if self.keep_results else None
-        binding.nep_compute_batch(hs, req_n, [r.model for r in batch], req_box, req_pbc, types, pos, e, wt, None, F, W)
+        req_n = np.array([r.system.n for r in batch], np.int32)
+        n = int(req_n.sum())
+        req_box = np.array([r.system.box for r in batch], np.float64)
+        req_pbc = np.array([r.system.pbc for r in batch], np.int32)
+        a = staging.ensure(n, k)
+        types, pos = a["types"][:n], a["pos"][:3 * n]
+        o = 0
+        for r in batch:  # pack straight into the staging buffers
+            nr = r.system.n
+            types[o:o + nr] = r.system.types
+            pos[3 * o:3 * (o + nr)] = np.asarray(r.system.pos, np.float64).reshape(-1)
+            o += nr
+        e, wt = a["energy"][:k], a["virial_total"][:9 * k].reshape(k, 9)
+        F = a["force"][:3 * n]
+        W = a["virial"][:9 * n] if self.keep_results else None
+        binding.nep_compute_batch(hs, req_n, [r.model for r in batch], req_box, req_pbc, types, pos, e, wt, None, F,
+                                  W)
         t = time.perf_counter()
         if self.keep_results:
             Fs = binding.unpack_blocks(F, req_n, 3)
@@ -127,7 +191,8 @@ class Server:
             r.done = t
             r.batch_size = k
             if self.keep_results:
-                r.result = {"energy": e[q], "virial_total": wt[q], "force": Fs[q], "virial": Ws[q]}
+                r.result = {"energy": float(e[q]), "virial_total": wt[q].copy(), "force": Fs[q].copy(),
+                            "virial": Ws[q].copy()}
         with self._cv:
             self.batches += 1
             self.batch_requests += k
@@ -137,6 +202,9 @@ class Server:
         """Release request k at arrival_times[k] seconds after the start (sorted),
         serve all of them, return ServeStats."""
         reqs = list(requests)
+        for r in reqs:
+            if not r.ws:
+                r.ws = self.workspace_bytes(r)
         self._closed = False
         self.batches = self.batch_requests = 0
         threads = [threading.Thread(target=self._lane, args=(lane,), daemon=True) for lane in self.lanes]

@@ -1,7 +1,8 @@
 """Host logic of the continuous-batching server (paper_2603_01234_gb300/serving.py)
-without a GPU: admission order and budgets, and the threaded serve loop with the
-batched evaluation replaced by a host stub that writes per-request values, so that
-packing, unpacking and hand-back of results to their requests are checked."""
+without a GPU: admission order and budgets (by each request's workspace bytes), and
+the threaded serve loop with the batched evaluation and the workspace query replaced
+by host stubs that write per-request values, so that packing into the lane's
+staging buffers, unpacking and hand-back of results to their requests are checked."""
 import threading
 
 import numpy as np
@@ -16,13 +17,13 @@ def make_requests(sizes, seed=0):
     for k, n in enumerate(sizes):
         s = inputs.System(pos=rng.uniform(0.0, 10.0, (3, n)), types=np.zeros(n, np.int32),
                           box=np.array([10.0, 10.0, 10.0]), pbc=np.array([1, 1, 1], np.int32))
-        out.append(serving.Request(rid=k, model=k % 2, system=s))
+        out.append(serving.Request(rid=k, model=k % 2, system=s, ws=n))  # one byte per particle
     return out
 
 
-def bare_server(max_particles, max_requests):
+def bare_server(max_bytes, max_requests):
     srv = serving.Server.__new__(serving.Server)  # no model handles (they need a GPU)
-    srv.max_particles = max_particles
+    srv.max_bytes = max_bytes
     srv.max_requests = max_requests
     srv.keep_results = True
     srv._cv = threading.Condition()
@@ -34,7 +35,7 @@ def bare_server(max_particles, max_requests):
 
 
 def test_admission_in_arrival_order_within_budgets():
-    srv = bare_server(max_particles=100, max_requests=3)
+    srv = bare_server(max_bytes=100, max_requests=3)
     reqs = make_requests([40, 50, 20, 10, 300, 5])
     srv._pending.extend(reqs)
     assert [r.rid for r in srv._admit()] == [0, 1]        # 40 + 50; adding 20 would pass 100
@@ -42,7 +43,7 @@ def test_admission_in_arrival_order_within_budgets():
     assert [r.rid for r in srv._admit()] == [4]           # an oversized request goes alone
     assert [r.rid for r in srv._admit()] == [5]
     assert srv._admit() == []
-    srv2 = bare_server(max_particles=10_000, max_requests=2)
+    srv2 = bare_server(max_bytes=10_000, max_requests=2)
     srv2._pending.extend(make_requests([1, 1, 1, 1, 1]))
     assert [len(srv2._admit()) for _ in range(3)] == [2, 2, 1]  # request budget
 
@@ -72,9 +73,10 @@ def test_serve_loop_hands_each_result_to_its_request(monkeypatch):
 
     monkeypatch.setattr(binding, "Model", FakeModel)
     monkeypatch.setattr(binding, "nep_compute_batch", fake_batch)
+    monkeypatch.setattr(binding, "nep_request_workspace", lambda hs, model, n, box, pbc: 10 * n)
     params = [inputs.random_model(seed=1), inputs.random_model(seed=2)]
-    srv = serving.Server(params, lanes=2, lane_bytes=200 * serving.bytes_per_particle(params[0]), max_requests=8)
-    assert srv.max_particles == 200
+    srv = serving.Server(params, lanes=3, lane_bytes=2250 * 9 // 8 + 1, max_requests=8, pinned=False)
+    assert srv.max_bytes == 2250
     sizes = [64, 17, 130, 5, 99, 64, 1, 250, 33, 70]
     reqs = make_requests(sizes, seed=3)
     stats = srv.serve(reqs, serving.poisson_arrivals(len(reqs), rate=2000.0, seed=4))
