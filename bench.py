@@ -105,7 +105,7 @@ def workload_model_note(name):
 
 
 # ---- algorithmic work per kernel (FMA = 2 flop; sin/cos, rsqrt, tanh, div = 1) ----
-def algorithmic_flops(m, pairs_r, pairs_a, n):
+def algorithmic_flops(m, pairs_r, pairs_a, n, fused=True):
     """Minimal flops of one evaluation per launch: every ordered pair's gradient
     f_ij counted once (the gather form computes both directions, so it does more),
     and the linear Chebyshev contractions of Eq. 6 moved to the bead level where
@@ -136,7 +136,11 @@ def algorithmic_flops(m, pairs_r, pairs_a, n):
     f_r = 13 + basis_d(KR) + 2 * KR + 6 + 18
     f_a = 16 + basis_d(KA) + 4 * nA * KA + 150 + 24 * (4 * nA + 10) + 12 + 18
     # the FP32 form's two evaluation kernels: descriptor + network + angular pair
-    # forces (stage "descriptor_network"), radial pair forces + outputs ("force_virial")
+    # forces (stage "descriptor_network"), radial pair forces + outputs ("force_virial");
+    # the FP64 form (fused=False): descriptor + network, then all pair forces
+    if not fused:
+        return {"descriptor_network": d_r * pairs_r + d_a * pairs_a + d_b * n,
+                "force_virial": f_r * pairs_r + f_a * pairs_a}
     return {"descriptor_network": d_r * pairs_r + d_a * pairs_a + d_b * n + f_a * pairs_a,
             "force_virial": f_r * pairs_r}
 
@@ -302,6 +306,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks0 = measured_peaks()
     binding.load(build_if_missing=True)
 
     model, system, vel0 = workload()
@@ -516,6 +521,10 @@ def run_ours(args):
                                 "timed like the headline")
 
     m.close()
+    configs = None
+    if not args.quick and not args.no_configs and world == 1:
+        sm_cfg = (peaks0 or {}).get("sm_max_mhz") or 2070.0
+        configs = config_legs(dev, n_sms, sm_cfg)
     serve = None
     if not args.quick and not args.no_serve and rank == 0:
         serve = serving_leg(local)
@@ -582,9 +591,145 @@ def run_ours(args):
                                 "chosen_by": "fixed (--tuning)" if args.tuning else "autotuner"},
             "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
             "steady_state_graph": steady, "plain_fp64": plain, "bf16_weights": bf16, "many_body": many_body,
-            "serving": serve}
+            "configs": configs, "serving": serve}
     print(json.dumps(line))
     return 0
+
+
+# FP64 rate of the part: 1.25 TFLOP/s nominal (no measured FP64 peak exists for it)
+FP64_PEAK_TFLOPS = 1.25
+
+
+def md_leg(name, model, system, vel0, precision, steps, dt, dev, n_sms, sm_max, strain=None, interval=100):
+    """One continuous velocity-Verlet trajectory of `steps` steps (no state restore),
+    timed with CUDA events on the launch stream, in calls of `interval` steps (graph
+    chunks); with strain = (axis, factor), positions and the box are rescaled by
+    `factor` along `axis` after every call (nep_scale_positions on the device).
+    Then a separate eager pass of 20 steps from the same start with CUDA events
+    between stages, for the dominant kernel's roofline."""
+    import torch
+
+    from paper_2603_01234_gb300 import binding
+    m = binding.Model(model, precision, device=dev.index or 0)
+    types = torch.from_numpy(system.types).to(dev)
+    pos0 = torch.from_numpy(system.pos.copy()).to(dev)
+    vel0_d = torch.from_numpy(vel0.copy()).to(dev)
+    pos, vel = pos0.clone(), vel0_d.clone()
+    force = torch.zeros(3, system.n, dtype=torch.float64, device=dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    box = np.array(system.box, dtype=np.float64)
+
+    def run(k, fv=1):
+        binding.nep_md_step(m.h, types, system.masses, box, system.pbc, pos, vel, force, fv, k, dt, 0, None, stream=sp)
+
+    run(0, 0)
+    f0 = force.clone()
+    run(min(interval, 10))  # warm-up: captures the step graph
+    binding.nep_sync(m.h)
+    pos.copy_(pos0)
+    vel.copy_(vel0_d)
+    force.copy_(f0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    done = 0
+    scale = None
+    if strain:
+        scale = np.ones(3)
+        scale[strain[0]] = strain[1]
+    while done < steps:
+        k = min(interval, steps - done)
+        run(k)
+        done += k
+        if strain and done < steps:
+            binding.nep_scale_positions(m.h, pos, scale, stream=sp)
+            box = box * scale
+    e1.record()
+    torch.cuda.synchronize()
+    binding.nep_sync(m.h)
+    ms = e0.elapsed_time(e1)
+    # stage times: a separate eager pass from the start
+    box = np.array(system.box, dtype=np.float64)
+    pos.copy_(pos0)
+    vel.copy_(vel0_d)
+    force.copy_(f0)
+    binding.nep_set_timing(m.h, 1)
+    run(20)
+    binding.nep_sync(m.h)
+    stages, tsteps = binding.nep_get_timing(m.h)
+    binding.nep_set_timing(m.h, 0)
+    cnt_r, _, _ = binding.nep_neighbors(m.h, system.types, system.pos, system.box, system.pbc, 0, 1)
+    cnt_a, _, _ = binding.nep_neighbors(m.h, system.types, system.pos, system.box, system.pbc, 1, 1)
+    tuning = binding.nep_get_tuning(m.h)
+    m.close()
+    n = system.n
+    fp64 = precision == "fp64"
+    work = algorithmic_flops(model, int(cnt_r.sum()), int(cnt_a.sum()), n, fused=not fp64)
+    st = {k: v / max(1, tsteps) for k, v in stages.items()}
+    dom = max(("descriptor_network", "force_virial"), key=lambda k: st[k])
+    achieved = work[dom] / (st[dom] / 1000.0) / 1e12
+    peak = FP64_PEAK_TFLOPS if fp64 else n_sms * 128 * 2 * sm_max * 1e6 / 1e12
+    return {"workload": name, "n": n, "precision": precision, "steps": steps, "dt_fs": dt,
+            "value": n * steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / steps,
+            "ns_per_day": (1000.0 * steps / ms) * dt * 0.0864,
+            "strain": None if not strain else {"axis": "xyz"[strain[0]], "factor": strain[1], "every_steps": interval},
+            "pairs_per_bead": {"radial": float(cnt_r.mean()), "angular": float(cnt_a.mean())},
+            "stages_ms_per_step": st, "kernel_variants": list(tuning),
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak,
+                         "peak_note": "FP64 nominal 1.25 TFLOP/s" if fp64 else
+                         f"FP32 ALU: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz"},
+            "how": "one continuous trajectory, calls of graph-captured step chunks, CUDA events around the run"}
+
+
+def drift_leg(model, system, vel0, precision, steps, dt, dev, every=10):
+    """NVE energy drift: `steps` velocity-Verlet steps from the start with a thermo
+    row every `every` steps; the slope of a linear fit of E_pot + E_kin against time,
+    per ns and per bead."""
+    import torch
+
+    from paper_2603_01234_gb300 import binding
+    m = binding.Model(model, precision, device=dev.index or 0)
+    types = torch.from_numpy(system.types).to(dev)
+    pos = torch.from_numpy(system.pos.copy()).to(dev)
+    vel = torch.from_numpy(vel0.copy()).to(dev)
+    force = torch.zeros(3, system.n, dtype=torch.float64, device=dev)
+    th = np.zeros((steps // every, 12))
+    binding.nep_md_step(m.h, types, system.masses, system.box, system.pbc, pos, vel, force, 0, steps, dt, every, th,
+                        stream=torch.cuda.current_stream(dev).cuda_stream)
+    binding.nep_sync(m.h)
+    m.close()
+    t_ns = th[:, 0] * dt * 1e-6
+    etot = th[:, 1] + th[:, 2]
+    slope, icpt = np.polyfit(t_ns, etot, 1)
+    resid = etot - (slope * t_ns + icpt)
+    return {"precision": precision, "steps": steps, "dt_fs": dt, "sample_every": every,
+            "drift_eV_per_ns_per_bead": slope / system.n,
+            "etot_fluct_rms_eV_per_bead": float(np.sqrt(np.mean(resid ** 2))) / system.n}
+
+
+def config_legs(dev, n_sms, sm_max):
+    """The other configurations at 1 GPU, each a continuous run: 512-bead water in
+    FP64 (and FP32 beside it), the 200,000-bead four-type monolayer in FP32 and with
+    BF16 hidden-layer weights, and the 1,000,000-particle nanowire over 2,000 steps
+    with the box rescaled by 1.001 along x every 100 steps; NVE drift of the 100,000-
+    bead water and of the nanowire in FP32 and FP64."""
+    out = {}
+    model, system, vel = workload("water512")
+    out["water512_fp64"] = md_leg("water512", model, system, vel, "fp64", 1000, 10.0, dev, n_sms, sm_max)
+    out["water512_fp32"] = md_leg("water512", model, system, vel, "fp32", 1000, 10.0, dev, n_sms, sm_max)
+    model, system, vel = workload("monolayer200k")
+    out["monolayer200k_fp32"] = md_leg("monolayer200k", model, system, vel, "fp32", 500, 20.0, dev, n_sms, sm_max)
+    out["monolayer200k_bf16"] = md_leg("monolayer200k", model, system, vel, "bf16", 500, 20.0, dev, n_sms, sm_max)
+    model, system, vel = workload("nanowire1M")
+    out["nanowire1M_fp32_strain"] = md_leg("nanowire1M", model, system, vel, "fp32", 2000, 5.0, dev, n_sms, sm_max,
+                                           strain=(0, 1.001), interval=100)
+    out["drift"] = {"nanowire1M": [drift_leg(model, system, vel, "fp32", 1000, 5.0, dev),
+                                   drift_leg(model, system, vel, "fp64", 200, 5.0, dev)]}
+    model, system, vel = workload("water100k")
+    out["drift"]["water100k"] = [drift_leg(model, system, vel, "fp32", 1000, 10.0, dev),
+                                 drift_leg(model, system, vel, "fp64", 1000, 10.0, dev)]
+    return out
 
 
 def serving_leg(device, n_requests=4096, fractions=(0.25, 0.5, 0.75, 0.9), repeats=5, lanes=2):
@@ -697,6 +842,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the steady-state, e2e and FP64 legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serve", action="store_true", help="skip the served-stream leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' runs")
     ap.add_argument("--workload", default="water100k", choices=sorted(WORKLOADS),
                     help="the metric is quoted on water100k; the others are further configurations")
     ap.add_argument("--drift", action="store_true", help="NVE energy-drift run (1000 steps, FP32 and FP64)")

@@ -1074,9 +1074,14 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
     }
     m->eval_per_bead = dr.on != 0;
 
-    // Size the neighbour lists (one synchronous probe) only for a new
-    // configuration shape; continuation calls rely on the deferred status.
-    const bool new_shape = (n != m->md_n) || memcmp(&g, &m->md_grid, sizeof g) != 0;
+    // Size the neighbour lists (one synchronous probe, and the autotuner) only for a
+    // new configuration shape: particle count, cells per axis, search ranges and
+    // periodicity.  A box that changes within those (a strain schedule rescaling it
+    // by 0.1%) keeps the lists' capacities and the tuned variants; the step graph,
+    // whose key holds the whole grid, is captured again.  Continuation calls rely
+    // on the deferred status.
+    const bool new_shape = (n != m->md_n) || memcmp(g.nc, m->md_grid.nc, sizeof g.nc) != 0 ||
+                           memcmp(g.S, m->md_grid.S, sizeof g.S) != 0 || memcmp(g.pbc, m->md_grid.pbc, sizeof g.pbc) != 0;
     if (new_shape || !forces_valid) {
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->cur));
         NEP_TRY(run_cells<real>(m, p, types_d, pos_d));
