@@ -499,7 +499,7 @@ template <typename real>
 int run_cells(nep_model* m, const Plan& p, const int* types_d, const double* pos_d)
 {
     cudaError_t e = launch_cell_build<real>(
-        d_counts(p), p.n_cap, p.items_cap, p.ncell_cap, m->cells_dirty, d_items(p), d_reqs(p), d_models<real>(p),
+        d_counts(p), p.n_cap, p.items_cap, p.ncell_cap, m->cells_dirty, false, d_items(p), d_reqs(p), d_models<real>(p),
         pos_d, types_d, m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(), m->cell_count.as<int>(),
         m->cell_local.as<int>(), m->block_off.as<int>(), m->cell_fill.as<int>(), m->perm_tmp.as<int>(),
         m->perm.as<int>(), m->cell_start.as<int>(), m->cell_s.as<int>(), m->rec_s.as<PosRec<real>>(),
@@ -507,6 +507,39 @@ int run_cells(nep_model* m, const Plan& p, const int* types_d, const double* pos
     if (e != cudaSuccess) {
         m->cells_dirty = true;
         return fail(NEP_ERR_CUDA, std::string("cell build: ") + cudaGetErrorString(e));
+    }
+    m->cells_dirty = false;
+    return NEP_OK;
+}
+
+// The MD step's opening (kicks, drift, binning in one kernel) and the rest of the
+// cell build.  Counters that may be dirty are cleared before the binning counts.
+template <typename real>
+int run_kick_drift_cells(nep_model* m, const Plan& p, const int* types_d, const double* inv_m_acc, int n_kicks,
+                         double half_dt, double dt, double* pos, double* vel, const double* force,
+                         cudaEvent_t* ev = nullptr)
+{
+    if (m->cells_dirty) {
+        NEP_CUDA(cudaMemsetAsync(m->cell_count.p, 0, sizeof(int) * p.ncell_cap, m->cur));
+        NEP_CUDA(cudaMemsetAsync(m->cell_fill.p, 0, sizeof(int) * p.ncell_cap, m->cur));
+    }
+    TypeTable tt;
+    for (int k = 0; k < kMdMaxTypes; ++k) tt.v[k] = k < m->T ? inv_m_acc[k] : 0.0;
+    cudaError_t e = launch_kick_drift_bin<real>(d_counts(p), p.items_cap, d_items(p), d_reqs(p), d_models<real>(p),
+                                                types_d, tt, n_kicks, half_dt, dt, pos, vel, force,
+                                                m->cell_of.as<int>(), m->rec_user.as<PosRec<real>>(),
+                                                m->cell_count.as<int>(), m->flags.as<int>() + 2, m->cur);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], m->cur);
+    if (e == cudaSuccess)
+        e = launch_cell_build<real>(d_counts(p), p.n_cap, p.items_cap, p.ncell_cap, false, true, d_items(p), d_reqs(p),
+                                    d_models<real>(p), pos, types_d, m->cell_of.as<int>(),
+                                    m->rec_user.as<PosRec<real>>(), m->cell_count.as<int>(), m->cell_local.as<int>(),
+                                    m->block_off.as<int>(), m->cell_fill.as<int>(), m->perm_tmp.as<int>(),
+                                    m->perm.as<int>(), m->cell_start.as<int>(), m->cell_s.as<int>(),
+                                    m->rec_s.as<PosRec<real>>(), m->flags.as<int>() + 2, m->cur);
+    if (e != cudaSuccess) {
+        m->cells_dirty = true;
+        return fail(NEP_ERR_CUDA, std::string("kick/drift + cell build: ") + cudaGetErrorString(e));
     }
     m->cells_dirty = false;
     return NEP_OK;
@@ -938,9 +971,14 @@ int md_forces(nep_model* m, const Plan& p, int n, double* force, const Drive& dr
 
 // One MD step's launches (used eagerly and under stream capture).
 template <typename real>
+// n_kicks: the opening half-kicks (2 when the previous step's closing kick was
+// deferred into this step's opening); close: emit this step's closing kick (a step
+// defers it only when nothing before the next step's opening reads the velocities:
+// no thermo row, thermostat or heat current, and not the last step of the call).
+// Kicks are separately rounded either way, so deferral changes no result.
 int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_m_acc, const double* mass,
                      const CellGrid& g, double* pos, double* vel, double* force, double dt, bool sample,
-                     int step_stride, const Thermostat& th, const Drive& dr)
+                     int step_stride, const Thermostat& th, const Drive& dr, int n_kicks, bool close)
 {
     const Plan& p = m->plan;
     cudaEvent_t* ev = nullptr;
@@ -952,17 +990,20 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
         m->timer.head = (r + 1) % StageTimer::kRing;
         NEP_CUDA(cudaEventRecord(ev[0], m->cur));
     }
-    cudaError_t e = launch_kick_drift(n, types_d, inv_m_acc, m->T, 0.5 * dt, dt, g, pos, vel, force, m->cur);
-    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick/drift: ") + cudaGetErrorString(e));
-    if (ev) NEP_CUDA(cudaEventRecord(ev[1], m->cur));
-    NEP_TRY(run_cells<real>(m, p, types_d, pos));
+    (void)g;  // the kernels take the grid from the plan's request table
+    if (!close && (sample || th.noise || dr.on)) return fail(NEP_ERR_ARG, "closing kick cannot be deferred here");
+    // stage 0: kicks + drift + binning; stage 1: the rest of the cell build
+    NEP_TRY(run_kick_drift_cells<real>(m, p, types_d, inv_m_acc, n_kicks, 0.5 * dt, dt, pos, vel, force, ev));
     if (ev) NEP_CUDA(cudaEventRecord(ev[2], m->cur));
     NEP_TRY(run_neighbors<real>(m, p));
     if (ev) NEP_CUDA(cudaEventRecord(ev[3], m->cur));
     NEP_TRY(md_forces<real>(m, p, n, force, dr, ev ? ev[4] : nullptr));
     if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
-    e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
-    if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
+    cudaError_t e = cudaSuccess;
+    if (close) {
+        e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
+        if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
+    }
     if (th.noise) {
         e = launch_bussi(n, types_d, mass, m->T, vel, m->partial2.as<double>(), m->counters.as<unsigned int>(),
                          th.noise, m->bussi.as<int>(), th.c, th.kbar, th.n_f, m->bussi.as<double>() + 1, m->cur);
@@ -1159,9 +1200,14 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         m->graph.reset();
         NEP_CUDA(cudaStreamBeginCapture(m->cur, cudaStreamCaptureModeThreadLocal));
         int rc = NEP_OK;
-        for (int s = 0; s < chunk && rc == NEP_OK; ++s)
-            rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                        sample_every > 0 && s == chunk - 1, sample_every, th, dr);
+        bool prev_close = true;
+        for (int s = 0; s < chunk && rc == NEP_OK; ++s) {
+            const bool smp = sample_every > 0 && s == chunk - 1;
+            const bool close = s == chunk - 1 || smp || th.noise || dr.on;
+            rc = md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt, smp,
+                                        sample_every, th, dr, prev_close ? 1 : 2, close);
+            prev_close = close;
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t ec = cudaStreamEndCapture(m->cur, &graph);
         if (rc != NEP_OK) {
@@ -1221,9 +1267,13 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
             pending = true;
         }
     }
-    for (; done < n_steps; ++done)
-        NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt,
-                                       sample_every > 0 && (done + 1) % sample_every == 0, sample_every, th, dr));
+    for (bool prev_close = true; done < n_steps; ++done) {
+        const bool smp = sample_every > 0 && (done + 1) % sample_every == 0;
+        const bool close = done == n_steps - 1 || smp || th.noise || dr.on;
+        NEP_TRY(md_step_launches<real>(m, n, types_d, inv_m.data(), mass.data(), g, pos_d, vel_d, force_d, dt, smp,
+                                       sample_every, th, dr, prev_close ? 1 : 2, close));
+        prev_close = close;
+    }
     NEP_CUDA(cudaMemcpyAsync(m->h_async, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
     NEP_CUDA(cudaEventRecord(m->ev_flags, m->cur));
     m->async_pending = true;
@@ -1531,6 +1581,7 @@ int nep_create(nep_model** out, int n_types, const double* rc_radial, const doub
     o.rcAl = p; p += TT;
     const int cRs = coef_stride(m->nR, m->KR), cAs = coef_stride(m->nA, m->KA);
     o.cR = p; p += TT * cRs;
+    if (T == 1) p = (p + 3) & ~3;  // one type: its angular table is read with 16-byte vector loads
     o.cA = p; p += TT * cAs;
     o.n_cut_coef = p;
     // W0 rows: one type pads them to a multiple of 4 reals at a 16-byte aligned start
@@ -2202,7 +2253,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     NEP_CUDA(cudaMemsetAsync(counters, 0, 16, m->cur));
     // the scratch's regions move with n, so the cell counters are cleared here
     cudaError_t e = launch_cell_build<real>(
-        d_cnt, n, n_items, g.ncell, true, d_it, d_rq, d_md, pos, types, (int*)(base + L.cell_of),
+        d_cnt, n, n_items, g.ncell, true, false, d_it, d_rq, d_md, pos, types, (int*)(base + L.cell_of),
         (PosRec<real>*)(base + L.rec_user), (int*)(base + L.cell_count), (int*)(base + L.cell_local),
         (int*)(base + L.block_off), (int*)(base + L.cell_fill), (int*)(base + L.perm_tmp), (int*)(base + L.perm),
         (int*)(base + L.cell_start), (int*)(base + L.cell_s), (PosRec<real>*)(base + L.rec_s), flags + 2, m->cur);

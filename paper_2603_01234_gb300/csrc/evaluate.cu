@@ -245,6 +245,20 @@ __device__ __forceinline__ void loadN(const real* p, real* o)
 // consistent sign, which through |u| = |r| / r and the homogeneous harmonics would
 // bias the angular descriptors; after the step the quadratic term is ~1e-14 and
 // what remains is the (unsigned) rounding of y^2.
+// A type pair's n x K coefficient table into registers.  A one-type model's single
+// table starts on a 16-byte boundary and is read with vector loads; several types'
+// tables sit at odd strides (bank spread) and are read as scalars.
+template <typename real, int N>
+__device__ __forceinline__ void load_coef(const real* c, bool aligned, real (&o)[N])
+{
+    if (aligned) {
+        loadN<real, N>(c, o);
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) o[q] = c[q];
+    }
+}
+
 __device__ __forceinline__ float rsqrt_r(float x)
 {
     const float y = rsqrtf(x);
@@ -682,7 +696,8 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
         const int tp = ti * T + rj.t;
         real f[KA];
         basis<real, KA>(r, P[off.rcAi + tp], P[off.rcAl + tp], f);
-        const real* c = P + off.cA + tp * coef_stride(NA, KA);
+        real c[NA * KA];
+        load_coef(P + off.cA + tp * coef_stride(NA, KA), T == 1, c);
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
 #pragma unroll
@@ -743,10 +758,16 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
                 real x = -b0[mu];
 #pragma unroll
                 for (int v = 0; v < ND; ++v) x += w[v] * q[v];
-                if constexpr (kRes) {  // residual row straight from shared memory (no register copy)
+                if constexpr (kRes) {  // residual row four entries at a time (vector loads)
                     real xl = -b0l[mu];
 #pragma unroll
-                    for (int v = 0; v < ND; ++v) xl += w0l[mu * NDV + v] * q[v];
+                    for (int v4 = 0; v4 < NDV; v4 += 4) {
+                        real wl[4];
+                        load4(w0l + mu * NDV + v4, wl);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (v4 + u < ND) xl += wl[u] * q[v4 + u];
+                    }
                     x += xl;
                 }
                 const real h = tanh_r(x);
@@ -1172,7 +1193,8 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
         real f[KA], df[KA];
         basis_d<real, KA>(r, P[off.rcAi + tij], P[off.rcAl + tij], f, df);
         real g[NA], dg[NA];
-        const real* cc = P + off.cA + tij * coef_stride(NA, KA);
+        real cc[NA * KA];
+        load_coef(P + off.cA + tij * coef_stride(NA, KA), T == 1, cc);
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) {
             real s0 = real(0), s1 = real(0);

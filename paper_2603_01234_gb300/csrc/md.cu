@@ -1,6 +1,6 @@
 // Velocity-Verlet NVE integration in FP64 (the MD loop in which the potential is
 // evaluated) and the kinetic-energy sample.
-//   k_kick_drift   v += dt/2 F/m ;  r += dt v ;  wrap periodic axes to [0, L)
+//   (the opening kick, drift and wrap run fused with the cell binning: k_kick_drift_bin)
 //   k_kick         v += dt/2 F/m
 //   k_sample       E_kin = sum 1/2 m v^2 (FP64, deterministic last-block total) and
 //                  one thermo row (step, E_pot, E_kin, W[9])
@@ -19,11 +19,6 @@ namespace nep {
 
 // 1 eV / (Angstrom amu) in Angstrom / fs^2 (acceleration of a force in eV/A on a mass in amu)
 constexpr double kAcc = 9.648533212e-3;
-constexpr int kMdMaxTypes = 16;
-
-struct TypeTable {
-    double v[kMdMaxTypes];
-};
 
 // Sum of partial[b * NC + c] over the nb blocks, by the whole (last) block: fixed
 // strides per thread and a fixed tree, so the result does not depend on timing.
@@ -53,23 +48,6 @@ __device__ __forceinline__ void last_block_sum(const double* partial, unsigned n
     }
 }
 
-__global__ void __launch_bounds__(kBlock) k_kick_drift(int n, const int* __restrict__ types, TypeTable inv_m_acc,
-                                                       double half_dt, double dt, CellGrid g, double* __restrict__ pos,
-                                                       double* __restrict__ vel, const double* __restrict__ force)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double im = inv_m_acc.v[types[i]];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const size_t k = (size_t)a * n + i;
-        const double v = vel[k] + half_dt * force[k] * im;
-        vel[k] = v;
-        const double x = pos[k] + dt * v;
-        pos[k] = g.pbc[a] ? wrap_periodic(x, g.box[a]) : x;
-    }
-}
-
 __global__ void __launch_bounds__(kBlock) k_kick(int n, const int* __restrict__ types, TypeTable inv_m_acc,
                                                  double half_dt, double* __restrict__ vel,
                                                  const double* __restrict__ force)
@@ -80,7 +58,7 @@ __global__ void __launch_bounds__(kBlock) k_kick(int n, const int* __restrict__ 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const size_t k = (size_t)a * n + i;
-        vel[k] += half_dt * force[k] * im;
+        vel[k] = half_kick(vel[k], half_dt, force[k], im);
     }
 }
 
@@ -288,15 +266,6 @@ static TypeTable make_table(const double* v, int T)
     TypeTable t;
     for (int k = 0; k < kMdMaxTypes; ++k) t.v[k] = k < T ? v[k] : 0.0;
     return t;
-}
-
-cudaError_t launch_kick_drift(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double dt,
-                              const CellGrid& g, double* pos, double* vel, const double* force, cudaStream_t st)
-{
-    if (T > kMdMaxTypes) return cudaErrorInvalidValue;
-    k_kick_drift<<<(n + kBlock - 1) / kBlock, kBlock, 0, st>>>(n, types, make_table(inv_m_acc, T), half_dt, dt, g,
-                                                               pos, vel, force);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_kick(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double* vel,

@@ -13,6 +13,43 @@
 
 namespace nep {
 
+// Bin particle i (caller index, request q) at position x: wrap periodic axes, find
+// its cell, store its cell-relative record and count it in its cell.
+template <typename real>
+__device__ __forceinline__ void bin_one(const ReqInfo& q, int i, double (&x)[3], int t, int n_types,
+                                        int* __restrict__ cell_of, PosRec<real>* __restrict__ rec,
+                                        int* __restrict__ cell_count, int* __restrict__ err)
+{
+    const CellGrid& g = q.g;
+    int c3[3];
+    real xr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(x[a])) {
+            atomicOr(err, 1);
+            x[a] = 0.0;
+        }
+        if (g.pbc[a]) x[a] = wrap_periodic(x[a], g.box[a]);
+        const double cf = floor(x[a] * g.inv_len[a]);
+        int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
+        c3[a] = c;
+        xr[a] = (real)(x[a] - (double)c * g.len[a]);
+    }
+    if (t < 0 || t >= n_types) {
+        atomicOr(err, 2);
+        t = 0;
+    }
+    const int cell = q.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+    cell_of[i] = cell;
+    PosRec<real> r;
+    r.x = xr[0];
+    r.y = xr[1];
+    r.z = xr[2];
+    r.t = t;
+    rec[i] = r;
+    atomicAdd(&cell_count[cell], 1);
+}
+
 template <typename real>
 __global__ void __launch_bounds__(kBlock) k_bin(const PlanCounts* __restrict__ pc, const WorkItem* __restrict__ items,
                                                 const ReqInfo* __restrict__ reqs,
@@ -27,38 +64,64 @@ __global__ void __launch_bounds__(kBlock) k_bin(const PlanCounts* __restrict__ p
         const int i = it.begin + threadIdx.x;
         if (i >= it.end) continue;
         const ReqInfo& q = reqs[it.req];
-        const CellGrid& g = q.g;
         const int local = i - q.begin;
-        int c3[3];
-        real xr[3];
+        double x[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double x = pos[(size_t)3 * q.begin + (size_t)a * q.n + local];
-            if (!isfinite(x)) {
-                atomicOr(err, 1);
-                x = 0.0;
-            }
-            if (g.pbc[a]) x = wrap_periodic(x, g.box[a]);
-            const double cf = floor(x * g.inv_len[a]);
-            int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
-            c3[a] = c;
-            xr[a] = (real)(x - (double)c * g.len[a]);
-        }
-        int t = types[i];
-        if (t < 0 || t >= models[q.model].T) {
-            atomicOr(err, 2);
-            t = 0;
-        }
-        const int cell = q.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
-        cell_of[i] = cell;
-        PosRec<real> r;
-        r.x = xr[0];
-        r.y = xr[1];
-        r.z = xr[2];
-        r.t = t;
-        rec[i] = r;
-        atomicAdd(&cell_count[cell], 1);
+        for (int a = 0; a < 3; ++a) x[a] = pos[(size_t)3 * q.begin + (size_t)a * q.n + local];
+        bin_one<real>(q, i, x, types[i], models[q.model].T, cell_of, rec, cell_count, err);
     }
+}
+
+// The MD step's opening kicks, drift and binning in one pass (one request).
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_kick_drift_bin(const PlanCounts* __restrict__ pc,
+                                                           const WorkItem* __restrict__ items,
+                                                           const ReqInfo* __restrict__ reqs,
+                                                           const ModelDesc<real>* __restrict__ models,
+                                                           const int* __restrict__ types, TypeTable inv_m_acc,
+                                                           int n_kicks, double half_dt, double dt,
+                                                           double* __restrict__ pos, double* __restrict__ vel,
+                                                           const double* __restrict__ force, int* __restrict__ cell_of,
+                                                           PosRec<real>* __restrict__ rec, int* __restrict__ cell_count,
+                                                           int* __restrict__ err)
+{
+    if ((int)blockIdx.x >= pc->n_items) return;
+    const WorkItem it = items[blockIdx.x];
+    const int i = it.begin + threadIdx.x;
+    if (i >= it.end) return;
+    const ReqInfo& q = reqs[it.req];
+    const int n = q.n, local = i - q.begin;
+    const int t = types[i];
+    const int T = models[q.model].T;
+    const double im = inv_m_acc.v[t >= 0 && t < T ? t : 0];
+    double x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const size_t k = (size_t)3 * q.begin + (size_t)a * n + local;
+        double v = vel[k];
+        const double f = force[k];
+        for (int s = 0; s < n_kicks; ++s) v = half_kick(v, half_dt, f, im);  // separately rounded, as two kernels
+        vel[k] = v;
+        double xa = drift(pos[k], dt, v);
+        if (q.g.pbc[a]) xa = wrap_periodic(xa, q.g.box[a]);
+        pos[k] = xa;
+        x[a] = xa;
+    }
+    bin_one<real>(q, i, x, t, T, cell_of, rec, cell_count, err);
+}
+
+template <typename real>
+cudaError_t launch_kick_drift_bin(const PlanCounts* counts, int items_cap, const WorkItem* items,
+                                  const ReqInfo* reqs, const ModelDesc<real>* models, const int* types,
+                                  const TypeTable& inv_m_acc, int n_kicks, double half_dt, double dt, double* pos,
+                                  double* vel, const double* force, int* cell_of, PosRec<real>* rec_user,
+                                  int* cell_count, int* err, cudaStream_t st)
+{
+    if (items_cap < 1 || n_kicks < 1 || n_kicks > 2) return cudaErrorInvalidValue;
+    k_kick_drift_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, types, inv_m_acc, n_kicks,
+                                                         half_dt, dt, pos, vel, force, cell_of, rec_user, cell_count,
+                                                         err);
+    return cudaGetLastError();
 }
 
 // Block-local exclusive scan of kScanItems counts (4 per thread, 1024 threads),
@@ -201,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_cell_rank(const PlanCounts* __restri
 
 template <typename real>
 cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap, int ncell_cap, bool zero_counts,
-                              const WorkItem* items, const ReqInfo* reqs, const ModelDesc<real>* models,
+                              bool skip_bin, const WorkItem* items, const ReqInfo* reqs, const ModelDesc<real>* models,
                               const double* pos, const int* types, int* cell_of, PosRec<real>* rec_user,
                               int* cell_count, int* cell_start_local, int* block_off, int* cell_fill, int* perm_tmp,
                               int* perm, int* cell_start, int* cell_s, PosRec<real>* rec_sorted, int* err,
@@ -214,8 +277,9 @@ cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap
         if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
     }
-    k_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, pos, types, cell_of, rec_user, cell_count,
-                                              err);
+    if (!skip_bin)
+        k_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, pos, types, cell_of, rec_user,
+                                                  cell_count, err);
     k_scan_local<<<nb_scan, 1024, 0, st>>>(counts, cell_count, cell_start_local, block_off, cell_fill);
     k_scan_top<<<1, 1024, 0, st>>>(counts, block_off);
     const int nt = (n_cap > ncell_cap + 1 ? n_cap : ncell_cap + 1);
@@ -364,7 +428,11 @@ cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t 
 }
 
 #define NEP_INSTANTIATE(real)                                                                                   \
-    template cudaError_t launch_cell_build<real>(const PlanCounts*, int, int, int, bool, const WorkItem*,      \
+    template cudaError_t launch_kick_drift_bin<real>(const PlanCounts*, int, const WorkItem*, const ReqInfo*, \
+                                                     const ModelDesc<real>*, const int*, const TypeTable&, int,   \
+                                                     double, double, double*, double*, const double*, int*,       \
+                                                     PosRec<real>*, int*, int*, cudaStream_t);                    \
+    template cudaError_t launch_cell_build<real>(const PlanCounts*, int, int, int, bool, bool, const WorkItem*, \
                                                  const ReqInfo*, const ModelDesc<real>*, const double*,           \
                                                  const int*, int*, PosRec<real>*, int*, int*, int*, int*, int*,   \
                                                  int*, int*, int*, PosRec<real>*, int*, cudaStream_t);            \

@@ -109,6 +109,20 @@ __host__ __device__ inline double wrap_periodic(double x, double L)
     return (x >= L || x < 0.0) ? 0.0 : x;
 }
 
+// Per-type values passed by value to the integration kernels (at most 16 types).
+constexpr int kMdMaxTypes = 16;
+struct TypeTable {
+    double v[kMdMaxTypes];
+};
+
+// Velocity-Verlet half-kick and drift of one coordinate, as every integration
+// kernel forms them (explicit FMAs, so fused and separate kernels round alike).
+__device__ __forceinline__ double half_kick(double v, double half_dt, double f, double im)
+{
+    return fma(half_dt * f, im, v);
+}
+__device__ __forceinline__ double drift(double x, double dt, double v) { return fma(dt, v, x); }
+
 // Offsets (in elements of `real`) of the model tables inside one device buffer.
 struct ParamLayout {
     int rcR2, rcA2, rcRi, rcAi; // [T][T] each: squared and inverse cutoffs
@@ -213,11 +227,24 @@ struct EvalArgs {
 // them first for callers whose buffers may hold anything.
 template <typename real>
 cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap, int ncell_cap, bool zero_counts,
+                              bool skip_bin,
                               const WorkItem* items, const ReqInfo* reqs, const ModelDesc<real>* models,
                               const double* pos, const int* types, int* cell_of, PosRec<real>* rec_user,
                               int* cell_count, int* cell_start_local, int* block_off, int* cell_fill, int* perm_tmp,
                               int* perm, int* cell_start, int* cell_s, PosRec<real>* rec_sorted, int* err,
                               cudaStream_t st);
+
+// The MD step's opening: n_kicks (1 or 2) velocity half-kicks v += dt/2 F/m (two when
+// the previous step's closing kick was deferred into this one), the drift
+// r += dt v, the wrap, and the cell binning of the new positions (what k_bin does),
+// in one pass; the cell build then runs with skip_bin.  A single request (the MD
+// configuration), one work item per block.
+template <typename real>
+cudaError_t launch_kick_drift_bin(const PlanCounts* counts, int items_cap, const WorkItem* items,
+                                  const ReqInfo* reqs, const ModelDesc<real>* models, const int* types,
+                                  const TypeTable& inv_m_acc, int n_kicks, double half_dt, double dt, double* pos,
+                                  double* vel, const double* force, int* cell_of, PosRec<real>* rec_user,
+                                  int* cell_count, int* err, cudaStream_t st);
 
 template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st);
@@ -237,8 +264,6 @@ bool evaluate_shape_supported(int nR, int nA, int KR, int KA);
 template <typename real>
 cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, size_t smem_force);
 
-cudaError_t launch_kick_drift(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double dt,
-                              const CellGrid& g, double* pos, double* vel, const double* force, cudaStream_t st);
 cudaError_t launch_kick(int n, const int* types, const double* inv_m_acc, int T, double half_dt, double* vel,
                         const double* force, cudaStream_t st);
 cudaError_t launch_sample(int n, const int* types, const double* mass, int T, const double* vel,
