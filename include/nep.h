@@ -355,7 +355,7 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
 
 /*
  * Autotuner.  The FP32 descriptor and force kernels are compiled in variants
- * that keep 2 or 3 (force: 2, 3 or 4) thread blocks resident per SM (a register
+ * that keep 2 or 3 (force: 3, 4 or 5) thread blocks resident per SM (a register
  * budget per thread).  nep_autotune evaluates the configuration several times with
  * each variant, times the two kernels separately with CUDA events, and keeps for
  * each kernel the 3-block default unless another variant is at least 5% faster;
@@ -366,7 +366,7 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
 int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
                  const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force);
 
-/* Set the variants (descriptor 2 or 3, force 2, 3 or 4) and whether MD calls tune
+/* Set the variants (descriptor 2 or 3, force 3, 4 or 5) and whether MD calls tune
  * automatically (1/0); other values give NEP_ERR_ARG. */
 int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force);
 

@@ -225,7 +225,7 @@ struct nep_model {
     // workspace
     Buf cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
-    Buf partial, partial2, counters, totals, flags, thermo, sample_index;
+    Buf partial, partial2, counters, gcounters, totals, flags, thermo, sample_index;
     Buf acc;  // FP32 form: force and virial fixed-point lines, thread virial sums (acc_bytes)
     bool eval_per_bead = false;  // the evaluation in progress returns per-particle virials
     bool cells_dirty = true;     // the cell counters may be non-zero (new buffer, or a build that failed)
@@ -442,6 +442,9 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     if (m->counters.cap / sizeof(unsigned int) != old_req)  // fresh buffer: counters start at zero
         NEP_CUDA(cudaMemsetAsync(m->counters.p, 0, m->counters.cap, m->cur));
     NEP_TRY(m->totals.ensure(sizeof(double) * 10 * (size_t)n_req));
+    const size_t old_items = m->gcounters.cap;
+    NEP_TRY(m->gcounters.ensure(sizeof(unsigned int) * (size_t)n_items));
+    if (m->gcounters.cap != old_items) NEP_CUDA(cudaMemsetAsync(m->gcounters.p, 0, m->gcounters.cap, m->cur));
     return NEP_OK;
 }
 
@@ -459,12 +462,13 @@ int ensure_cells(nep_model* m, int ncell)
     // buffer starts with anything in it, so the next build clears them first
     const void* c0 = m->cell_count.p;
     const void* f0 = m->cell_fill.p;
+    const void* b0 = m->block_off.p;
     NEP_TRY(m->cell_count.ensure(sizeof(int) * ncell));
     NEP_TRY(m->cell_local.ensure(sizeof(int) * ncell));
     NEP_TRY(m->block_off.ensure(sizeof(int) * (kScanItems + 1)));
     NEP_TRY(m->cell_fill.ensure(sizeof(int) * ncell));
     NEP_TRY(m->cell_start.ensure(sizeof(int) * (ncell + 1)));
-    if (m->cell_count.p != c0 || m->cell_fill.p != f0) m->cells_dirty = true;
+    if (m->cell_count.p != c0 || m->cell_fill.p != f0 || m->block_off.p != b0) m->cells_dirty = true;
     return NEP_OK;
 }
 
@@ -575,9 +579,17 @@ int run_neighbors(nep_model* m, const Plan& p)
     return NEP_OK;
 }
 
+// The MD step's closing half-kick, when the output pass applies it.
+struct FusedKick {
+    double* vel;
+    const int* types;
+    const double* inv_m_acc;  // host, [T]
+    double half_dt;
+};
+
 template <typename real>
 int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, double* site, double* totals,
-                 cudaEvent_t mid = nullptr)
+                 cudaEvent_t mid = nullptr, const FusedKick* kick = nullptr)
 {
     EvalArgs<real> a;
     a.n = p.n_cap;
@@ -607,7 +619,15 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.wsum = acc_wsum(m->acc.p, p.n_cap);
     a.partial = m->partial.as<double>();
     a.counter = m->counters.as<unsigned int>() + 2;
+    a.gcounter = m->gcounters.as<unsigned int>();
     a.totals = totals;
+    if (kick) {
+        if (m->T > kMdMaxTypes) return fail(NEP_ERR_ARG, "too many types for MD");
+        a.kick_vel = kick->vel;
+        a.kick_types = kick->types;
+        a.kick_half_dt = kick->half_dt;
+        for (int t = 0; t < kMdMaxTypes; ++t) a.kick_im.v[t] = t < m->T ? kick->inv_m_acc[t] : 0.0;
+    }
     cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, p.items_cap, p.smem_desc,
                                           p.smem_force, m->cur, mid, m->mb_desc, m->mb_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
@@ -665,6 +685,21 @@ int eval_pipeline(nep_model* m, const Plan& p, const int* types_d, const double*
     return NEP_OK;
 }
 
+// The device addresses of every workspace buffer a pipeline launch bakes in: part
+// of every graph key, so a graph is never replayed after a buffer moved.
+void put_workspace_ptrs(std::vector<unsigned char>& key, const nep_model* m)
+{
+    const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
+                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
+                         &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters,
+                         &m->gcounters, &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->acc, &m->bussi,
+                         &m->md_virial, &m->md_site, &m->heat, &m->heat_rows};
+    for (const Buf* b : bufs) {
+        const unsigned char* q = (const unsigned char*)&b->p;
+        key.insert(key.end(), q, q + sizeof(void*));
+    }
+}
+
 // Everything a captured evaluation graph bakes in: launch shapes, shared-memory
 // sizes, kernel variants, list capacities and every device pointer.
 template <typename real>
@@ -680,11 +715,8 @@ std::vector<unsigned char> eval_graph_key(const nep_model* m, const Plan& p, con
     put(ints, sizeof ints);
     const size_t sm[] = {p.smem_desc, p.smem_force, p.smem_nbr, p.off_reqs, p.off_items, p.off_models};
     put(sm, sizeof sm);
-    const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
-                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
-                         &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->counters, &m->flags,
-                         &m->acc, &p.dev};
-    for (const Buf* b : bufs) put(&b->p, sizeof(void*));
+    put_workspace_ptrs(key, m);
+    put(&p.dev.p, sizeof(void*));
     put(io, sizeof(void*) * n_io);
     return key;
 }
@@ -903,8 +935,8 @@ int autotune_plan(nep_model* m, const Plan& p, double* force_d)
     for (cudaEvent_t& x : ev.e) NEP_CUDA(cudaEventCreate(&x));
     cudaEvent_t e0 = ev.e[0], em = ev.e[1], e1 = ev.e[2];
     // (descriptor, force) blocks per SM; every variant of each kernel appears
-    const int pairs[3][2] = {{2, 2}, {3, 3}, {3, 4}};
-    float best_d[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f}, best_f[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+    const int pairs[3][2] = {{2, 3}, {3, 4}, {3, 5}};
+    float best_d[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f}, best_f[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     const int keep_d = m->mb_desc, keep_f = m->mb_force;
     auto trial = [&](int c, bool timed) -> int {
         m->mb_desc = pairs[c][0];
@@ -934,7 +966,7 @@ int autotune_plan(nep_model* m, const Plan& p, double* force_d)
     const float margin = 0.95f;
     m->mb_desc = best_d[2] < margin * best_d[3] ? 2 : 3;
     int bf = 3;
-    for (int v = 2; v <= 4; v += 2)
+    for (int v = 4; v <= 5; ++v)
         if (best_f[v] < margin * best_f[3] && best_f[v] < best_f[bf]) bf = v;
     m->mb_force = bf;
     return NEP_OK;
@@ -958,10 +990,12 @@ struct Drive {
 
 // The force evaluation of an MD step, with the driving force added when it is on.
 template <typename real>
-int md_forces(nep_model* m, const Plan& p, int n, double* force, const Drive& dr, cudaEvent_t mid = nullptr)
+int md_forces(nep_model* m, const Plan& p, int n, double* force, const Drive& dr, cudaEvent_t mid = nullptr,
+              const FusedKick* kick = nullptr)
 {
+    if (kick && dr.on) return fail(NEP_ERR_ARG, "the driving force precedes the closing kick");
     NEP_TRY(run_evaluate<real>(m, p, force, dr.on ? dr.virial : nullptr, dr.on ? dr.site : nullptr,
-                               m->totals.as<double>(), mid));
+                               m->totals.as<double>(), mid, kick));
     if (dr.on) {
         cudaError_t e = launch_hnemd_force(n, dr.fe, dr.virial, m->totals.as<double>(), force, m->cur);
         if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("driving force: ") + cudaGetErrorString(e));
@@ -997,10 +1031,14 @@ int md_step_launches(nep_model* m, int n, const int* types_d, const double* inv_
     if (ev) NEP_CUDA(cudaEventRecord(ev[2], m->cur));
     NEP_TRY(run_neighbors<real>(m, p));
     if (ev) NEP_CUDA(cudaEventRecord(ev[3], m->cur));
-    NEP_TRY(md_forces<real>(m, p, n, force, dr, ev ? ev[4] : nullptr));
+    // the closing kick rides on the output pass unless the driving force still has
+    // to be added to the forces
+    const bool fuse_kick = close && !dr.on;
+    const FusedKick kick = {vel, types_d, inv_m_acc, 0.5 * dt};
+    NEP_TRY(md_forces<real>(m, p, n, force, dr, ev ? ev[4] : nullptr, fuse_kick ? &kick : nullptr));
     if (ev) NEP_CUDA(cudaEventRecord(ev[5], m->cur));
     cudaError_t e = cudaSuccess;
-    if (close) {
+    if (close && !fuse_kick) {
         e = launch_kick(n, types_d, inv_m_acc, m->T, 0.5 * dt, vel, force, m->cur);
         if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("kick: ") + cudaGetErrorString(e));
     }
@@ -1175,10 +1213,9 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
             const unsigned char* b = (const unsigned char*)q;
             key.insert(key.end(), b, b + sz);
         };
-        const void* ptrs[] = {types_d, pos_d, vel_d, force_d, m->nlR.p, m->nlA.p, m->cell_start.p, m->thermo.p,
-                              m->partial.p, m->rec_s.p, m->phi.p, m->e.p, m->cur, p.dev.p, m->counters.p,
-                              m->totals.p, m->acc.p};
+        const void* ptrs[] = {types_d, pos_d, vel_d, force_d, m->cur, p.dev.p};
         put(ptrs, sizeof ptrs);
+        put_workspace_ptrs(key, m);
         put(&n, sizeof n);
         put(&g, sizeof g);
         put(&dt, sizeof dt);
@@ -1495,7 +1532,8 @@ int nep_destroy(nep_model* m)
     m->timer.destroy();
     Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
                    &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
-                   &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->totals, &m->flags,
+                   &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->gcounters,
+                   &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
                    &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev, &m->noise_d, &m->bussi,
                    &m->md_virial, &m->md_site, &m->heat, &m->heat_rows, &m->acc};
@@ -1936,8 +1974,8 @@ int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, c
 int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force)
 {
     if (!m) return fail(NEP_ERR_ARG, "null model");
-    if ((mb_desc != 2 && mb_desc != 3) || (mb_force < 2 || mb_force > 4))
-        return fail(NEP_ERR_ARG, "kernel variants: descriptor 2 or 3, force 2, 3 or 4");
+    if ((mb_desc != 2 && mb_desc != 3) || (mb_force < 3 || mb_force > 5))
+        return fail(NEP_ERR_ARG, "kernel variants: descriptor 2 or 3, force 3, 4 or 5");
     m->autotune = autotune != 0;
     m->mb_desc = mb_desc;
     m->mb_force = mb_force;
@@ -2052,7 +2090,7 @@ int nep_request_workspace(nep_model* const* models, int n_models, int model, int
     per_particle += 4 + 24 + 24 + 72 + 8;          // host-call staging: types, positions, F, W, U
     const size_t per_cell = 16;                    // count, local prefix, fill, start
     const size_t items = ((size_t)n + kBlock - 1) / kBlock;
-    const size_t per_item = 10 * sizeof(double) + sizeof(WorkItem);
+    const size_t per_item = 10 * sizeof(double) + sizeof(WorkItem) + sizeof(unsigned int);  // + group counter
     const size_t per_req = sizeof(ReqInfo) + 10 * sizeof(double) + sizeof(unsigned int);
     *bytes = per_particle * n + per_cell * g.ncell + per_item * items + per_req;
     return NEP_OK;
@@ -2064,8 +2102,9 @@ int nep_workspace_bytes(nep_model* m, size_t* bytes)
     const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
                          &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
                          &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters,
-                         &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d,
-                         &m->force_d, &m->virial_d, &m->site_d, &m->force_tmp, &m->totals_tmp, &m->plan.dev,
+                         &m->gcounters, &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->types_d,
+                         &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d, &m->site_d, &m->force_tmp,
+                         &m->totals_tmp, &m->plan.dev,
                          &m->noise_d, &m->bussi, &m->md_virial, &m->md_site, &m->heat, &m->heat_rows, &m->acc};
     size_t t = 0;
     for (const Buf* b : bufs) t += b->p ? b->cap : 0;
@@ -2128,6 +2167,7 @@ constexpr int kStaticMaxNA = phi_pad(5);  // padded n_A of the compiled shapes
 constexpr int kStaticMaxT = 4;           // particle types of the model
 constexpr int kStaticMaxKRP = 12;        // padded K_R
 constexpr int kStaticMaxItems = (kStaticMaxN + kBlock - 1) / kBlock;
+static_assert(kStaticMaxItems <= kGroup, "the static path's totals use one item group");
 constexpr size_t kStaticTableBytes = 2048;  // one request, its work items, one model
 constexpr int kStaticMaxDevices = 64;
 // the counts, the request, its work items and one model table must fit the table region
@@ -2306,6 +2346,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.wsum = sizeof(real) == 4 ? acc_wsum(base + L.acc, n) : nullptr;
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
+    a.gcounter = counters + 1;  // one group: at most kStaticMaxN / 128 <= 32 work items
     a.totals = totals;
     e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur, nullptr,
                               m->mb_desc, m->mb_force);

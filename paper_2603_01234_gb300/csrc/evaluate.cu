@@ -883,65 +883,103 @@ __device__ __forceinline__ real warp_sum(real v)
     return v;
 }
 
-// FP64 block partials of (E, W[9]); the last block of a request sums its request's
-// partials into totals[req]: every thread takes a fixed stride of the items
-// (counted from the request's first, so a request sums alike alone or in a batch),
-// then a fixed tree combines the threads, so the result does not depend on timing.
-template <int BS>
-__device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const WorkItem& it, const ReqInfo& rq,
-                                              double* partial, unsigned int* counter, double* totals)
+// FP64 sums of (E, W[9]) over each request, in a fixed order whatever the timing:
+//   1. each block sums its particles: the 10 values of its threads go to shared
+//      memory, 80 threads sum 16 each (value k = t / 8, a stride-8 subset), then 10
+//      threads sum the 8 parts, into partial[item];
+//   2. the last block of each group of kGroup consecutive items of a request (counted
+//      from the request's first item) sums the group's block partials and writes the
+//      group sum over the group's first partial;
+//   3. the last group of the request sums the group sums into totals[req].
+// The summing threads take fixed subsets, so a request sums alike alone or in a
+// batch.  Spreading the sums over the groups' last blocks keeps the serial tail of
+// the kernel (FP64 arithmetic is scarce on this part) to two short passes.
+
+// out[k] = sum over b < nb of src[b * 10 + k] (L2 reads: written by other blocks),
+// with 120 threads in a fixed order; the result is valid in threads < 10
+__device__ __forceinline__ double sum_partials(const double* src, int nb, int stride_items, double (&part)[10][12])
 {
-    __shared__ double red[BS / 32][10];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        const double s = warp_sum(v[k]);
-        if (lane == 0) red[warp][k] = s;
+    const int t = threadIdx.x;
+    if (t < 120) {
+        const int k = t % 10, q = t / 10;
+        double s = 0.0;
+#pragma unroll 4
+        for (int b = q; b < nb; b += 12) s += __ldcg(src + (size_t)b * stride_items * 10 + k);
+        part[k][q] = s;
     }
     __syncthreads();
-    if (threadIdx.x < 10) {
+    double s = 0.0;
+    if (t < 10) {
+#pragma unroll
+        for (int q = 0; q < 12; ++q) s += part[t][q];
+    }
+    return s;
+}
+
+template <int BS>
+__device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const WorkItem& it, const ReqInfo& rq,
+                                              double* partial, unsigned int* gcounter, unsigned int* counter,
+                                              double* totals)
+{
+    static_assert(BS % 8 == 0 && BS >= 120, "block size");
+    __shared__ double red[10][BS + 8];  // row stride 2 words mod 32 apart: 2-way for 64-bit loads
+    __shared__ double part[10][12];
+    __shared__ bool last;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) red[k][t] = v[k];
+    __syncthreads();
+    if (t < 80) {
+        const int k = t >> 3, q = t & 7;
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < BS / 32; ++w) s += red[w][threadIdx.x];
-        partial[(size_t)item * 10 + threadIdx.x] = s;
+        for (int j = 0; j < BS / 8; ++j) s += red[k][8 * j + q];
+        part[k][q] = s;
+    }
+    __syncthreads();
+    if (t < 10) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += part[t][q];
+        partial[(size_t)item * 10 + t] = s;
     }
     __threadfence();
     __syncthreads();
-    const unsigned int n_items = (unsigned int)(rq.item_end - rq.item_begin);
-    if (threadIdx.x == 0) last = (atomicAdd(&counter[it.req], 1u) == n_items - 1);
+    const int rel = item - rq.item_begin;
+    const int n_items = rq.item_end - rq.item_begin;
+    const int g0 = rq.item_begin + rel / kGroup * kGroup;  // the group's first item
+    const int gn = min(kGroup, rq.item_end - g0);
+    if (t == 0) last = (atomicAdd(&gcounter[g0], 1u) == (unsigned int)gn - 1u);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double s[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) s[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)n_items; b += BS) {
-        const double* q = partial + (size_t)(rq.item_begin + b) * 10;
-#pragma unroll
-        for (int k = 0; k < 10; ++k) s[k] += __ldcg(q + k);  // L2: written by other blocks
+    const double gs = sum_partials(partial + (size_t)g0 * 10, gn, 1, part);
+    const int ng = (n_items + kGroup - 1) / kGroup;
+    if (ng == 1) {  // one group: its sum is the total
+        if (t < 10) totals[(size_t)it.req * 10 + t] = gs;
+        if (t == 0) gcounter[g0] = 0u;
+        return;
     }
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        const double w = warp_sum(s[k]);
-        if (lane == 0) red[warp][k] = w;
-    }
+    if (t < 10) partial[(size_t)g0 * 10 + t] = gs;  // over the group's first partial
+    if (t == 0) gcounter[g0] = 0u;
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x < 10) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < BS / 32; ++w) t += red[w][threadIdx.x];
-        totals[(size_t)it.req * 10 + threadIdx.x] = t;
-    }
-    if (threadIdx.x == 0) counter[it.req] = 0u;
+    if (t == 0) last = (atomicAdd(&counter[it.req], 1u) == (unsigned int)ng - 1u);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double ts = sum_partials(partial + (size_t)rq.item_begin * 10, ng, kGroup, part);
+    if (t < 10) totals[(size_t)it.req * 10 + t] = ts;
+    if (t == 0) counter[it.req] = 0u;
 }
-
 
 // Radial pairs of slots s0, s0 + ds, ... :
 //   f_ij = (e_i^{t_j} . f') u,  f_ji = -(e_j^{t_i} . f') u,  F_i += f_ij - f_ji,
 //   W_i += r_ij (x) f_ji.  The pair body has no branch, so the scheduler can
-//   interleave the four bodies of each walk step.
-template <typename real, int NR, int KR>
+//   interleave the four bodies of each walk step.  f_ji is parallel to r_ij, so the
+//   radial terms of W_i are symmetric: with SYM, c.W[0..5] holds xx, yy, zz, xy, xz,
+//   yz of the radial part alone (6 products per pair instead of 9).
+template <typename real, int NR, int KR, bool SYM = false>
 __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
                                              ForceCtx<real, (KR + 3) & ~3>& c, int s0, int ds)
 {
@@ -973,12 +1011,23 @@ __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real
         c.F[0] += fs * ux;
         c.F[1] += fs * uy;
         c.F[2] += fs * uz;
-        const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
+        if constexpr (SYM) {
+            const real w = bj * inv_r;
+            const real wx = w * dx, wy = w * dy, wz = w * dz;
+            c.W[0] -= wx * dx;
+            c.W[1] -= wy * dy;
+            c.W[2] -= wz * dz;
+            c.W[3] -= wx * dy;
+            c.W[4] -= wx * dz;
+            c.W[5] -= wy * dz;
+        } else {
+            const real d[3] = {dx, dy, dz}, u[3] = {ux, uy, uz};
 #pragma unroll
-        for (int p = 0; p < 3; ++p) {
-            const real bd = bj * d[p];
+            for (int p = 0; p < 3; ++p) {
+                const real bd = bj * d[p];
 #pragma unroll
-            for (int q = 0; q < 3; ++q) c.W[3 * p + q] -= bd * u[q];
+                for (int q = 0; q < 3; ++q) c.W[3 * p + q] -= bd * u[q];
+            }
         }
     };
     const uint32_t* nl = a.nlR + (size_t)s0 * a.n + c.i;
@@ -1107,6 +1156,19 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
     }
 }
 
+// The MD step's closing half-kick of particle ui (caller index; lu within its
+// request) from its final force, rounded as the separate kick kernel rounds it.
+template <typename real>
+__device__ __forceinline__ void closing_kick(const EvalArgs<real>& a, const ReqInfo& rq, int ui, int lu,
+                                             const double (&F)[3])
+{
+    const int t = a.kick_types[ui];
+    const double im = a.kick_im.v[t >= 0 && t < kMdMaxTypes ? t : 0];
+    double* v = a.kick_vel + (size_t)3 * rq.begin + lu;
+#pragma unroll
+    for (int p = 0; p < 3; ++p) v[(size_t)p * rq.n] = half_kick(v[(size_t)p * rq.n], a.kick_half_dt, F[p], im);
+}
+
 template <typename real>
 __device__ __forceinline__ void force_outputs(const EvalArgs<real>& a, const ReqInfo& rq, int i, const real* F,
                                               const real* W, double (&tot)[10])
@@ -1117,6 +1179,10 @@ __device__ __forceinline__ void force_outputs(const EvalArgs<real>& a, const Req
     double* fo = a.force + (size_t)3 * rq.begin + lu;
 #pragma unroll
     for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
+    if (a.kick_vel) {
+        double F64[3] = {(double)F[0], (double)F[1], (double)F[2]};
+        closing_kick(a, rq, ui, lu, F64);
+    }
     if (a.virial) {
         double* vo = a.virial + (size_t)9 * rq.begin + lu;
 #pragma unroll
@@ -1163,7 +1229,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
         force_angular_k<real, NA, KA, 0, kNLM>(a, P, off, c);
         force_outputs(a, rq, i, c.F, c.W, tot);
     }
-    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.counter, a.totals);
+    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.gcounter, a.counter, a.totals);
 }
 
 // ---- FP32 form: angular pairs in scatter form inside the descriptor kernel ------
@@ -1281,16 +1347,21 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
         for (int k = 0; k < 3; ++k) c.F[k] = real(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) c.W[k] = real(0);
-        force_radial<real, NR, KR>(a, P, off, c, 0, 1);
+        force_radial<real, NR, KR, true>(a, P, off, c, 0, 1);
+        // the radial virial in full (row-major 3 x 3) from its symmetric part
+        const real Wr[9] = {c.W[0], c.W[3], c.W[4], c.W[3], c.W[1], c.W[5], c.W[4], c.W[5], c.W[2]};
         ulonglong2* line = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
         const ulonglong2 f01 = line[0], f2x = line[1];
         line[0] = line[1] = make_ulonglong2(0ull, 0ull);
         const int ui = a.perm[i];
         const int lu = ui - rq.begin;
         double* fo = a.force + (size_t)3 * rq.begin + lu;
-        fo[0] = fix_value(f01.x) + (double)c.F[0];
-        fo[rq.n] = fix_value(f01.y) + (double)c.F[1];
-        fo[(size_t)2 * rq.n] = fix_value(f2x.x) + (double)c.F[2];
+        double Fi[3] = {fix_value(f01.x) + (double)c.F[0], fix_value(f01.y) + (double)c.F[1],
+                        fix_value(f2x.x) + (double)c.F[2]};
+        fo[0] = Fi[0];
+        fo[rq.n] = Fi[1];
+        fo[(size_t)2 * rq.n] = Fi[2];
+        if (a.kick_vel) closing_kick(a, rq, ui, lu, Fi);
         if (a.virial) {  // W_i: the angular terms its neighbours sent, plus its radial terms
             ulonglong2* wl = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
             double* vo = a.virial + (size_t)9 * rq.begin + lu;
@@ -1298,17 +1369,17 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
             for (int q = 0; q < 5; ++q) {
                 const ulonglong2 v = wl[q];
                 wl[q] = make_ulonglong2(0ull, 0ull);
-                vo[(size_t)(2 * q) * rq.n] = fix_value(v.x) + (double)c.W[2 * q];
-                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = fix_value(v.y) + (double)c.W[2 * q + 1];
+                vo[(size_t)(2 * q) * rq.n] = fix_value(v.x) + (double)Wr[2 * q];
+                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = fix_value(v.y) + (double)Wr[2 * q + 1];
             }
         }
         const real Ui = a.U[i];
         if (a.site) a.site[ui] = (double)Ui;
         tot[0] = (double)Ui;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)a.wsum[(size_t)k * a.n + i] + (double)c.W[k];
+        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)a.wsum[(size_t)k * a.n + i] + (double)Wr[k];
     }
-    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.counter, a.totals);
+    reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.gcounter, a.counter, a.totals);
 }
 
 // ---- shape dispatch -----------------------------------------------------------
@@ -1367,10 +1438,13 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
         cudaError_t e;                                                                           \
         if ((e = set_smem_desc<real, a_, b_, c_, d_, 2>(smem_desc)) != cudaSuccess) return e;    \
         if ((e = set_smem_desc<real, a_, b_, c_, d_, 3>(smem_desc)) != cudaSuccess) return e;    \
-        if ((e = set_smem_force<real, a_, b_, c_, d_, 2>(smem_force)) != cudaSuccess) return e;  \
         if ((e = set_smem_force<real, a_, b_, c_, d_, 3>(smem_force)) != cudaSuccess) return e;  \
-        if constexpr (sizeof(real) == 4) /* K2 also at 4 blocks per SM */                        \
+        if constexpr (sizeof(real) == 4) { /* K2 also at 4 and 5 blocks per SM */                \
             if ((e = set_smem_force<real, a_, b_, c_, d_, 4>(smem_force)) != cudaSuccess) return e; \
+            if ((e = set_smem_force<real, a_, b_, c_, d_, 5>(smem_force)) != cudaSuccess) return e; \
+        } else {                                                                                 \
+            if ((e = set_smem_force<real, a_, b_, c_, d_, 2>(smem_force)) != cudaSuccess) return e; \
+        }                                                                                        \
         return cudaSuccess;                                                                      \
     }
     NEP_SHAPES(NEP_CASE)
@@ -1379,19 +1453,18 @@ cudaError_t evaluate_set_smem(int nR, int nA, int KR, int KA, size_t smem_desc, 
 }
 
 template <typename real, int NR, int NA, int KR, int KA, int MBT>
-void launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_t st, int mb_desc)
+cudaError_t launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_t st, int mb_desc)
 {
     if constexpr (sizeof(real) == 4) {
         if (a.net_bf16) {
-            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 1, MBT, 1><<<nb, kBlock, smem, st>>>(a);
-            else k_descriptor<real, NR, NA, KR, KA, 3, 1, MBT, 1><<<nb, kBlock, smem, st>>>(a);
-        } else {
-            if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 1><<<nb, kBlock, smem, st>>>(a);
-            else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 1><<<nb, kBlock, smem, st>>>(a);
+            if (mb_desc == 2) return launch_k(k_descriptor<real, NR, NA, KR, KA, 2, 1, MBT, 1>, nb, kBlock, smem, st, a);
+            return launch_k(k_descriptor<real, NR, NA, KR, KA, 3, 1, MBT, 1>, nb, kBlock, smem, st, a);
         }
+        if (mb_desc == 2) return launch_k(k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 1>, nb, kBlock, smem, st, a);
+        return launch_k(k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 1>, nb, kBlock, smem, st, a);
     } else {
-        if (mb_desc == 2) k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 0><<<nb, kBlock, smem, st>>>(a);
-        else k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 0><<<nb, kBlock, smem, st>>>(a);
+        if (mb_desc == 2) return launch_k(k_descriptor<real, NR, NA, KR, KA, 2, 0, MBT, 0>, nb, kBlock, smem, st, a);
+        return launch_k(k_descriptor<real, NR, NA, KR, KA, 3, 0, MBT, 0>, nb, kBlock, smem, st, a);
     }
 }
 
@@ -1405,20 +1478,18 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
     }
 #define NEP_CASE(a_, b_, c_, d_)                                                                          \
     if (nR == a_ && nA == b_ && KR == c_ && KA == d_) {                                                   \
-        if (a.many_body)                                                                                  \
-            launch_descriptor<real, a_, b_, c_, d_, 1>(a, nb, smem_desc, st, mb_desc);                    \
-        else                                                                                              \
-            launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc);                    \
-        if (mid) cudaEventRecord(mid, st);                                                                \
+        cudaError_t e = a.many_body ? launch_descriptor<real, a_, b_, c_, d_, 1>(a, nb, smem_desc, st, mb_desc) \
+                                    : launch_descriptor<real, a_, b_, c_, d_, 0>(a, nb, smem_desc, st, mb_desc); \
+        if (e != cudaSuccess) return e;                                                                   \
+        if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;                               \
         if constexpr (sizeof(real) == 4) {                                                                \
-            if (mb_force == 4) k_force_radial<real, a_, c_, 4><<<nb, kBlock, smem_force, st>>>(a);        \
-            else if (mb_force == 3) k_force_radial<real, a_, c_, 3><<<nb, kBlock, smem_force, st>>>(a);   \
-            else k_force_radial<real, a_, c_, 2><<<nb, kBlock, smem_force, st>>>(a);                      \
+            if (mb_force == 5) return launch_k(k_force_radial<real, a_, c_, 5>, nb, kBlock, smem_force, st, a); \
+            if (mb_force == 4) return launch_k(k_force_radial<real, a_, c_, 4>, nb, kBlock, smem_force, st, a); \
+            return launch_k(k_force_radial<real, a_, c_, 3>, nb, kBlock, smem_force, st, a);           \
         } else {                                                                                          \
-            if (mb_force == 3) k_force<real, a_, b_, c_, d_, 3><<<nb, kBlock, smem_force, st>>>(a);       \
-            else k_force<real, a_, b_, c_, d_, 2><<<nb, kBlock, smem_force, st>>>(a);                     \
+            if (mb_force == 3) return launch_k(k_force<real, a_, b_, c_, d_, 3>, nb, kBlock, smem_force, st, a); \
+            return launch_k(k_force<real, a_, b_, c_, d_, 2>, nb, kBlock, smem_force, st, a);          \
         }                                                                                                 \
-        return cudaGetLastError();                                                                        \
     }
     NEP_SHAPES(NEP_CASE)
 #undef NEP_CASE

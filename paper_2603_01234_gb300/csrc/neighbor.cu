@@ -3,7 +3,7 @@
 // Per batch of configurations (requests), each with its own box and cell grid:
 //   k_bin        wrap periodic axes, bin every particle into a cell, store its
 //                cell-relative position (FP32 or FP64) and count cell members
-//   k_scan_*     exclusive scan of the cell counts (two levels)
+//   k_scan       exclusive scan of the cell counts (two levels, one launch)
 //   k_scatter    counting-sort scatter of particle indices into cell order
 //   k_cell_rank  order each cell's members by caller index (deterministic order)
 //                and gather the records into cell order
@@ -23,17 +23,19 @@ __device__ __forceinline__ void bin_one(const ReqInfo& q, int i, double (&x)[3],
     const CellGrid& g = q.g;
     int c3[3];
     real xr[3];
+    // FP64 work is kept to what the result needs (the part's FP64 rate is low): the
+    // floor and the clamp are one rounding conversion and integer compares, and the
+    // cell-relative position one FMA
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        if (!isfinite(x[a])) {
+        if (!finite_bits(x[a])) {
             atomicOr(err, 1);
             x[a] = 0.0;
         }
         if (g.pbc[a]) x[a] = wrap_periodic(x[a], g.box[a]);
-        const double cf = floor(x[a] * g.inv_len[a]);
-        int c = cf < 0.0 ? 0 : (cf >= (double)g.nc[a] ? g.nc[a] - 1 : (int)cf);
+        const int c = min(max(__double2int_rd(x[a] * g.inv_len[a]), 0), g.nc[a] - 1);  // saturating floor
         c3[a] = c;
-        xr[a] = (real)(x[a] - (double)c * g.len[a]);
+        xr[a] = (real)fma(-(double)c, g.len[a], x[a]);
     }
     if (t < 0 || t >= n_types) {
         atomicOr(err, 2);
@@ -118,79 +120,16 @@ cudaError_t launch_kick_drift_bin(const PlanCounts* counts, int items_cap, const
                                   int* cell_count, int* err, cudaStream_t st)
 {
     if (items_cap < 1 || n_kicks < 1 || n_kicks > 2) return cudaErrorInvalidValue;
-    k_kick_drift_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, types, inv_m_acc, n_kicks,
-                                                         half_dt, dt, pos, vel, force, cell_of, rec_user, cell_count,
-                                                         err);
-    return cudaGetLastError();
+    return launch_k(k_kick_drift_bin<real>, items_cap, kBlock, 0, st, counts, items, reqs, models, types, inv_m_acc,
+                      n_kicks, half_dt, dt, pos, vel, force, cell_of, rec_user, cell_count, err);
 }
 
-// Block-local exclusive scan of kScanItems counts (4 per thread, 1024 threads),
-// blocks striding over the cells.  The counters it reads (cell counts and the
-// scatter's fill counters) are cleared here for the next build.
-__global__ void __launch_bounds__(1024) k_scan_local(const PlanCounts* __restrict__ pc, int* __restrict__ count,
-                                                     int* __restrict__ local, int* __restrict__ block_sum,
-                                                     int* __restrict__ fill)
+// Exclusive scan of v[0..4) over a block of 1024 threads (4 values per thread);
+// returns the thread's first exclusive prefix and the block total in *total.
+__device__ __forceinline__ int block_scan4(const int (&v)[4], int* warp_tot, int* total)
 {
-    __shared__ int warp_tot[32];
-    const int ncell = pc->ncell;
-    const int nb = (ncell + kScanItems - 1) / kScanItems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int blk = blockIdx.x; blk < nb; blk += gridDim.x) {
-        const int base = blk * kScanItems + threadIdx.x * 4;
-        int v[4], s = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = 0;
-            if (base + k < ncell) {
-                v[k] = count[base + k];
-                count[base + k] = 0;
-                fill[base + k] = 0;
-            }
-            s += v[k];
-        }
-        int incl = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) warp_tot[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int w = warp_tot[lane];
-            int wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
-            if (lane == 31) block_sum[blk] = wi;
-        }
-        __syncthreads();
-        int run = warp_tot[warp] + incl - s;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (base + k < ncell) local[base + k] = run;
-            run += v[k];
-        }
-        __syncthreads();  // warp_tot is reused by the next block of cells
-    }
-}
-
-// Exclusive scan of the block sums in place (one block; nb <= 4096).
-__global__ void __launch_bounds__(1024) k_scan_top(const PlanCounts* __restrict__ pc, int* __restrict__ block_sum)
-{
-    __shared__ int warp_tot[32];
-    const int nb = (pc->ncell + kScanItems - 1) / kScanItems;
-    const int base = threadIdx.x * 4;
-    int v[4], s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = (base + k < nb) ? block_sum[base + k] : 0;
-        s += v[k];
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s = v[0] + v[1] + v[2] + v[3];
     int incl = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -207,15 +146,69 @@ __global__ void __launch_bounds__(1024) k_scan_top(const PlanCounts* __restrict_
             int y = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += y;
         }
-        warp_tot[lane] = wi - w;
+        warp_tot[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) warp_tot[32] = wi;
     }
     __syncthreads();
-    int run = warp_tot[warp] + incl - s;
+    const int run = warp_tot[warp] + incl - s;
+    *total = warp_tot[32];
+    __syncthreads();  // warp_tot is reused by the caller's next scan
+    return run;
+}
+
+// Two-level exclusive scan of the cell counts in one launch.  Each block scans
+// kScanItems counts (4 per thread, 1024 threads) into local[] and its total into
+// block_sum[blk]; the last block to finish (a counter at block_sum[kScanItems],
+// self-resetting) scans the block totals in place (nb <= kScanItems).  The counters
+// it reads (cell counts and the scatter's fill counters) are cleared here for the
+// next build.
+__global__ void __launch_bounds__(1024) k_scan(const PlanCounts* __restrict__ pc, int* __restrict__ count,
+                                               int* __restrict__ local, int* __restrict__ block_sum,
+                                               int* __restrict__ fill)
+{
+    __shared__ int warp_tot[33];
+    __shared__ bool last;
+    const int ncell = pc->ncell;
+    const int nb = (ncell + kScanItems - 1) / kScanItems;
+    for (int blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+        const int base = blk * kScanItems + threadIdx.x * 4;
+        int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = 0;
+            if (base + k < ncell) {
+                v[k] = count[base + k];
+                count[base + k] = 0;
+                fill[base + k] = 0;
+            }
+        }
+        int total;
+        int run = block_scan4(v, warp_tot, &total);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < ncell) local[base + k] = run;
+            run += v[k];
+        }
+        if (threadIdx.x == 0) block_sum[blk] = total;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&block_sum[kScanItems], 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int base = threadIdx.x * 4;
+    int v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (base + k < nb) ? __ldcg(block_sum + base + k) : 0;
+    int total;
+    int run = block_scan4(v, warp_tot, &total);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         if (base + k < nb) block_sum[base + k] = run;
         run += v[k];
     }
+    if (threadIdx.x == 0) block_sum[kScanItems] = 0;
 }
 
 // Counting-sort scatter (thread per particle, arbitrary order within a cell) and the
@@ -276,18 +269,21 @@ cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap
     if (zero_counts) {
         if ((e = cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(cell_fill, 0, sizeof(int) * ncell_cap, st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(block_off + kScanItems, 0, sizeof(int), st)) != cudaSuccess) return e;
     }
-    if (!skip_bin)
-        k_bin<real><<<items_cap, kBlock, 0, st>>>(counts, items, reqs, models, pos, types, cell_of, rec_user,
-                                                  cell_count, err);
-    k_scan_local<<<nb_scan, 1024, 0, st>>>(counts, cell_count, cell_start_local, block_off, cell_fill);
-    k_scan_top<<<1, 1024, 0, st>>>(counts, block_off);
+    if (!skip_bin &&
+        (e = launch_k(k_bin<real>, items_cap, kBlock, 0, st, counts, items, reqs, models, pos, types, cell_of,
+                        rec_user, cell_count, err)) != cudaSuccess)
+        return e;
+    if ((e = launch_k(k_scan, nb_scan, 1024, 0, st, counts, cell_count, cell_start_local, block_off, cell_fill)) !=
+        cudaSuccess)
+        return e;
     const int nt = (n_cap > ncell_cap + 1 ? n_cap : ncell_cap + 1);
-    k_scatter<<<(nt + kBlock - 1) / kBlock, kBlock, 0, st>>>(counts, cell_of, cell_start_local, block_off, cell_fill,
-                                                              perm_tmp, cell_start);
-    k_cell_rank<real><<<(n_cap + kBlock - 1) / kBlock, kBlock, 0, st>>>(counts, cell_of, cell_start, perm_tmp, perm,
-                                                                        cell_s, rec_user, rec_sorted);
-    return cudaGetLastError();
+    if ((e = launch_k(k_scatter, (nt + kBlock - 1) / kBlock, kBlock, 0, st, counts, cell_of, cell_start_local,
+                        block_off, cell_fill, perm_tmp, cell_start)) != cudaSuccess)
+        return e;
+    return launch_k(k_cell_rank<real>, (n_cap + kBlock - 1) / kBlock, kBlock, 0, st, counts, cell_of, cell_start,
+                      perm_tmp, perm, cell_s, rec_user, rec_sorted);
 }
 
 // One thread per sorted particle i: scan the cells at offsets [-S, S]^3 from i's
@@ -423,8 +419,7 @@ cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t 
     // the kernel indexes the slot-major lists with 32-bit slot * n + i
     if ((unsigned long long)(a.mnR > a.mnA ? a.mnR : a.mnA) * (unsigned long long)a.n > (1ull << 32))
         return cudaErrorInvalidValue;
-    k_neighbors<real><<<items_cap, kBlock, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(k_neighbors<real>, items_cap, kBlock, smem, st, a);
 }
 
 #define NEP_INSTANTIATE(real)                                                                                   \

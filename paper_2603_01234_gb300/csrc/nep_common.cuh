@@ -12,7 +12,24 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace nep {
+
+// Launch helper: the kernels of the evaluation and MD pipeline are launched
+// through cudaLaunchKernelEx, which returns launch errors directly.
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*kernel)(P...), int grid, int block, size_t smem, cudaStream_t st,
+                              A&&... args)
+{
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3((unsigned)grid);
+    c.blockDim = dim3((unsigned)block);
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    c.numAttrs = 0;
+    return cudaLaunchKernelEx(&c, kernel, std::forward<A>(args)...);
+}
 
 // A neighbour entry packs the sorted index j (low 23 bits) and the cell offset
 // (dx, dy, dz) in [-2, 2]^3 of j's cell relative to i's cell (3 bits each).
@@ -101,12 +118,25 @@ struct CellGrid {
 // Wrap onto a periodic axis of length L: positions already in [0, L) are kept;
 // others become x - L floor(x / L), and a result that rounds to L (or below 0)
 // becomes 0.  Moving particles leave the box rarely, so the FP64 division (slow
-// on this GPU) runs only for the few outside.
+// on this GPU) runs only for the few outside.  On the device the range test
+// compares bit patterns: for L > 0, 0 <= x < L exactly when x's bits, read as an
+// unsigned integer, are below L's (negative x, -0 and NaN have larger patterns),
+// which keeps the test off the FP64 pipe.
 __host__ __device__ inline double wrap_periodic(double x, double L)
 {
+#ifdef __CUDA_ARCH__
+    if ((unsigned long long)__double_as_longlong(x) < (unsigned long long)__double_as_longlong(L)) return x;
+#else
     if (x >= 0.0 && x < L) return x;
+#endif
     x = x - L * floor(x / L);
     return (x >= L || x < 0.0) ? 0.0 : x;
+}
+
+// x is neither infinite nor NaN (exponent bits not all set), by integer test
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
 }
 
 // Per-type values passed by value to the integration kernels (at most 16 types).
@@ -188,6 +218,9 @@ struct NeighborArgs {
     unsigned long long* accW;   // FP32 form with per-particle virials: [n][12] fixed-point virial lines (or null)
 };
 
+// Work items per group of the totals' two-level reduction (see reduce_totals).
+constexpr int kGroup = 32;
+
 template <typename real>
 struct EvalArgs {
     int n, mnR, mnA;            // n: the list / array stride (particle capacity)
@@ -216,8 +249,18 @@ struct EvalArgs {
                                 // same rules; used only when virial is non-null
     float* wsum;                // FP32 form: [9][n] each thread's angular virial sum (for the totals)
     double* partial;            // [items][10] per work item (E, W[9])
-    unsigned int* counter;      // [requests] last-block counters (self-resetting)
+    unsigned int* counter;      // [requests] last-group counters (self-resetting)
+    unsigned int* gcounter;     // [items] last-block counters of the item groups, at each
+                                // group's first item (self-resetting)
     double* totals;             // [requests][10]: E, W[9]
+    // MD: the step's closing half-kick applied by the output pass as soon as F_i is
+    // final, v_i <- half_kick(v_i, kick_half_dt, F_i, kick_im[t_i]), with the same
+    // rounding as a separate kick kernel; kick_vel per request [3][n_r] blocks, or
+    // null (no kick).  kick_types is indexed by caller index.
+    double* kick_vel = nullptr;
+    const int* kick_types = nullptr;
+    double kick_half_dt = 0.0;
+    TypeTable kick_im = {};
 };
 
 // ---- host-side launchers (defined in the .cu files) ----
