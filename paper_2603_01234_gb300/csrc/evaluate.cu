@@ -96,6 +96,30 @@ __device__ __forceinline__ void basis(real r, real inv_rc, real inv_lo, real* f)
     }
 }
 
+// Pair sums of the basis, split as f_k = (f_c/2) T_k + f_c/2: acc[k] += (f_c/2) T_k
+// and hs += f_c/2, so that sum_j f_k = acc[k] + hs (one FMA per term instead of a
+// product and an add).
+template <typename real, int K>
+__device__ __forceinline__ void basis_acc(real r, real inv_rc, real inv_lo, real (&acc)[K], real& hs)
+{
+    const real xr = scaled_r(r, inv_rc, inv_lo);
+    const real hf = cut_half(xr);  // f_c / 2
+    const real s = xr - real(1);
+    const real x = real(2) * s * s - real(1);
+    const real x2 = x + x;
+    real t0 = real(1), t1 = x;
+    hs += hf;
+    acc[0] += hf;
+    if (K > 1) acc[1] = fma(hf, x, acc[1]);
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        const real t2 = x2 * t1 - t0;
+        acc[k] = fma(hf, t2, acc[k]);
+        t0 = t1;
+        t1 = t2;
+    }
+}
+
 // f_k and df_k/dr:  df_k = 1/2 [T_k'(x) x'(r) f_c + (T_k + 1) f_c'],
 // with T'_{k+1} = 2 T_k + 2 x T'_k - T'_{k-1}.
 template <typename real, int K>
@@ -613,11 +637,13 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
     if (T == 1) {
         // one pair type: q_n = sum_k c_nk (sum_j f_k(r_ij)), contracted once per bead;
         // the pair sums are kept as four partial sums (see walk4p)
-        real fp[4][KR];
+        real fp[4][KR], hp[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
+        for (int p = 0; p < 4; ++p) {
+            hp[p] = real(0);
 #pragma unroll
             for (int k = 0; k < KR; ++k) fp[p][k] = real(0);
+        }
         const real inv_rc = P[off.rcRi], inv_lo = P[off.rcRl];
         walk4p(a.nlR + i, (size_t)a.n, cR, [&](uint32_t e, int p) {
             const PosRec<real> rj = a.rec[e & kJMask];
@@ -625,14 +651,12 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
             pair_vec(len, ri, rj, e, dx, dy, dz);
             const real r2 = dx * dx + dy * dy + dz * dz;
             const real r = r2 * rsqrt_r(r2);
-            real f[KR];
-            basis<real, KR>(r, inv_rc, inv_lo, f);
-#pragma unroll
-            for (int k = 0; k < KR; ++k) fp[p][k] += f[k];
+            basis_acc<real, KR>(r, inv_rc, inv_lo, fp[p], hp[p]);
         });
+        const real hs = (hp[0] + hp[1]) + (hp[2] + hp[3]);
         real fs[KR];
 #pragma unroll
-        for (int k = 0; k < KR; ++k) fs[k] = (fp[0][k] + fp[1][k]) + (fp[2][k] + fp[3][k]);
+        for (int k = 0; k < KR; ++k) fs[k] = ((fp[0][k] + fp[1][k]) + (fp[2][k] + fp[3][k])) + hs;
         const real* c = P + off.cR;
 #pragma unroll
         for (int nn = 0; nn < NR; ++nn) {
@@ -1238,6 +1262,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
 // in registers; F_j loses it (and W_j gains r_ji (x) f_ij) through the fixed-point
 // atomic adds.  For A = g(r) Y(u) with Y homogeneous of degree l:
 //   dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
+// Summed over the components with G_k = sum_n Phi_nk g_n and dG_k likewise with
+// g_n', Euler's identity for homogeneous polynomials, u . grad Y = l Y, turns the
+// l-weighted sum into a projection:
+//   f_ij = (sum_k dG_k Y_k) u + (ga - (u . ga) u) / r,   ga = sum_k G_k grad Y_k,
+// so no per-component degree factor is needed.
 template <typename real, int NA, int KA, typename Ctx>
 __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
                                                       const real (&Phi)[NA][24], Ctx& c, bool per_bead)
@@ -1274,7 +1303,7 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
         }
         const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
         const ShMono<real> mono = sh_mono(ux, uy, uz);
-        real sr = real(0);
+        real D = real(0);
         real ga[3] = {real(0), real(0), real(0)};
 #pragma unroll
         for (int k = 0; k < kNLM; ++k) {
@@ -1286,11 +1315,12 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
             }
             real y, gx, gy, gz;
             sh_val_grad(k, mono, y, gx, gy, gz);
-            sr += (dG - real(l_of(k)) * inv_r * G) * y;
+            D += dG * y;
             ga[0] += G * gx;
             ga[1] += G * gy;
             ga[2] += G * gz;
         }
+        const real sr = D - (ux * ga[0] + uy * ga[1] + uz * ga[2]) * inv_r;
         const real fij[3] = {sr * ux + ga[0] * inv_r, sr * uy + ga[1] * inv_r, sr * uz + ga[2] * inv_r};
         unsigned long long* acc_j = a.accF + (size_t)j * 4;
 #pragma unroll
