@@ -583,11 +583,15 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(system),
             "ns_per_day": (1000.0 / ms_step) * DT_FS * 0.0864,
-            "gpu_launches": 10 * args.steps,  # per step: kick/drift, 5 cell-build, neighbours, descriptor+angular forces, radial forces+outputs, kick
+            # per step: kick+drift+binning, scan, scatter, in-cell ranking, neighbours,
+            # descriptor+network+angular forces, radial forces+outputs+closing kick
+            "gpu_launches": 7 * args.steps,
             "stages_ms_per_step": {k: v / max(1, tsteps) for k, v in stages.items()},
             "stages_how": "separate pass of the same number of steps, eager launches, CUDA events between "
-                          "stages on the launch stream, L2 flushed before each step; descriptor_network is the "
-                          "descriptor + network + angular-force kernel, force_virial the radial-force + output kernel",
+                          "stages on the launch stream, L2 flushed before each step; kick_drift is the opening "
+                          "kick + drift + cell binning, descriptor_network the descriptor + network + "
+                          "angular-force kernel, force_virial the radial-force + output kernel (with the closing "
+                          "kick), kick_sample what follows it (thermostat, thermo row; empty here)",
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "kernel_variants": {"descriptor_blocks_per_sm": tuning[0], "force_blocks_per_sm": tuning[1],
                                 "chosen_by": "fixed (--tuning)" if args.tuning else "autotuner"},

@@ -314,8 +314,11 @@ int nep_set_timing(nep_model* m, int enable);
 
 /*
  * Summed device time in ms of each stage over the timed steps, waiting for the
- * pending events first:  stage_ms[6] = kick+drift, cell build, neighbour lists,
- * descriptor+network, force+virial, kick(+sample);  steps = steps timed.
+ * pending events first:  stage_ms[6] = opening kick+drift+binning, rest of the
+ * cell build, neighbour lists, descriptor+network+angular forces, radial
+ * forces+outputs (with the closing kick unless the HNEMD force is on), and what
+ * follows (separate kick, thermostat, heat current, thermo row);  steps = steps
+ * timed.
  */
 int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
 
