@@ -526,7 +526,7 @@ def run_ours(args):
     configs = None
     if not args.quick and not args.no_configs and world == 1:
         sm_cfg = (peaks0 or {}).get("sm_max_mhz") or 2070.0
-        configs = config_legs(dev, n_sms, sm_cfg)
+        configs = config_legs(dev, n_sms, sm_cfg, cpu=not args.no_cpu)
     serve = None
     if not args.quick and not args.no_serve and rank == 0:
         serve = serving_leg(local)
@@ -714,22 +714,43 @@ def drift_leg(model, system, vel0, precision, steps, dt, dev, every=10):
             "etot_fluct_rms_eV_per_bead": float(np.sqrt(np.mean(resid ** 2))) / system.n}
 
 
-def config_legs(dev, n_sms, sm_max):
+def cpu_sample_leg(model, system, what):
+    """The oracle (as it stands) on the host cores: one full FP64 velocity-Verlet
+    step of `system`, a bounded sample of a configuration (per bead-step)."""
+    vel = inputs.maxwell_boltzmann(system, 300.0, seed=7)
+    secs, st, cores = cpu_oracle_run(model, system, vel, 1)
+    return {"value": system.n * st / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": what}
+
+
+def config_legs(dev, n_sms, sm_max, cpu=True):
     """The other configurations at 1 GPU, each a continuous run: 512-bead water in
     FP64 (and FP32 beside it), the 200,000-bead four-type monolayer in FP32 and with
     BF16 hidden-layer weights, and the 1,000,000-particle nanowire over 2,000 steps
     with the box rescaled by 1.001 along x every 100 steps; NVE drift of the 100,000-
-    bead water and of the nanowire in FP32 and FP64."""
+    bead water and of the nanowire in FP32 and FP64.  With cpu, each configuration's
+    record carries the oracle timed on a bounded sample of it (one step of the whole
+    512-bead box; of an 8,000-bead monolayer and a 20,000-particle nanowire built the
+    same way)."""
     out = {}
     model, system, vel = workload("water512")
     out["water512_fp64"] = md_leg("water512", model, system, vel, "fp64", 1000, 10.0, dev, n_sms, sm_max)
     out["water512_fp32"] = md_leg("water512", model, system, vel, "fp32", 1000, 10.0, dev, n_sms, sm_max)
+    if cpu:
+        out["water512_fp64"]["cpu_baseline"] = cpu_sample_leg(model, system, "1 full step of the 512-bead box")
     model, system, vel = workload("monolayer200k")
     out["monolayer200k_fp32"] = md_leg("monolayer200k", model, system, vel, "fp32", 500, 20.0, dev, n_sms, sm_max)
     out["monolayer200k_bf16"] = md_leg("monolayer200k", model, system, vel, "bf16", 500, 20.0, dev, n_sms, sm_max)
+    if cpu:
+        sample = inputs.monolayer(50, 40, seed=1002)
+        out["monolayer200k_fp32"]["cpu_baseline"] = cpu_sample_leg(
+            model, sample, f"1 full step of a {sample.n}-bead monolayer built like the 200,000-bead one")
     model, system, vel = workload("nanowire1M")
     out["nanowire1M_fp32_strain"] = md_leg("nanowire1M", model, system, vel, "fp32", 2000, 5.0, dev, n_sms, sm_max,
                                            strain=(0, 1.001), interval=100)
+    if cpu:
+        sample = inputs.nanowire(20_000, seed=1003)
+        out["nanowire1M_fp32_strain"]["cpu_baseline"] = cpu_sample_leg(
+            model, sample, f"1 full step of a {sample.n}-particle nanowire built like the 1,000,000-particle one")
     out["drift"] = {"nanowire1M": [drift_leg(model, system, vel, "fp32", 1000, 5.0, dev),
                                    drift_leg(model, system, vel, "fp64", 200, 5.0, dev)]}
     model, system, vel = workload("water100k")

@@ -966,8 +966,8 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const W
 #pragma unroll
         for (int q = 0; q < 8; ++q) s += part[t][q];
         partial[(size_t)item * 10 + t] = s;
+        __threadfence();  // the writers publish their partials before the count below
     }
-    __threadfence();
     __syncthreads();
     const int rel = item - rq.item_begin;
     const int n_items = rq.item_end - rq.item_begin;
@@ -984,9 +984,11 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const W
         if (t == 0) gcounter[g0] = 0u;
         return;
     }
-    if (t < 10) partial[(size_t)g0 * 10 + t] = gs;  // over the group's first partial
-    if (t == 0) gcounter[g0] = 0u;
-    __threadfence();
+    if (t < 10) {
+        partial[(size_t)g0 * 10 + t] = gs;  // over the group's first partial
+        if (t == 0) gcounter[g0] = 0u;
+        __threadfence();
+    }
     __syncthreads();
     if (t == 0) last = (atomicAdd(&counter[it.req], 1u) == (unsigned int)ng - 1u);
     __syncthreads();
