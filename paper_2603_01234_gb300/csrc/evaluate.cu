@@ -1363,8 +1363,8 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
     const ReqInfo& rq = a.reqs[it.req];
     const ModelDesc<real> md = a.models[rq.model];
     const ParamLayout off = md.off;
-    stage_params(md.params, P, off.n_cut_coef);
     const int i = it.begin + threadIdx.x;
+    stage_params(md.params, P, off.n_cut_coef);
     double tot[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) tot[k] = 0.0;
@@ -1408,8 +1408,10 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
         const real Ui = a.U[i];
         if (a.site) a.site[ui] = (double)Ui;
         tot[0] = (double)Ui;
+        // i's contribution to the virial total: its angular sum plus its radial terms,
+        // added in the working precision and widened once (FP64 arithmetic is scarce)
 #pragma unroll
-        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)a.wsum[(size_t)k * a.n + i] + (double)Wr[k];
+        for (int k = 0; k < 9; ++k) tot[1 + k] = (double)(a.wsum[(size_t)k * a.n + i] + Wr[k]);
     }
     reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.gcounter, a.counter, a.totals);
 }
