@@ -574,14 +574,15 @@ struct ForceCtx {
 // 64-bit fixed-point accumulation (2^-32 units): integer sums do not depend on the
 // order in which atomic adds arrive, so scattered forces stay bitwise reproducible.
 constexpr float kFixScale = 4294967296.0f;  // 2^32 fixed-point units per eV/A (or eV)
-constexpr double kFixUnit = 1.0 / 4294967296.0;
 
 __device__ __forceinline__ void fix_add(unsigned long long* p, float v)
 {
     atomicAdd(p, (unsigned long long)__float2ll_rn(v * kFixScale));
 }
 
-__device__ __forceinline__ double fix_value(unsigned long long v) { return (double)(long long)v * kFixUnit; }
+// A fixed-point sum in FP32, the working precision of the forces (kept off the FP64
+// pipe)
+__device__ __forceinline__ float fix_value_f(unsigned long long v) { return (float)(long long)v * (1.0f / kFixScale); }
 
 __device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
 __device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
@@ -1388,8 +1389,10 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
         const int ui = a.perm[i];
         const int lu = ui - rq.begin;
         double* fo = a.force + (size_t)3 * rq.begin + lu;
-        double Fi[3] = {fix_value(f01.x) + (double)c.F[0], fix_value(f01.y) + (double)c.F[1],
-                        fix_value(f2x.x) + (double)c.F[2]};
+        // F_i: the angular part from the fixed-point line plus the radial part, added in
+        // the working precision and widened once (FP64 arithmetic is scarce)
+        double Fi[3] = {(double)(fix_value_f(f01.x) + c.F[0]), (double)(fix_value_f(f01.y) + c.F[1]),
+                        (double)(fix_value_f(f2x.x) + c.F[2])};
         fo[0] = Fi[0];
         fo[rq.n] = Fi[1];
         fo[(size_t)2 * rq.n] = Fi[2];
@@ -1401,8 +1404,8 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
             for (int q = 0; q < 5; ++q) {
                 const ulonglong2 v = wl[q];
                 wl[q] = make_ulonglong2(0ull, 0ull);
-                vo[(size_t)(2 * q) * rq.n] = fix_value(v.x) + (double)Wr[2 * q];
-                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = fix_value(v.y) + (double)Wr[2 * q + 1];
+                vo[(size_t)(2 * q) * rq.n] = (double)(fix_value_f(v.x) + Wr[2 * q]);
+                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = (double)(fix_value_f(v.y) + Wr[2 * q + 1]);
             }
         }
         const real Ui = a.U[i];
