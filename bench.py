@@ -724,10 +724,11 @@ def cpu_sample_leg(model, system, what):
 
 def config_legs(dev, n_sms, sm_max, cpu=True):
     """The other configurations at 1 GPU, each a continuous run: 512-bead water in
-    FP64 (and FP32 beside it), the 200,000-bead four-type monolayer in FP32 and with
-    BF16 hidden-layer weights, and the 1,000,000-particle nanowire over 2,000 steps
-    with the box rescaled by 1.001 along x every 100 steps; NVE drift of the 100,000-
-    bead water and of the nanowire in FP32 and FP64.  With cpu, each configuration's
+    FP64 (and FP32 beside it), the 200,000-bead four-type monolayer in FP32, with
+    BF16 hidden-layer weights and (20 steps) in FP64, and the 1,000,000-particle
+    nanowire over 2,000 steps with the box rescaled by 1.001 along x every 100 steps
+    (and 10 steps in FP64); NVE drift over 1,000 steps of the 100,000-bead water and
+    of the nanowire in FP32 and FP64.  With cpu, each configuration's
     record carries the oracle timed on a bounded sample of it (one step of the whole
     512-bead box; of an 8,000-bead monolayer and a 20,000-particle nanowire built the
     same way)."""
@@ -740,6 +741,7 @@ def config_legs(dev, n_sms, sm_max, cpu=True):
     model, system, vel = workload("monolayer200k")
     out["monolayer200k_fp32"] = md_leg("monolayer200k", model, system, vel, "fp32", 500, 20.0, dev, n_sms, sm_max)
     out["monolayer200k_bf16"] = md_leg("monolayer200k", model, system, vel, "bf16", 500, 20.0, dev, n_sms, sm_max)
+    out["monolayer200k_fp64"] = md_leg("monolayer200k", model, system, vel, "fp64", 20, 20.0, dev, n_sms, sm_max)
     if cpu:
         sample = inputs.monolayer(50, 40, seed=1002)
         out["monolayer200k_fp32"]["cpu_baseline"] = cpu_sample_leg(
@@ -747,12 +749,13 @@ def config_legs(dev, n_sms, sm_max, cpu=True):
     model, system, vel = workload("nanowire1M")
     out["nanowire1M_fp32_strain"] = md_leg("nanowire1M", model, system, vel, "fp32", 2000, 5.0, dev, n_sms, sm_max,
                                            strain=(0, 1.001), interval=100)
+    out["nanowire1M_fp64"] = md_leg("nanowire1M", model, system, vel, "fp64", 10, 5.0, dev, n_sms, sm_max)
     if cpu:
         sample = inputs.nanowire(20_000, seed=1003)
         out["nanowire1M_fp32_strain"]["cpu_baseline"] = cpu_sample_leg(
             model, sample, f"1 full step of a {sample.n}-particle nanowire built like the 1,000,000-particle one")
     out["drift"] = {"nanowire1M": [drift_leg(model, system, vel, "fp32", 1000, 5.0, dev),
-                                   drift_leg(model, system, vel, "fp64", 200, 5.0, dev)]}
+                                   drift_leg(model, system, vel, "fp64", 1000, 5.0, dev)]}
     model, system, vel = workload("water100k")
     out["drift"]["water100k"] = [drift_leg(model, system, vel, "fp32", 1000, 10.0, dev),
                                  drift_leg(model, system, vel, "fp64", 1000, 10.0, dev)]
