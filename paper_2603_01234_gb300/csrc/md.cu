@@ -1,7 +1,9 @@
 // Velocity-Verlet NVE integration in FP64 (the MD loop in which the potential is
 // evaluated) and the kinetic-energy sample.
-//   (the opening kick, drift and wrap run fused with the cell binning: k_kick_drift_bin)
-//   k_kick         v += dt/2 F/m
+//   (the opening kick, drift and wrap run fused with the cell binning: k_kick_drift_bin;
+//   the closing kick normally runs in the radial-force/output kernel)
+//   k_kick         v += dt/2 F/m, the closing kick when the HNEMD force must be added
+//                  to the forces first
 //   k_sample       E_kin = sum 1/2 m v^2 (FP64, deterministic last-block total) and
 //                  one thermo row (step, E_pot, E_kin, W[9])
 //   k_bussi_ke     E_kin and the stochastic-velocity-rescaling factor (Bussi,
