@@ -315,8 +315,8 @@ def run_ours(args):
     n = system.n
     m = binding.Model(model, "fp32", device=local)
     if args.tuning:  # fixed kernel variants (profiling: ncu's replay would distort the autotuner)
-        mb_d, mb_f = (int(x) for x in args.tuning.split(","))
-        binding.nep_set_tuning(m.h, 0, mb_d, mb_f)
+        tv = [int(x) for x in args.tuning.split(",")]
+        binding.nep_set_tuning(m.h, 0, *tv)
     types = torch.from_numpy(system.types).to(dev)
     pos = torch.from_numpy(system.pos.copy()).to(dev)
     vel = torch.from_numpy(vel0.copy()).to(dev)
@@ -594,6 +594,7 @@ def run_ours(args):
                           "kick), kick_sample what follows it (thermostat, thermo row; empty here)",
             "pairs_per_bead": {"radial": pairs_r / n, "angular": pairs_a / n},
             "kernel_variants": {"descriptor_blocks_per_sm": tuning[0], "force_blocks_per_sm": tuning[1],
+                                "force_walk_chunk": tuning[2],
                                 "chosen_by": "fixed (--tuning)" if args.tuning else "autotuner"},
             "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu, "e2e": e2e,
             "steady_state_graph": steady, "plain_fp64": plain, "bf16_weights": bf16, "many_body": many_body,
@@ -876,8 +877,9 @@ def main():
     ap.add_argument("--workload", default="water100k", choices=sorted(WORKLOADS),
                     help="the metric is quoted on water100k; the others are further configurations")
     ap.add_argument("--drift", action="store_true", help="NVE energy-drift run (1000 steps, FP32 and FP64)")
-    ap.add_argument("--tuning", default=None, help="fix the kernel variants 'D,F' (resident blocks per SM of "
-                                                    "the descriptor and force kernels); default: autotuned")
+    ap.add_argument("--tuning", default=None, help="fix the kernel variants 'D,F[,C]' (resident blocks per SM of "
+                                                    "the descriptor and radial-force kernels, and the radial "
+                                                    "kernel's walk chunk 4 or 8); default: autotuned")
     ap.add_argument("--n-beads", type=int, default=N_BEADS,
                     help="size of the water box (profiling captures only; the metric is quoted at 100000)")
     args = ap.parse_args()

@@ -357,24 +357,27 @@ int nep_compute_static(nep_model* m, int n, const int32_t* types, const double* 
                        double* site_energy, double* force, double* virial);
 
 /*
- * Autotuner.  The FP32 descriptor and force kernels are compiled in variants
- * that keep 2 or 3 (force: 3, 4 or 5) thread blocks resident per SM (a register
- * budget per thread).  nep_autotune evaluates the configuration several times with
- * each variant, times the two kernels separately with CUDA events, and keeps for
- * each kernel the 3-block default unless another variant is at least 5% faster;
- * the first nep_md_step of a new configuration shape (n and cell grid) does the
- * same unless disabled.  All variants give identical results.  Inputs as in
- * nep_compute; the chosen variants are returned (may be NULL).
+ * Autotuner.  The FP32 descriptor kernel is compiled in variants that keep 2 or 3
+ * thread blocks resident per SM, and the radial-force kernel in variants that keep
+ * 3, 4 or 5 resident (a register budget per thread) and walk the neighbour list in
+ * groups of 4 or 8 entries (the next group's entries load while the current group
+ * is evaluated).  nep_autotune evaluates the configuration several times with each
+ * variant, times the two kernels separately with CUDA events, and keeps for each
+ * kernel its default (3 blocks; groups of 4) unless another variant is at least 5%
+ * faster; the first nep_md_step of a new configuration shape (n and cell grid) does
+ * the same unless disabled.  All variants give identical results.  Inputs as in
+ * nep_compute; the chosen variants are returned (any output may be NULL).
  */
 int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
-                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force);
+                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force, int* chunk);
 
-/* Set the variants (descriptor 2 or 3, force 3, 4 or 5) and whether MD calls tune
- * automatically (1/0); other values give NEP_ERR_ARG. */
-int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force);
+/* Set the variants (descriptor 2 or 3 blocks per SM; radial force 3, 4 or 5 blocks
+ * per SM and chunk 4 or 8) and whether MD calls tune automatically (1/0); other
+ * values give NEP_ERR_ARG. */
+int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force, int chunk);
 
 /* The variants in use. */
-int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force);
+int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force, int* chunk);
 
 /* Current neighbour-list capacities (entries per particle). */
 int nep_get_capacity(nep_model* m, int* radial, int* angular);

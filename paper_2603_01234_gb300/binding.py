@@ -108,11 +108,11 @@ def load(build_if_missing: bool = False):
     lib.nep_cg_map.restype = i
     lib.nep_virial_correction.argtypes = [p, i, i, d]
     lib.nep_virial_correction.restype = i
-    lib.nep_autotune.argtypes = [p, i, p, p, p, p, i, p, C.POINTER(i), C.POINTER(i)]
+    lib.nep_autotune.argtypes = [p, i, p, p, p, p, i, p, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     lib.nep_autotune.restype = i
-    lib.nep_set_tuning.argtypes = [p, i, i, i]
+    lib.nep_set_tuning.argtypes = [p, i, i, i, i]
     lib.nep_set_tuning.restype = i
-    lib.nep_get_tuning.argtypes = [p, C.POINTER(i), C.POINTER(i)]
+    lib.nep_get_tuning.argtypes = [p, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     lib.nep_get_tuning.restype = i
     lib.nep_request_workspace.argtypes = [p, i, i, i, p, p, C.POINTER(C.c_size_t)]
     lib.nep_request_workspace.restype = i
@@ -351,25 +351,27 @@ def nep_virial_correction(virial, n_atoms, n_beads, temperature_K):
 
 
 def nep_autotune(h, types, pos, box, pbc, stream=None):
-    """Tune the kernel variants on this configuration; returns (mb_desc, mb_force)."""
+    """Tune the kernel variants on this configuration; returns (mb_desc, mb_force, chunk)."""
     mem = NEP_DEVICE if _is_torch(pos) and pos.is_cuda else NEP_HOST
     if mem == NEP_HOST:
         types, pos = _host(types, np.int32), _host(pos, np.float64)
-    a, b = C.c_int(), C.c_int()
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
     _check(load().nep_autotune(h, int(types.shape[0]), _ptr(types), _ptr(pos), _ptr(_host(box, np.float64)),
-                               _ptr(_host(pbc, np.int32)), mem, _stream_of(pos, stream), C.byref(a), C.byref(b)),
+                               _ptr(_host(pbc, np.int32)), mem, _stream_of(pos, stream), C.byref(a), C.byref(b),
+                               C.byref(c)),
            "nep_autotune")
-    return a.value, b.value
+    return a.value, b.value, c.value
 
 
-def nep_set_tuning(h, autotune, mb_desc, mb_force):
-    _check(load().nep_set_tuning(h, int(autotune), int(mb_desc), int(mb_force)), "nep_set_tuning")
+def nep_set_tuning(h, autotune, mb_desc, mb_force, chunk=4):
+    _check(load().nep_set_tuning(h, int(autotune), int(mb_desc), int(mb_force), int(chunk)), "nep_set_tuning")
 
 
 def nep_get_tuning(h):
-    a, b = C.c_int(), C.c_int()
-    _check(load().nep_get_tuning(h, C.byref(a), C.byref(b)), "nep_get_tuning")
-    return a.value, b.value
+    """The kernel variants in use: (mb_desc, mb_force, chunk)."""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(load().nep_get_tuning(h, C.byref(a), C.byref(b), C.byref(c)), "nep_get_tuning")
+    return a.value, b.value, c.value
 
 
 def nep_request_workspace(handles, model, n, box, pbc):

@@ -211,6 +211,7 @@ struct nep_model {
     size_t smem_desc = 0, smem_force = 0;
     int mnR = 0, mnA = 0;  // neighbour capacities
     int mb_desc = 3, mb_force = 3;  // register-cap variants of the FP32 evaluation kernels
+    int ch_force = 4;               // neighbour entries per walk group of the FP32 radial kernel
     bool autotune = true;           // tune the variants on the first MD call of a configuration shape
     cudaStream_t st = nullptr;   // internal stream, used when the caller passes NULL
     cudaStream_t cur = nullptr;  // stream of the call in progress
@@ -629,7 +630,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
         for (int t = 0; t < kMdMaxTypes; ++t) a.kick_im.v[t] = t < m->T ? kick->inv_m_acc[t] : 0.0;
     }
     cudaError_t e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, p.items_cap, p.smem_desc,
-                                          p.smem_force, m->cur, mid, m->mb_desc, m->mb_force);
+                                          p.smem_force, m->cur, mid, m->mb_desc, m->mb_force, m->ch_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     return NEP_OK;
 }
@@ -710,7 +711,7 @@ std::vector<unsigned char> eval_graph_key(const nep_model* m, const Plan& p, con
         const unsigned char* b = (const unsigned char*)q;
         key.insert(key.end(), b, b + sz);
     };
-    const int ints[] = {p.n_cap, p.items_cap, p.ncell_cap, p.Tmax, m->mnR, m->mnA, m->mb_desc, m->mb_force,
+    const int ints[] = {p.n_cap, p.items_cap, p.ncell_cap, p.Tmax, m->mnR, m->mnA, m->mb_desc, m->mb_force, m->ch_force,
                         m->eval_per_bead ? 1 : 0, m->precision, m->MBT, (int)sizeof(real)};
     put(ints, sizeof ints);
     const size_t sm[] = {p.smem_desc, p.smem_force, p.smem_nbr, p.off_reqs, p.off_items, p.off_models};
@@ -934,13 +935,24 @@ int autotune_plan(nep_model* m, const Plan& p, double* force_d)
     TuneEvents ev;
     for (cudaEvent_t& x : ev.e) NEP_CUDA(cudaEventCreate(&x));
     cudaEvent_t e0 = ev.e[0], em = ev.e[1], e1 = ev.e[2];
-    // (descriptor, force) blocks per SM; every variant of each kernel appears
-    const int pairs[3][2] = {{2, 3}, {3, 4}, {3, 5}};
-    float best_d[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f}, best_f[6] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
-    const int keep_d = m->mb_desc, keep_f = m->mb_force;
-    auto trial = [&](int c, bool timed) -> int {
-        m->mb_desc = pairs[c][0];
-        m->mb_force = pairs[c][1];
+    // variants: the descriptor kernel at 2 or 3 blocks per SM; the radial kernel at
+    // 3, 4 or 5 blocks per SM, each with walk groups of 4 or 8 neighbour entries.
+    // Each trial runs one descriptor and one radial variant; every radial variant
+    // appears once per round and each descriptor variant three times.
+    struct Trial {
+        int md, mf, ch;
+    };
+    const Trial trials[6] = {{2, 3, 4}, {3, 3, 8}, {2, 4, 4}, {3, 4, 8}, {2, 5, 4}, {3, 5, 8}};
+    const Trial trials2[6] = {{3, 3, 4}, {2, 3, 8}, {3, 4, 4}, {2, 4, 8}, {3, 5, 4}, {2, 5, 8}};
+    float best_d[4] = {1e30f, 1e30f, 1e30f, 1e30f};  // by blocks per SM
+    float best_f[6][9];                              // [blocks per SM][chunk]
+    for (auto& r : best_f)
+        for (float& x : r) x = 1e30f;
+    const int keep_d = m->mb_desc, keep_f = m->mb_force, keep_c = m->ch_force;
+    auto trial = [&](const Trial& t, bool timed) -> int {
+        m->mb_desc = t.md;
+        m->mb_force = t.mf;
+        m->ch_force = t.ch;
         NEP_CUDA(cudaEventRecord(e0, m->cur));
         NEP_TRY(run_evaluate<real>(m, p, force_d, nullptr, nullptr, m->totals.as<double>(), em));
         NEP_CUDA(cudaEventRecord(e1, m->cur));
@@ -949,26 +961,32 @@ int autotune_plan(nep_model* m, const Plan& p, double* force_d)
         float td = 0.f, tf = 0.f;
         NEP_CUDA(cudaEventElapsedTime(&td, e0, em));
         NEP_CUDA(cudaEventElapsedTime(&tf, em, e1));
-        best_d[pairs[c][0]] = std::min(best_d[pairs[c][0]], td);
-        best_f[pairs[c][1]] = std::min(best_f[pairs[c][1]], tf);
+        best_d[t.md] = std::min(best_d[t.md], td);
+        best_f[t.mf][t.ch] = std::min(best_f[t.mf][t.ch], tf);
         return NEP_OK;
     };
     int rc = NEP_OK;
     for (int round = -1; round < 4 && rc == NEP_OK; ++round)  // round -1 warms up
-        for (int c = 0; c < 3 && rc == NEP_OK; ++c) rc = trial(c, round >= 0);
+        for (int c = 0; c < 6 && rc == NEP_OK; ++c) rc = trial((round & 1) ? trials2[c] : trials[c], round >= 0);
     m->mb_desc = keep_d;
     m->mb_force = keep_f;
+    m->ch_force = keep_c;
     if (rc != NEP_OK) return rc;
-    // leave the default (3 blocks) only for a clear win: timed back to back in
-    // isolation the variants can rank a few percent differently than inside an
-    // MD step (measured on 100k-bead water: 4 blocks won here by up to 3-4% and
+    // leave the default (3 blocks, groups of 4) only for a clear win: timed back to
+    // back in isolation the variants can rank a few percent differently than inside
+    // an MD step (measured on 100k-bead water: 4 blocks won here by up to 3-4% and
     // lost 1-2% in the step; where 4 blocks win in the step they win by 7-12%)
     const float margin = 0.95f;
     m->mb_desc = best_d[2] < margin * best_d[3] ? 2 : 3;
-    int bf = 3;
-    for (int v = 4; v <= 5; ++v)
-        if (best_f[v] < margin * best_f[3] && best_f[v] < best_f[bf]) bf = v;
+    int bf = 3, bc = 4;
+    for (int v = 3; v <= 5; ++v)
+        for (int c = 4; c <= 8; c += 4)
+            if (best_f[v][c] < margin * best_f[3][4] && best_f[v][c] < best_f[bf][bc]) {
+                bf = v;
+                bc = c;
+            }
     m->mb_force = bf;
+    m->ch_force = bc;
     return NEP_OK;
 }
 
@@ -1227,6 +1245,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
         put(&th, sizeof th);
         put(&m->mb_desc, sizeof m->mb_desc);
         put(&m->mb_force, sizeof m->mb_force);
+        put(&m->ch_force, sizeof m->ch_force);
         const size_t offs[] = {p.off_reqs, p.off_items, p.off_models};
         put(offs, sizeof offs);
         const void* tptr[] = {m->bussi.p, dr.virial, dr.site, dr.acc, dr.rows};
@@ -1932,7 +1951,7 @@ int nep_virial_correction(double* virial, int n_atoms, int n_beads, double tempe
 }
 
 int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, const double box[3],
-                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force)
+                 const int32_t pbc[3], int mem, void* stream, int* mb_desc, int* mb_force, int* chunk)
 {
     NEP_TRY(validate_common(m, n, types, pos, box, pbc, mem));
     Guard guard(m->device);
@@ -1968,26 +1987,29 @@ int nep_autotune(nep_model* m, int n, const int32_t* types, const double* pos, c
     NEP_TRY(leave(m, stream));
     if (mb_desc) *mb_desc = m->mb_desc;
     if (mb_force) *mb_force = m->mb_force;
+    if (chunk) *chunk = m->ch_force;
     return NEP_OK;
 }
 
-int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force)
+int nep_set_tuning(nep_model* m, int autotune, int mb_desc, int mb_force, int chunk)
 {
     if (!m) return fail(NEP_ERR_ARG, "null model");
-    if ((mb_desc != 2 && mb_desc != 3) || (mb_force < 3 || mb_force > 5))
-        return fail(NEP_ERR_ARG, "kernel variants: descriptor 2 or 3, force 3, 4 or 5");
+    if ((mb_desc != 2 && mb_desc != 3) || (mb_force < 3 || mb_force > 5) || (chunk != 4 && chunk != 8))
+        return fail(NEP_ERR_ARG, "kernel variants: descriptor 2 or 3, force 3, 4 or 5, chunk 4 or 8");
     m->autotune = autotune != 0;
     m->mb_desc = mb_desc;
     m->mb_force = mb_force;
+    m->ch_force = chunk;
     m->graph.reset();
     return NEP_OK;
 }
 
-int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force)
+int nep_get_tuning(nep_model* m, int* mb_desc, int* mb_force, int* chunk)
 {
     if (!m) return fail(NEP_ERR_ARG, "null model");
     if (mb_desc) *mb_desc = m->mb_desc;
     if (mb_force) *mb_force = m->mb_force;
+    if (chunk) *chunk = m->ch_force;
     return NEP_OK;
 }
 
@@ -2349,7 +2371,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.gcounter = counters + 1;  // one group: at most kStaticMaxN / 128 <= 32 work items
     a.totals = totals;
     e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur, nullptr,
-                              m->mb_desc, m->mb_force);
+                              m->mb_desc, m->mb_force, m->ch_force);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("evaluate: ") + cudaGetErrorString(e));
     if (energy_total) NEP_CUDA(cudaMemcpyAsync(energy_total, totals, sizeof(double), cudaMemcpyDeviceToDevice, m->cur));
     if (virial_total)

@@ -217,6 +217,32 @@ __device__ __forceinline__ void walk4(const uint32_t* nl, size_t stride, int cnt
     if (s + 2 < cnt) body(q2);
 }
 
+// walk4 generalised to groups of CH entries (CH = 4 or 8): the next group's
+// entries are loaded while the current group is evaluated, so up to 2 CH entries
+// (and CH pairs' neighbour loads) are in flight per thread.
+template <int CH, typename Body>
+__device__ __forceinline__ void walk_chunk(const uint32_t* nl, size_t stride, int cnt, Body&& body)
+{
+    auto ld = [&](int s) { return s < cnt ? nl[(size_t)s * stride] : 0u; };
+    uint32_t q[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) q[u] = ld(u);
+    int s = 0;
+    for (; s + CH <= cnt; s += CH) {
+        uint32_t cur[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            cur[u] = q[u];
+            q[u] = ld(s + CH + u);
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) body(cur[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < CH - 1; ++u)
+        if (s + u < cnt) body(q[u]);
+}
+
 // walk4 with the entry's position in its group of four passed as the second
 // argument (0..3, a constant after unrolling), so that a body can keep four
 // partial sums: each then grows to a quarter of the total, which cuts the FP32
@@ -1006,7 +1032,7 @@ __device__ __forceinline__ void reduce_totals(double (&v)[10], int item, const W
 //   interleave the four bodies of each walk step.  f_ji is parallel to r_ij, so the
 //   radial terms of W_i are symmetric: with SYM, c.W[0..5] holds xx, yy, zz, xy, xz,
 //   yz of the radial part alone (6 products per pair instead of 9).
-template <typename real, int NR, int KR, bool SYM = false>
+template <typename real, int NR, int KR, bool SYM = false, int CH = 4>
 __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
                                              ForceCtx<real, (KR + 3) & ~3>& c, int s0, int ds)
 {
@@ -1062,9 +1088,9 @@ __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real
     if (T == 1) {
         real ei1[KRP];  // the one partner type's vector
         loadN<real, KRP>(e_i, ei1);
-        walk4(nl, stride, cnt, [&](uint32_t e) { radial_pair(e, ei1); });
+        walk_chunk<CH>(nl, stride, cnt, [&](uint32_t e) { radial_pair(e, ei1); });
     } else {
-        walk4(nl, stride, cnt, [&](uint32_t e) {
+        walk_chunk<CH>(nl, stride, cnt, [&](uint32_t e) {
             real eij[KRP];
             loadN<real, KRP>(e_i + a.rec[e & kJMask].t * KRP, eij);
             radial_pair(e, eij);
@@ -1352,7 +1378,9 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
 // virials), or the thread's angular virial sum (totals only).  The kernel adds the
 // radial part, writes the caller-order FP64 outputs, clears the line for the next
 // evaluation, and reduces E and W in FP64 (Eq. 1, 16).
-template <typename real, int NR, int KR, int MB>
+// MB: resident blocks per SM (a register budget); CH: neighbour entries per walk
+// group (4 or 8), both chosen per configuration by the autotuner.
+template <typename real, int NR, int KR, int MB, int CH>
 __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
 {
     constexpr int KRP = (KR + 3) & ~3;
@@ -1380,7 +1408,7 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
         for (int k = 0; k < 3; ++k) c.F[k] = real(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) c.W[k] = real(0);
-        force_radial<real, NR, KR, true>(a, P, off, c, 0, 1);
+        force_radial<real, NR, KR, true, CH>(a, P, off, c, 0, 1);
         // the radial virial in full (row-major 3 x 3) from its symmetric part
         const real Wr[9] = {c.W[0], c.W[3], c.W[4], c.W[3], c.W[1], c.W[5], c.W[4], c.W[5], c.W[2]};
         ulonglong2* line = reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4);
@@ -1459,10 +1487,13 @@ cudaError_t set_smem_desc(size_t smem)
 template <typename real, int A_, int B_, int C_, int D_, int MB>
 cudaError_t set_smem_force(size_t smem)
 {
-    if constexpr (sizeof(real) == 4)
-        return cudaFuncSetAttribute(k_force_radial<real, A_, C_, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if constexpr (sizeof(real) == 4) {
+        cudaError_t e = cudaFuncSetAttribute(k_force_radial<real, A_, C_, MB, 4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_force_radial<real, A_, C_, MB, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
-    else
+    } else
         return cudaFuncSetAttribute(k_force<real, A_, B_, C_, D_, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem);
 }
@@ -1505,9 +1536,24 @@ cudaError_t launch_descriptor(const EvalArgs<real>& a, int nb, size_t smem, cuda
     }
 }
 
+// The FP32 radial kernel in its (blocks per SM, walk chunk) variant.
+template <typename real, int NR, int KR>
+cudaError_t launch_force_radial(const EvalArgs<real>& a, int nb, size_t smem, cudaStream_t st, int mb, int ch)
+{
+    if (ch == 8) {
+        if (mb == 5) return launch_k(k_force_radial<real, NR, KR, 5, 8>, nb, kBlock, smem, st, a);
+        if (mb == 4) return launch_k(k_force_radial<real, NR, KR, 4, 8>, nb, kBlock, smem, st, a);
+        return launch_k(k_force_radial<real, NR, KR, 3, 8>, nb, kBlock, smem, st, a);
+    }
+    if (mb == 5) return launch_k(k_force_radial<real, NR, KR, 5, 4>, nb, kBlock, smem, st, a);
+    if (mb == 4) return launch_k(k_force_radial<real, NR, KR, 4, 4>, nb, kBlock, smem, st, a);
+    return launch_k(k_force_radial<real, NR, KR, 3, 4>, nb, kBlock, smem, st, a);
+}
+
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int items_cap, size_t smem_desc,
-                            size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force)
+                            size_t smem_force, cudaStream_t st, cudaEvent_t mid, int mb_desc, int mb_force,
+                            int ch_force)
 {
     const int nb = items_cap;
     if constexpr (sizeof(real) == 4) {
@@ -1520,9 +1566,7 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
         if (e != cudaSuccess) return e;                                                                   \
         if (mid && (e = cudaEventRecord(mid, st)) != cudaSuccess) return e;                               \
         if constexpr (sizeof(real) == 4) {                                                                \
-            if (mb_force == 5) return launch_k(k_force_radial<real, a_, c_, 5>, nb, kBlock, smem_force, st, a); \
-            if (mb_force == 4) return launch_k(k_force_radial<real, a_, c_, 4>, nb, kBlock, smem_force, st, a); \
-            return launch_k(k_force_radial<real, a_, c_, 3>, nb, kBlock, smem_force, st, a);           \
+            return launch_force_radial<real, a_, c_>(a, nb, smem_force, st, mb_force, ch_force);          \
         } else {                                                                                          \
             if (mb_force == 3) return launch_k(k_force<real, a_, b_, c_, d_, 3>, nb, kBlock, smem_force, st, a); \
             return launch_k(k_force<real, a_, b_, c_, d_, 2>, nb, kBlock, smem_force, st, a);          \
@@ -1537,7 +1581,7 @@ cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>
     template bool evaluate_shape_supported<real>(int, int, int, int);                                     \
     template cudaError_t evaluate_set_smem<real>(int, int, int, int, size_t, size_t);                     \
     template cudaError_t launch_evaluate<real>(int, int, int, int, const EvalArgs<real>&, int, size_t, size_t, \
-                                               cudaStream_t, cudaEvent_t, int, int);
+                                               cudaStream_t, cudaEvent_t, int, int, int);
 NEP_INSTANTIATE(float)
 NEP_INSTANTIATE(double)
 #undef NEP_INSTANTIATE

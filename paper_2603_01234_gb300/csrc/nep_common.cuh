@@ -299,7 +299,7 @@ cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t 
 template <typename real>
 cudaError_t launch_evaluate(int nR, int nA, int KR, int KA, const EvalArgs<real>& a, int items_cap, size_t smem_desc,
                             size_t smem_force, cudaStream_t st, cudaEvent_t mid = nullptr, int mb_desc = 3,
-                            int mb_force = 2);
+                            int mb_force = 3, int ch_force = 4);
 
 template <typename real>
 bool evaluate_shape_supported(int nR, int nA, int KR, int KA);

@@ -128,24 +128,26 @@ def test_error_paths(nep_lib):
 
 
 def test_kernel_variants_identical_and_autotune(nep_lib):
-    """Register-cap variants compute the same numbers bit for bit; the autotuner picks one."""
+    """Register-cap and walk-chunk variants compute the same numbers bit for bit; the
+    autotuner picks one."""
     model, system = water_model(), inputs.water_box(3000, seed=17)
     m = binding.Model(model, "fp32")
     ref = None
     for md_ in (2, 3):
         for mf in (3, 4, 5):
-            binding.nep_set_tuning(m.h, 0, md_, mf)
-            got = m.compute(system)
-            if ref is None:
-                ref = got
-            else:
-                np.testing.assert_array_equal(got["force"], ref["force"])
-                np.testing.assert_array_equal(got["virial"], ref["virial"])
-                assert got["energy"] == ref["energy"]
-    for bad in ((4, 3), (3, 6), (3, 2), (1, 3)):
+            for ch in (4, 8):
+                binding.nep_set_tuning(m.h, 0, md_, mf, ch)
+                got = m.compute(system)
+                if ref is None:
+                    ref = got
+                else:
+                    np.testing.assert_array_equal(got["force"], ref["force"])
+                    np.testing.assert_array_equal(got["virial"], ref["virial"])
+                    assert got["energy"] == ref["energy"]
+    for bad in ((4, 3, 4), (3, 6, 4), (3, 2, 4), (1, 3, 4), (3, 3, 6), (3, 3, 2)):
         with pytest.raises(binding.NepError):
             binding.nep_set_tuning(m.h, 0, *bad)
-    md_, mf = binding.nep_autotune(m.h, system.types, system.pos, system.box, system.pbc)
-    assert md_ in (2, 3) and mf in (3, 4, 5)
-    assert binding.nep_get_tuning(m.h) == (md_, mf)
+    md_, mf, ch = binding.nep_autotune(m.h, system.types, system.pos, system.box, system.pbc)
+    assert md_ in (2, 3) and mf in (3, 4, 5) and ch in (4, 8)
+    assert binding.nep_get_tuning(m.h) == (md_, mf, ch)
     m.close()
