@@ -9,6 +9,7 @@
 //                and gather the records into cell order
 //   k_neighbors  one thread per particle scans the (2S+1)^3 surrounding cells and
 //                writes the radial (r < r_c^R) and angular (r < r_c^A) lists
+//                (k_neighbors_warp: one warp per particle, for small batches)
 #include "nep_common.cuh"
 
 namespace nep {
@@ -413,12 +414,123 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
     }
 }
 
+// Small batches: one warp per particle.  With few work items the thread-per-particle
+// kernel leaves most SMs idle and each thread's candidate loop (about 500 candidates
+// for water) is the whole kernel's latency.  Here the warp's lanes test 32 of the
+// particle's candidates at a time (consecutive records of one stencil cell, a
+// coalesced load), and ballots compact the accepted ones in candidate order, so the
+// lists are exactly those the thread-per-particle kernel writes.  A block of kBlock
+// threads takes kBlock / 32 particles of one work item.
+constexpr int kNbrWarpParticles = kBlock / 32;
+
+template <typename real>
+__global__ void __launch_bounds__(kBlock) k_neighbors_warp(NeighborArgs<real> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* cut = reinterpret_cast<real*>(smem_raw);  // rcR2[T*T], rcA2[T*T]
+    constexpr int kPerItem = kBlock / kNbrWarpParticles;  // blocks per work item
+    const int item = (int)blockIdx.x / kPerItem;
+    if (item >= a.counts->n_items) return;
+    const WorkItem it = a.items[item];
+    const ReqInfo& q = a.reqs[it.req];
+    const ModelDesc<real> md = a.models[q.model];
+    const int T = md.T, TT = T * T;
+    for (int k = threadIdx.x; k < TT; k += blockDim.x) {
+        cut[k] = md.params[md.off.rcR2 + k];
+        cut[TT + k] = md.params[md.off.rcA2 + k];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int i = it.begin + ((int)blockIdx.x % kPerItem) * kNbrWarpParticles + ((int)threadIdx.x >> 5);
+    if (i >= it.end) return;  // warp-uniform
+    const CellGrid& g = q.g;
+    const PosRec<real> ri = a.rec[i];
+    const int c = a.cell_s[i] - q.cell_base;
+    const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+    const real* cutR = cut + ri.t * T;
+    const real* cutA = cut + TT + ri.t * T;
+    const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
+    const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
+    const uint32_t stride = (uint32_t)a.n, col = (uint32_t)i;
+    int nr = 0, na = 0;  // warp-uniform
+    for (int dz = -g.S[2]; dz <= g.S[2]; ++dz) {
+        int z = cz + dz;
+        if (g.pbc[2]) {
+            while (z < 0) z += ncz;
+            while (z >= ncz) z -= ncz;
+        } else if (z < 0 || z >= ncz) {
+            continue;
+        }
+        for (int dy = -g.S[1]; dy <= g.S[1]; ++dy) {
+            int y = cy + dy;
+            if (g.pbc[1]) {
+                while (y < 0) y += ncy;
+                while (y >= ncy) y -= ncy;
+            } else if (y < 0 || y >= ncy) {
+                continue;
+            }
+            for (int dx = -g.S[0]; dx <= g.S[0]; ++dx) {
+                int x = cx + dx;
+                if (g.pbc[0]) {
+                    while (x < 0) x += ncx;
+                    while (x >= ncx) x -= ncx;
+                } else if (x < 0 || x >= ncx) {
+                    continue;
+                }
+                const int cell = q.cell_base + (z * ncy + y) * ncx + x;
+                const real bx = ri.x - (real)dx * lx, by = ri.y - (real)dy * ly, bz = ri.z - (real)dz * lz;
+                const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
+                const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+                const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
+                for (int k0 = kb; k0 < ke; k0 += 32) {
+                    const int k = k0 + lane;
+                    bool inR = false, inA = false;
+                    if (k < ke) {
+                        const PosRec<real> rj = ldg_rec(a.rec + k);
+                        const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
+                        const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        const bool other = k != self;
+                        inR = (r2 < cutR[rj.t]) & other;
+                        inA = (r2 < cutA[rj.t]) & other;
+                    }
+                    const unsigned mR = __ballot_sync(0xffffffffu, inR), mA = __ballot_sync(0xffffffffu, inA);
+                    const uint32_t ent = (uint32_t)k | code;
+                    const int sR = nr + __popc(mR & below), sA = na + __popc(mA & below);
+                    if (inR && sR < a.mnR) a.nlR[(uint32_t)sR * stride + col] = ent;
+                    if (inA && sA < a.mnA) a.nlA[(uint32_t)sA * stride + col] = ent;
+                    nr += __popc(mR);
+                    na += __popc(mA);
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        a.cntR[i] = nr;
+        a.cntA[i] = na;
+        atomicMax(&a.maxcnt[0], nr);
+        atomicMax(&a.maxcnt[1], na);
+    }
+    if (a.accF && lane < 2) {  // i's fixed-point lines start the evaluation at zero
+        reinterpret_cast<ulonglong2*>(a.accF + (size_t)i * 4)[lane] = make_ulonglong2(0ull, 0ull);
+    }
+    if (a.accW && lane < 6) {
+        reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12)[lane] = make_ulonglong2(0ull, 0ull);
+    }
+}
+
+// Work items up to which the warp-per-particle kernel runs (a batch of at most this
+// many items leaves the thread-per-particle kernel with at most one block per SM).
+constexpr int kNbrWarpMaxItems = 152;
+
 template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st)
 {
-    // the kernel indexes the slot-major lists with 32-bit slot * n + i
+    // the kernels index the slot-major lists with 32-bit slot * n + i
     if ((unsigned long long)(a.mnR > a.mnA ? a.mnR : a.mnA) * (unsigned long long)a.n > (1ull << 32))
         return cudaErrorInvalidValue;
+    if (items_cap <= kNbrWarpMaxItems)
+        return launch_k(k_neighbors_warp<real>, items_cap * (kBlock / kNbrWarpParticles), kBlock, smem, st, a);
     return launch_k(k_neighbors<real>, items_cap, kBlock, smem, st, a);
 }
 

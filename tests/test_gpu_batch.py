@@ -139,3 +139,23 @@ def test_batches_of_one_size_class_share_a_graph(nep_lib):
             np.testing.assert_array_equal(g["virial"], alone["virial"])
     for h in batch_handles + alone_handles:
         h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_small_and_large_batches_build_the_same_lists(nep_lib, precision):
+    """A configuration evaluated alone (a small batch: the warp-per-particle
+    neighbour kernel) and inside a batch of more than 152 work items (the
+    thread-per-particle kernel) gives bitwise equal results: both kernels write the
+    same neighbour lists in the same order."""
+    models = [water_model(), monolayer_model()]
+    handles = [binding.Model(p, precision) for p in models]
+    small = [(0, inputs.water_box(900, seed=71)), (1, inputs.monolayer(4, 3, seed=72))]
+    big = (0, inputs.water_box(20000, seed=73))  # 157 work items on its own
+    got = run_batch([h.h for h in handles], small + [big])
+    for (mi, s), g in zip(small, got):
+        alone = handles[mi].compute(s)
+        assert g["energy"] == alone["energy"]
+        np.testing.assert_array_equal(g["force"], alone["force"])
+        np.testing.assert_array_equal(g["virial"], alone["virial"])
+    for h in handles:
+        h.close()
