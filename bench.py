@@ -771,20 +771,32 @@ def serving_leg(device, n_requests=4096, fractions=(0.25, 0.5, 0.75, 0.9), repea
     and p50/p99 latency under Poisson arrivals at fractions of each form's own
     saturation rate, each load repeated `repeats` times with fresh arrival times
     (median and range reported), for the batched server (`lanes` lanes, admission by
-    the library's workspace bytes) and for one launch sequence per request."""
+    the library's workspace bytes), for the same server with the requests'
+    configurations and results on the GPU (device_resident: no host copies), and for
+    one launch sequence per request."""
+    import torch
+
     from paper_2603_01234_gb300 import serving
 
     m_water = inputs.random_model(n_types=1, hidden=30, rc_radial=8.0, rc_angular=5.0, seed=1)
     m_mono = inputs.random_model(n_types=4, hidden=50, rc_radial=15.0, rc_angular=11.0, seed=2)
     stream = inputs.request_stream(n_requests=n_requests, seed=1004)
+    dev = torch.device("cuda", device)
+    stream_dev = [(mi, inputs.System(pos=torch.from_numpy(np.ascontiguousarray(s.pos)).to(dev),
+                                     types=torch.from_numpy(s.types.astype(np.int32)).to(dev), box=s.box,
+                                     pbc=s.pbc)) for mi, s in stream]
     out = {"requests": n_requests, "particles": int(sum(s.n for _, s in stream)), "repeats_per_load": repeats,
            "workload": "log-uniform 64-4096 beads; water cubes (1 type, H=30, r_c 8/5) and 4-type monolayer "
-                       "patches (H=50, r_c 15/11), 50/50; host buffers"}
+                       "patches (H=50, r_c 15/11), 50/50; host buffers (device_resident: CUDA tensors)"}
     forms = {"batched": dict(lanes=lanes, lane_bytes=2 << 30, max_requests=4096),
+             "batched_device_resident": dict(lanes=lanes, lane_bytes=2 << 30, max_requests=4096,
+                                             device_resident=True),
              "one_launch_per_request": dict(lanes=1, lane_bytes=2 << 30, max_requests=1)}
+    streams = {name: (stream_dev if kw.get("device_resident") else stream) for name, kw in forms.items()}
     sat = {}
     for name, kw in forms.items():
         srv = serving.Server([m_water, m_mono], "fp32", device=device, keep_results=False, **kw)
+        stream = streams[name]
         # warm-up: the whole stream once, so every lane's workspace and staging are
         # sized (steady-state serving) before the timed runs
         warm = [serving.Request(k, mi, s) for k, (mi, s) in enumerate(stream)]
@@ -800,6 +812,7 @@ def serving_leg(device, n_requests=4096, fractions=(0.25, 0.5, 0.75, 0.9), repea
         srv.close()
     for name, kw in forms.items():
         srv = serving.Server([m_water, m_mono], "fp32", device=device, keep_results=False, **kw)
+        stream = streams[name]
         warm = [serving.Request(k, mi, s) for k, (mi, s) in enumerate(stream)]
         srv.serve(warm, np.zeros(len(warm)))
         rate_sat = sat[name].n_requests / sat[name].wall_s  # each form at fractions of its own saturation

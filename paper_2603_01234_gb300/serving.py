@@ -18,6 +18,11 @@ and from the device run at link speed.
 
 With lanes=1 and max_requests=1 the same server evaluates one request per launch
 sequence (the plain, unbatched form).
+
+With device_resident=True the requests' configurations live on the GPU (types and
+positions as torch CUDA tensors) and so do the results: each lane concatenates its
+batch on its own CUDA stream and evaluates it there, and no request data crosses
+the host link.
 """
 from __future__ import annotations
 
@@ -108,8 +113,10 @@ class Staging:
 
 class Server:
     def __init__(self, params_list, precision="fp32", lanes=2, lane_bytes=2 << 30, max_requests=4096, device=0,
-                 keep_results=True, pinned=True):
+                 keep_results=True, pinned=True, device_resident=False):
         self.params_list = params_list
+        self.device = device
+        self.device_resident = device_resident
         self.lanes = []
         for _ in range(lanes):
             self.lanes.append([binding.Model(p, precision, device) for p in params_list])
@@ -151,7 +158,11 @@ class Server:
 
     def _lane(self, handles):
         hs = [m.h for m in handles]
-        staging = Staging(self.pinned)
+        staging = None if self.device_resident else Staging(self.pinned)
+        stream = None
+        if self.device_resident:
+            import torch
+            stream = torch.cuda.Stream(device=self.device)
         try:
             while True:
                 with self._cv:
@@ -160,9 +171,47 @@ class Server:
                     if not self._pending and self._closed:
                         return
                     batch = self._admit()
-                self._run_batch(hs, batch, staging)
+                if self.device_resident:
+                    self._run_batch_device(hs, batch, stream)
+                else:
+                    self._run_batch(hs, batch, staging)
         finally:
-            staging.close()
+            if staging is not None:
+                staging.close()
+
+    def _run_batch_device(self, hs, batch, stream):
+        """A batch of device-resident requests: concatenated on the lane's stream,
+        evaluated there (the call synchronises once), results kept as device views."""
+        import torch
+
+        k = len(batch)
+        req_n = np.array([r.system.n for r in batch], np.int32)
+        n = int(req_n.sum())
+        req_box = np.array([r.system.box for r in batch], np.float64)
+        req_pbc = np.array([r.system.pbc for r in batch], np.int32)
+        dev = torch.device("cuda", self.device)
+        with torch.cuda.stream(stream):
+            types = torch.cat([r.system.types for r in batch])
+            pos = torch.cat([r.system.pos.reshape(-1) for r in batch])
+            e = torch.empty(k, dtype=torch.float64, device=dev)
+            wt = torch.empty(9 * k, dtype=torch.float64, device=dev)
+            F = torch.empty(3 * n, dtype=torch.float64, device=dev)
+            W = torch.empty(9 * n, dtype=torch.float64, device=dev) if self.keep_results else None
+            binding.nep_compute_batch(hs, req_n, [r.model for r in batch], req_box, req_pbc, types, pos, e, wt, None,
+                                      F, W, stream=stream.cuda_stream)
+        t = time.perf_counter()
+        o = 0
+        for q, r in enumerate(batch):
+            r.done = t
+            r.batch_size = k
+            if self.keep_results:
+                nr = r.system.n
+                r.result = {"energy": e[q], "virial_total": wt[9 * q:9 * q + 9], "force": F[3 * o:3 * (o + nr)].view(3, nr),
+                            "virial": W[9 * o:9 * (o + nr)].view(9, nr)}
+                o += nr
+        with self._cv:
+            self.batches += 1
+            self.batch_requests += k
 
     def _run_batch(self, hs, batch, staging):
         k = len(batch)

@@ -30,6 +30,32 @@ def test_served_results_equal_alone(nep_lib):
     srv.close()
 
 
+def test_device_resident_serving_equals_alone(nep_lib):
+    """Requests whose configurations are CUDA tensors are served without host
+    copies; every result (a device tensor) equals the request evaluated alone."""
+    torch = pytest.importorskip("torch")
+    models = [water_model(), monolayer_model()]
+    stream = inputs.request_stream(n_requests=60, seed=64, n_min=64, n_max=1024)
+    dev = torch.device("cuda", 0)
+    reqs = []
+    for k, (m, s) in enumerate(stream):
+        ds = inputs.System(pos=torch.from_numpy(np.ascontiguousarray(s.pos)).to(dev),
+                           types=torch.from_numpy(s.types.astype(np.int32)).to(dev), box=s.box, pbc=s.pbc)
+        reqs.append(serving.Request(k, m, ds))
+    srv = serving.Server(models, "fp32", lanes=2, lane_bytes=64 << 20, device_resident=True)
+    st = srv.serve(reqs, serving.poisson_arrivals(len(reqs), rate=4000.0, seed=65))
+    assert st.n_requests == len(reqs) and st.batches < len(reqs)
+    alone = [binding.Model(p, "fp32") for p in models]
+    for r, (m, s) in zip(reqs, stream):
+        ref = alone[m].compute(s)
+        assert float(r.result["energy"]) == ref["energy"]
+        np.testing.assert_array_equal(r.result["force"].cpu().numpy(), ref["force"])
+        np.testing.assert_array_equal(r.result["virial"].cpu().numpy(), ref["virial"])
+    for m in alone:
+        m.close()
+    srv.close()
+
+
 def test_memory_admission_bounds_batches(nep_lib):
     models = [water_model(), monolayer_model()]
     stream = inputs.request_stream(n_requests=40, seed=63, n_min=200, n_max=800)
