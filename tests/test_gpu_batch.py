@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_2603_01234_gb300 import binding, inputs
-from tests.gpu_common import assert_parity, monolayer_model, water_model
+from tests.gpu_common import assert_parity, monolayer_model, small_systems, water_model
 
 pytestmark = pytest.mark.gpu
 
@@ -159,3 +159,22 @@ def test_small_and_large_batches_build_the_same_lists(nep_lib, precision):
         np.testing.assert_array_equal(g["virial"], alone["virial"])
     for h in handles:
         h.close()
+
+
+@pytest.mark.parametrize("case", [c for c in small_systems()], ids=[c[0] for c in small_systems()])
+def test_thread_and_warp_neighbour_kernels_agree_on_small_systems(nep_lib, case):
+    """Every small parity case (tiny boxes whose stencils repeat cells as images,
+    open axes, several types, the second compiled shape) evaluated alone (a small
+    batch: the warp-per-particle neighbour kernel) equals the same configuration
+    inside a batch of copies spanning more than 152 work items (the thread-per-
+    particle kernel), bitwise."""
+    name, model, system = case
+    h = binding.Model(model, "fp32")
+    copies = -(-153 // -(-system.n // 128))  # enough copies for more than 152 work items
+    got = run_batch([h.h], [(0, system)] * copies)
+    alone = h.compute(system)
+    for g in (got[0], got[-1]):
+        assert g["energy"] == alone["energy"]
+        np.testing.assert_array_equal(g["force"], alone["force"])
+        np.testing.assert_array_equal(g["virial"], alone["virial"])
+    h.close()
