@@ -519,9 +519,11 @@ __global__ void __launch_bounds__(kBlock) k_neighbors_warp(NeighborArgs<real> a)
     }
 }
 
-// Work items up to which the warp-per-particle kernel runs (a batch of at most this
-// many items leaves the thread-per-particle kernel with at most one block per SM).
-constexpr int kNbrWarpMaxItems = 152;
+// Work items up to which the warp-per-particle kernel runs.  Measured on water boxes
+// (neighbour stage, ms): 16 items 0.027 (warp) against 0.084 (thread per particle),
+// 40 items 0.033 / 0.071, 79 items 0.055 / 0.066, 118 items 0.076 / 0.070, 157 items
+// 0.097 / 0.073.
+constexpr int kNbrWarpMaxItems = 96;
 
 template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st)

@@ -144,7 +144,7 @@ def test_batches_of_one_size_class_share_a_graph(nep_lib):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_small_and_large_batches_build_the_same_lists(nep_lib, precision):
     """A configuration evaluated alone (a small batch: the warp-per-particle
-    neighbour kernel) and inside a batch of more than 152 work items (the
+    neighbour kernel) and inside a batch of more than 96 work items (the
     thread-per-particle kernel) gives bitwise equal results: both kernels write the
     same neighbour lists in the same order."""
     models = [water_model(), monolayer_model()]
@@ -166,11 +166,11 @@ def test_thread_and_warp_neighbour_kernels_agree_on_small_systems(nep_lib, case)
     """Every small parity case (tiny boxes whose stencils repeat cells as images,
     open axes, several types, the second compiled shape) evaluated alone (a small
     batch: the warp-per-particle neighbour kernel) equals the same configuration
-    inside a batch of copies spanning more than 152 work items (the thread-per-
+    inside a batch of copies spanning more than 96 work items (the thread-per-
     particle kernel), bitwise."""
     name, model, system = case
     h = binding.Model(model, "fp32")
-    copies = -(-153 // -(-system.n // 128))  # enough copies for more than 152 work items
+    copies = -(-97 // -(-system.n // 128))  # enough copies for more than 96 work items
     got = run_batch([h.h], [(0, system)] * copies)
     alone = h.compute(system)
     for g in (got[0], got[-1]):
