@@ -621,6 +621,7 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     a.partial = m->partial.as<double>();
     a.counter = m->counters.as<unsigned int>() + 2;
     a.gcounter = m->gcounters.as<unsigned int>();
+    a.err = m->flags.as<int>() + 2;
     a.totals = totals;
     if (kick) {
         if (m->T > kMdMaxTypes) return fail(NEP_ERR_ARG, "too many types for MD");
@@ -635,6 +636,15 @@ int run_evaluate(nep_model* m, const Plan& p, double* force, double* virial, dou
     return NEP_OK;
 }
 
+// The error word's bits (see kErrCellList) as a status.
+int status_error(int word)
+{
+    if (word & 1) return fail(NEP_ERR_ARG, "non-finite position");
+    if (word & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+    if (word & kErrCellList) return fail(NEP_ERR_CUDA, "internal error: inconsistent cell list (access skipped)");
+    return NEP_OK;
+}
+
 template <typename real>
 int check_lists(nep_model* m, const Plan& p)
 {
@@ -642,8 +652,7 @@ int check_lists(nep_model* m, const Plan& p)
     for (int attempt = 0; attempt < 3; ++attempt) {
         NEP_CUDA(cudaMemcpyAsync(m->h_flags, m->flags.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
         NEP_CUDA(cudaStreamSynchronize(m->cur));
-        if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
-        if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+        NEP_TRY(status_error(m->h_flags[2]));
         int needR = m->h_flags[0], needA = m->h_flags[1];
         if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
         if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
@@ -780,8 +789,7 @@ int eval_launch(nep_model* m, const Plan& p, const int* types_d, const double* p
 int eval_status(nep_model* m, bool& retry)
 {
     retry = false;
-    if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
-    if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+    NEP_TRY(status_error(m->h_flags[2]));
     const int needR = m->h_flags[0], needA = m->h_flags[1];
     if (needR <= m->mnR && needA <= m->mnA) return NEP_OK;
     if (needR > m->mnR) m->mnR = ((int)(needR * 1.25) + 8 + 7) & ~7;
@@ -1100,6 +1108,7 @@ int inspect_async(nep_model* m, bool wait)
         // a later call on this stream runs after the current work; reset the words there
         NEP_CUDA(cudaMemsetAsync(m->flags.p, 0, 3 * sizeof(int), m->async_stream));
     }
+    if (err & kErrCellList) return status_error(err);
     if (err) return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
     if (grow_now) {
         const bool overflow = needR > m->mnR || needA > m->mnA;
@@ -1290,6 +1299,7 @@ int md_impl(nep_model* m, int n, const int32_t* types, const double* masses, con
                 const int needR = m->h_async[0], needA = m->h_async[1];
                 if (m->h_async[2]) {
                     NEP_CUDA(cudaStreamSynchronize(m->cur));
+                    if (m->h_async[2] & kErrCellList) return status_error(m->h_async[2]);
                     return fail(NEP_ERR_ARG, "non-finite position or bad type during MD");
                 }
                 if (needR > m->mnR || needA > m->mnA) {
@@ -2369,6 +2379,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     a.partial = (double*)(base + L.partial);
     a.counter = counters;
     a.gcounter = counters + 1;  // one group: at most kStaticMaxN / 128 <= 32 work items
+    a.err = flags + 2;
     a.totals = totals;
     e = launch_evaluate<real>(m->nR, m->nA, m->KR, m->KA, a, n_items, m->smem_desc, m->smem_force, m->cur, nullptr,
                               m->mb_desc, m->mb_force, m->ch_force);
@@ -2379,8 +2390,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     // the handle's pinned status buffer (allocated by nep_create) receives the words
     NEP_CUDA(cudaMemcpyAsync(m->h_flags, flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, m->cur));
     NEP_CUDA(cudaStreamSynchronize(m->cur));
-    if (m->h_flags[2] & 1) return fail(NEP_ERR_ARG, "non-finite position");
-    if (m->h_flags[2] & 2) return fail(NEP_ERR_ARG, "particle type out of range");
+    NEP_TRY(status_error(m->h_flags[2]));
     if (m->h_flags[0] > kStaticMNR || m->h_flags[1] > kStaticMNA)
         return fail(NEP_ERR_NEIGHBOR_OVERFLOW, "more neighbours than the static lists hold (256 radial, 128 angular)");
     return NEP_OK;

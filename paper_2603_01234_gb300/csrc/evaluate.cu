@@ -1229,19 +1229,23 @@ __device__ __forceinline__ void force_outputs(const EvalArgs<real>& a, const Req
     const int ui = a.perm[i];
     const int lu = ui - rq.begin;  // index within the request's output blocks
     const real Ui = a.U[i];
-    double* fo = a.force + (size_t)3 * rq.begin + lu;
+    if (lu >= 0 && lu < rq.n) {
+        double* fo = a.force + (size_t)3 * rq.begin + lu;
 #pragma unroll
-    for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
-    if (a.kick_vel) {
-        double F64[3] = {(double)F[0], (double)F[1], (double)F[2]};
-        closing_kick(a, rq, ui, lu, F64);
-    }
-    if (a.virial) {
-        double* vo = a.virial + (size_t)9 * rq.begin + lu;
+        for (int p = 0; p < 3; ++p) fo[(size_t)p * rq.n] = (double)F[p];
+        if (a.kick_vel) {
+            double F64[3] = {(double)F[0], (double)F[1], (double)F[2]};
+            closing_kick(a, rq, ui, lu, F64);
+        }
+        if (a.virial) {
+            double* vo = a.virial + (size_t)9 * rq.begin + lu;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) vo[(size_t)k * rq.n] = (double)W[k];
+            for (int k = 0; k < 9; ++k) vo[(size_t)k * rq.n] = (double)W[k];
+        }
+        if (a.site) a.site[ui] = (double)Ui;
+    } else if (a.err) {  // see kErrCellList
+        atomicOr(a.err, kErrCellList);
     }
-    if (a.site) a.site[ui] = (double)Ui;
     tot[0] = (double)Ui;
 #pragma unroll
     for (int k = 0; k < 9; ++k) tot[1 + k] = (double)W[k];
@@ -1416,15 +1420,19 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
         line[0] = line[1] = make_ulonglong2(0ull, 0ull);
         const int ui = a.perm[i];
         const int lu = ui - rq.begin;
+        const bool out_ok = lu >= 0 && lu < rq.n;  // see kErrCellList
+        if (!out_ok && a.err) atomicOr(a.err, kErrCellList);
         double* fo = a.force + (size_t)3 * rq.begin + lu;
         // F_i: the angular part from the fixed-point line plus the radial part, added in
         // the working precision and widened once (FP64 arithmetic is scarce)
         double Fi[3] = {(double)(fix_value_f(f01.x) + c.F[0]), (double)(fix_value_f(f01.y) + c.F[1]),
                         (double)(fix_value_f(f2x.x) + c.F[2])};
-        fo[0] = Fi[0];
-        fo[rq.n] = Fi[1];
-        fo[(size_t)2 * rq.n] = Fi[2];
-        if (a.kick_vel) closing_kick(a, rq, ui, lu, Fi);
+        if (out_ok) {
+            fo[0] = Fi[0];
+            fo[rq.n] = Fi[1];
+            fo[(size_t)2 * rq.n] = Fi[2];
+            if (a.kick_vel) closing_kick(a, rq, ui, lu, Fi);
+        }
         if (a.virial) {  // W_i: the angular terms its neighbours sent, plus its radial terms
             ulonglong2* wl = reinterpret_cast<ulonglong2*>(a.accW + (size_t)i * 12);
             double* vo = a.virial + (size_t)9 * rq.begin + lu;
@@ -1432,12 +1440,14 @@ __global__ void __launch_bounds__(kBlock, MB) k_force_radial(EvalArgs<real> a)
             for (int q = 0; q < 5; ++q) {
                 const ulonglong2 v = wl[q];
                 wl[q] = make_ulonglong2(0ull, 0ull);
-                vo[(size_t)(2 * q) * rq.n] = (double)(fix_value_f(v.x) + Wr[2 * q]);
-                if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = (double)(fix_value_f(v.y) + Wr[2 * q + 1]);
+                if (out_ok) {
+                    vo[(size_t)(2 * q) * rq.n] = (double)(fix_value_f(v.x) + Wr[2 * q]);
+                    if (2 * q + 1 < 9) vo[(size_t)(2 * q + 1) * rq.n] = (double)(fix_value_f(v.y) + Wr[2 * q + 1]);
+                }
             }
         }
         const real Ui = a.U[i];
-        if (a.site) a.site[ui] = (double)Ui;
+        if (a.site && out_ok) a.site[ui] = (double)Ui;
         tot[0] = (double)Ui;
         // i's contribution to the virial total: its angular sum plus its radial terms,
         // added in the working precision and widened once (FP64 arithmetic is scarce)

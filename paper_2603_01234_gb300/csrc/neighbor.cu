@@ -213,21 +213,37 @@ __global__ void __launch_bounds__(1024) k_scan(const PlanCounts* __restrict__ pc
 }
 
 // Counting-sort scatter (thread per particle, arbitrary order within a cell) and the
-// cell start offsets (thread per cell).
+// cell start offsets (thread per cell).  This kernel and k_cell_rank check the
+// indices they derive from the cell arrays and, should one ever fall outside its
+// array (an internal inconsistency, never an input error), set kErrCellList in the
+// error word and skip the access instead of touching memory out of bounds; every
+// cell start is kept within [0, n], and the neighbour kernels clamp each particle's
+// cell into its grid, so their searches stay inside the arrays too.
 __global__ void __launch_bounds__(kBlock) k_scatter(const PlanCounts* __restrict__ pc, const int* __restrict__ cell_of,
                                                     const int* __restrict__ local, const int* __restrict__ block_off,
                                                     int* __restrict__ fill, int* __restrict__ perm_tmp,
-                                                    int* __restrict__ cell_start)
+                                                    int* __restrict__ cell_start, int* __restrict__ err)
 {
     const int n = pc->n, ncell = pc->ncell;
     const int total = n > ncell + 1 ? n : ncell + 1;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         if (t < n) {
             const int c = cell_of[t];
-            const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
-            perm_tmp[slot] = t;
+            if (c < 0 || c >= ncell) {
+                atomicOr(err, kErrCellList);
+            } else {
+                const int slot = local[c] + block_off[c / kScanItems] + atomicAdd(&fill[c], 1);
+                if (slot < 0 || slot >= n)
+                    atomicOr(err, kErrCellList);
+                else
+                    perm_tmp[slot] = t;
+            }
         }
-        if (t < ncell) cell_start[t] = local[t] + block_off[t / kScanItems];
+        if (t < ncell) {  // kept within [0, n], so that no cell's range leaves the particles
+            const int v = local[t] + block_off[t / kScanItems];
+            if (v < 0 || v > n) atomicOr(err, kErrCellList);
+            cell_start[t] = min(max(v, 0), n);
+        }
         if (t == ncell) cell_start[ncell] = n;
     }
 }
@@ -240,16 +256,28 @@ __global__ void __launch_bounds__(kBlock) k_cell_rank(const PlanCounts* __restri
                                                       const int* __restrict__ cell_start,
                                                       const int* __restrict__ perm_tmp, int* __restrict__ perm,
                                                       int* __restrict__ cell_s, const PosRec<real>* __restrict__ rec,
-                                                      PosRec<real>* __restrict__ rec_s)
+                                                      PosRec<real>* __restrict__ rec_s, int* __restrict__ err)
 {
-    const int n = pc->n;
+    const int n = pc->n, ncell = pc->ncell;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int v = perm_tmp[k];
-        const int c = cell_of[v];
+        const int c = (v >= 0 && v < n) ? cell_of[v] : -1;
+        if (c < 0 || c >= ncell) {
+            atomicOr(err, kErrCellList);
+            continue;
+        }
         const int b = cell_start[c], e = cell_start[c + 1];
+        if (b < 0 || b > e || e > n) {
+            atomicOr(err, kErrCellList);
+            continue;
+        }
         int rank = 0;
         for (int q = b; q < e; ++q) rank += perm_tmp[q] < v;
         const int dst = b + rank;
+        if (dst >= e) {
+            atomicOr(err, kErrCellList);
+            continue;
+        }
         perm[dst] = v;
         cell_s[dst] = c;
         rec_s[dst] = rec[v];
@@ -281,10 +309,10 @@ cudaError_t launch_cell_build(const PlanCounts* counts, int n_cap, int items_cap
         return e;
     const int nt = (n_cap > ncell_cap + 1 ? n_cap : ncell_cap + 1);
     if ((e = launch_k(k_scatter, (nt + kBlock - 1) / kBlock, kBlock, 0, st, counts, cell_of, cell_start_local,
-                        block_off, cell_fill, perm_tmp, cell_start)) != cudaSuccess)
+                        block_off, cell_fill, perm_tmp, cell_start, err)) != cudaSuccess)
         return e;
     return launch_k(k_cell_rank<real>, (n_cap + kBlock - 1) / kBlock, kBlock, 0, st, counts, cell_of, cell_start,
-                      perm_tmp, perm, cell_s, rec_user, rec_sorted);
+                      perm_tmp, perm, cell_s, rec_user, rec_sorted, err);
 }
 
 // One thread per sorted particle i: scan the cells at offsets [-S, S]^3 from i's
@@ -324,7 +352,9 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
     if (i < it.end) {
         const CellGrid& g = q.g;
         const PosRec<real> ri = a.rec[i];
-        const int c = a.cell_s[i] - q.cell_base;
+        // clamped into the request's grid: an out-of-range cell (which k_cell_rank
+        // reports) cannot take the search outside the cell arrays
+        const int c = min(max(a.cell_s[i] - q.cell_base, 0), g.ncell - 1);
         const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
         const real* cutR = cut + ri.t * T;
         const real* cutA = cut + TT + ri.t * T;
@@ -362,7 +392,7 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
                     // j's position relative to i is (r_j + offset) - r_i = r_j - b
                     const real bx = ri.x - (real)dx * lx, by = ri.y - (real)dy * ly, bz = ri.z - (real)dz * lz;
                     const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
-                    const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+                    const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];  // within [0, n] (k_scatter)
                     // i itself (zero offset) is the one candidate at r = 0 to leave out
                     const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
                     // branch-free body: the tests predicate the stores and the counts
@@ -446,7 +476,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors_warp(NeighborArgs<real> a)
     if (i >= it.end) return;  // warp-uniform
     const CellGrid& g = q.g;
     const PosRec<real> ri = a.rec[i];
-    const int c = a.cell_s[i] - q.cell_base;
+    const int c = min(max(a.cell_s[i] - q.cell_base, 0), g.ncell - 1);  // clamped as in k_neighbors
     const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
     const real* cutR = cut + ri.t * T;
     const real* cutA = cut + TT + ri.t * T;
@@ -481,7 +511,7 @@ __global__ void __launch_bounds__(kBlock) k_neighbors_warp(NeighborArgs<real> a)
                 const int cell = q.cell_base + (z * ncy + y) * ncx + x;
                 const real bx = ri.x - (real)dx * lx, by = ri.y - (real)dy * ly, bz = ri.z - (real)dz * lz;
                 const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
-                const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];
+                const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];  // within [0, n] (k_scatter)
                 const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
                 for (int k0 = kb; k0 < ke; k0 += 32) {
                     const int k = k0 + lane;

@@ -221,6 +221,13 @@ struct NeighborArgs {
 // Work items per group of the totals' two-level reduction (see reduce_totals).
 constexpr int kGroup = 32;
 
+// Bits of the error word (flags[2]): 1 a non-finite position, 2 a type out of range
+// (both input errors), kErrCellList an index derived from the cell list that falls
+// outside its array.  The last cannot arise from any input; the kernels that check
+// for it skip the access, so an internal inconsistency fails the call instead of
+// touching memory out of bounds.
+constexpr int kErrCellList = 4;
+
 template <typename real>
 struct EvalArgs {
     int n, mnR, mnA;            // n: the list / array stride (particle capacity)
@@ -253,6 +260,7 @@ struct EvalArgs {
     unsigned int* gcounter;     // [items] last-block counters of the item groups, at each
                                 // group's first item (self-resetting)
     double* totals;             // [requests][10]: E, W[9]
+    int* err = nullptr;         // the error word (kErrCellList on an inconsistent cell list)
     // MD: the step's closing half-kick applied by the output pass as soon as F_i is
     // final, v_i <- half_kick(v_i, kick_half_dt, F_i, kick_im[t_i]), with the same
     // rounding as a separate kick kernel; kick_vel per request [3][n_r] blocks, or

@@ -37,6 +37,29 @@ def test_fp64_trajectory_matches_oracle(nep_lib):
     m.close()
 
 
+def test_fp64_trajectory_with_deferred_kicks_matches_oracle(nep_lib):
+    """A thermo row every 5 steps lets the steps in between defer their closing kick
+    into the next step's opening kernel (and the sampled and last steps apply it in
+    the output pass); the trajectory still equals the oracle's plain velocity-Verlet
+    one."""
+    model = water_model()
+    s, v = state(n=300, seed=13)
+    steps, dt = 20, 2.0
+    f0 = oracle.compute(model, s).force
+    p_ref, v_ref, f_ref, th_ref = oracle.md(model, s, s.pos, v, f0, steps, dt)
+    m = binding.Model(model, "fp64")
+    pos, vel, force = s.pos.copy(), v.copy(), np.zeros_like(s.pos)
+    thermo = np.zeros((steps // 5, 12))
+    binding.nep_md_step(m.h, s.types, s.masses, s.box, s.pbc, pos, vel, force, 0, steps, dt, 5, thermo)
+    np.testing.assert_allclose(pos, p_ref, atol=1e-9)
+    np.testing.assert_allclose(vel, v_ref, atol=1e-11)
+    np.testing.assert_allclose(force, f_ref, atol=1e-9)
+    np.testing.assert_allclose(thermo[:, 1], th_ref[4::5, 0], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(thermo[:, 2], th_ref[4::5, 1], rtol=1e-10, atol=1e-12)
+    np.testing.assert_array_equal(thermo[:, 0], [5, 10, 15, 20])
+    m.close()
+
+
 def test_graph_replay_equals_eager(nep_lib):
     model = water_model()
     s, v = state(n=500, seed=5)
