@@ -613,9 +613,57 @@ __device__ __forceinline__ float fix_value_f(unsigned long long v) { return (flo
 __device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
 __device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
 
+// One block of a sphere-reduced polynomial (layout of sh_reduce): the value and the x and
+// y derivatives of sum_{a+b<=D} c[o(a) + b] x^a y^b, by Horner's scheme in y for each
+// power of x (with the y-derivative) nested in Horner's scheme in x (with the
+// x-derivative).
+template <int D, bool BLOCK_B, typename real>
+__device__ __forceinline__ void red_block(const real* c, real x, real y, real& v, real& vx, real& vy)
+{
+#pragma unroll
+    for (int a = D; a >= 0; --a) {
+        const int o = BLOCK_B ? sh_red_b(a) : sh_red_a(a);
+        real al = c[o + D - a], dal = real(0);
+#pragma unroll
+        for (int b = D - a - 1; b >= 0; --b) {
+            dal = b == D - a - 1 ? al : fma(dal, y, al);
+            al = fma(al, y, c[o + b]);
+        }
+        if (a == D) {
+            v = al;
+            vx = vy = real(0);
+        } else if (a == D - 1) {
+            vx = v;
+            v = fma(v, x, al);
+            vy = dal;
+        } else {
+            vx = fma(vx, x, v);
+            v = fma(v, x, al);
+            vy = fma(vy, x, dal);
+        }
+    }
+}
+
+// Value and gradient at (x, y, z) of the sphere-reduced polynomial c (sh_reduce):
+// P = A + z B, grad P = (A_x + z B_x, A_y + z B_y, B).  On the unit sphere P equals
+// the harmonic sum it was reduced from, and grad P differs from that sum's gradient
+// only along the normal.
+template <typename real>
+__device__ __forceinline__ void sh_red_eval(const real* c, real x, real y, real z, real& v, real& vx, real& vy,
+                                            real& vz)
+{
+    real pa, pax, pay, pb, pbx, pby;
+    red_block<4, false>(c, x, y, pa, pax, pay);
+    red_block<3, true>(c, x, y, pb, pbx, pby);
+    v = fma(z, pb, pa);
+    vx = fma(z, pbx, pax);
+    vy = fma(z, pby, pay);
+    vz = pb;
+}
+
 template <typename real, int NA, int KA, typename Ctx>
 __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
-                                                      const real (&Phi)[NA][24], Ctx& c, bool per_bead);
+                                                      const real (&Psi)[NA][kShRed], Ctx& c, bool per_bead);
 
 template <typename real, int NR, int NA, int KR, int KA, int NET, int MBT, int FUSE>
 __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const WorkItem it, unsigned char* smem_raw);
@@ -885,6 +933,10 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
                     if (k >= 3 && k < 8) v += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
                 A[nn][k] = v;
             }
+        // each P_n = sum_k Phi_nk Y_k in its sphere-reduced form (see sh_red_eval)
+        real Psi[NA][kShRed];
+#pragma unroll
+        for (int nn = 0; nn < NA; ++nn) sh_reduce(A[nn], Psi[nn]);
         ForceCtx<real, KRP> c;
         c.i = i;
         c.T = T;
@@ -897,7 +949,7 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
 #pragma unroll
         for (int k = 0; k < 9; ++k) c.W[k] = real(0);
         const bool per_bead = a.virial != nullptr;
-        force_angular_phi_reg<real, NA, KA>(a, P, off, A, c, per_bead);
+        force_angular_phi_reg<real, NA, KA>(a, P, off, Psi, c, per_bead);
         // F_i's angular part into i's line; the thread's angular virial sum (what
         // the totals use, with or without per-particle virials) as plain stores
         unsigned long long* acc_i = a.accF + (size_t)i * 4;
@@ -1293,16 +1345,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
 // Each ordered angular pair is evaluated once, by the thread of its centre i, from
 // Phi_i alone while it is still in registers: f_ij = dU_i/dr_ij.  F_i gains f_ij
 // in registers; F_j loses it (and W_j gains r_ji (x) f_ij) through the fixed-point
-// atomic adds.  For A = g(r) Y(u) with Y homogeneous of degree l:
-//   dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
-// Summed over the components with G_k = sum_n Phi_nk g_n and dG_k likewise with
-// g_n', Euler's identity for homogeneous polynomials, u . grad Y = l Y, turns the
-// l-weighted sum into a projection:
-//   f_ij = (sum_k dG_k Y_k) u + (ga - (u . ga) u) / r,   ga = sum_k G_k grad Y_k,
-// so no per-component degree factor is needed.
+// atomic adds.  For A = g(r) Y(u), u = r / |r|, the gradient with respect to r is
+//   dA/dr = g' Y(u) u + (g / r) (grad Y(u) - (u . grad Y(u)) u),
+// where grad Y may be the gradient of any function equal to Y on the unit sphere
+// (only its surface part enters).  Summed over the components with
+// P_n = sum_k Phi_nk Y_k:
+//   f_ij = (sum_n g_n' P_n(u)) u + (ga - (u . ga) u) / r,   ga = sum_n g_n grad P_n(u),
+// evaluated from each P_n's sphere-reduced form Psi_n (sh_red_eval).
 template <typename real, int NA, int KA, typename Ctx>
 __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
-                                                      const real (&Phi)[NA][24], Ctx& c, bool per_bead)
+                                                      const real (&Psi)[NA][kShRed], Ctx& c, bool per_bead)
 {
     const int T = c.T, ti = c.ti;
     const int cA = min(a.cntA[c.i], a.mnA);
@@ -1335,23 +1387,16 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
             dg[nn] = s1;
         }
         const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-        const ShMono<real> mono = sh_mono(ux, uy, uz);
         real D = real(0);
         real ga[3] = {real(0), real(0), real(0)};
 #pragma unroll
-        for (int k = 0; k < kNLM; ++k) {
-            real G = real(0), dG = real(0);
-#pragma unroll
-            for (int nn = 0; nn < NA; ++nn) {
-                G += Phi[nn][k] * g[nn];
-                dG += Phi[nn][k] * dg[nn];
-            }
-            real y, gx, gy, gz;
-            sh_val_grad(k, mono, y, gx, gy, gz);
-            D += dG * y;
-            ga[0] += G * gx;
-            ga[1] += G * gy;
-            ga[2] += G * gz;
+        for (int nn = 0; nn < NA; ++nn) {
+            real v, vx, vy, vz;
+            sh_red_eval(Psi[nn], ux, uy, uz, v, vx, vy, vz);
+            D += dg[nn] * v;
+            ga[0] += g[nn] * vx;
+            ga[1] += g[nn] * vy;
+            ga[2] += g[nn] * vz;
         }
         const real sr = D - (ux * ga[0] + uy * ga[1] + uz * ga[2]) * inv_r;
         const real fij[3] = {sr * ux + ga[0] * inv_r, sr * uy + ga[1] * inv_r, sr * uz + ga[2] * inv_r};

@@ -1,6 +1,7 @@
 """Generate sh_poly.cuh: real orthonormal spherical harmonics l = 1..4 as homogeneous
-harmonic polynomials of the unit vector, and the gradient contraction
-sum_lm G_lm grad Y_lm used by the force kernel.
+harmonic polynomials of the unit vector, the gradient contraction
+sum_lm G_lm grad Y_lm used by the force kernels, and the harmonics' sphere-reduced
+form (z^2 = 1 - x^2 - y^2) that the fused FP32 angular forces evaluate.
 
 Run with sympy available:  python gen_sh.py > sh_poly.cuh
 The script checks harmonicity, homogeneity and orthonormality before writing.
@@ -147,7 +148,75 @@ def emit_per_k():
     return "\n".join(out) + "\n"
 
 
+# The sphere-reduced form: with z^2 = 1 - x^2 - y^2 (exact on the unit sphere) every
+# Y_k is A_k(x, y) + z B_k(x, y), deg A_k <= 4, deg B_k <= 3.  Coefficient layout of
+# a 25-entry vector: block A (x^a y^b, a + b <= 4) at red_a(a) + b, then block B
+# (z x^a y^b, a + b <= 3) at red_b(a) + b.
+RED_A = [(a, b) for a in range(5) for b in range(5 - a)]
+RED_B = [(a, b) for a in range(4) for b in range(4 - a)]
+
+
+def reduced(v):
+    """(A coefficients, B coefficients) of the reduced form of polynomial v."""
+    rem = sp.expand(sp.rem(sp.expand(v), z * z - (1 - x * x - y * y), z))
+    p = sp.Poly(rem, x, y, z)
+    assert p.degree(z) <= 1
+    ca = [p.coeff_monomial(x ** a * y ** b) for a, b in RED_A]
+    cb = [p.coeff_monomial(x ** a * y ** b * z) for a, b in RED_B]
+    return ca, cb
+
+
+def check_reduced():
+    """On random points of the sphere the reduced form equals Y_k, and its gradient
+    differs from grad Y_k only along the normal (equal surface gradients)."""
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((3, 200))
+    u /= np.linalg.norm(u, axis=0)
+    for k in KEYS:
+        ca, cb = reduced(Y[k])
+        red = sum(c * x ** a * y ** b for c, (a, b) in zip(ca, RED_A)) + \
+            z * sum(c * x ** a * y ** b for c, (a, b) in zip(cb, RED_B))
+        f = sp.lambdify((x, y, z), Y[k] - red, "numpy")
+        assert np.abs(f(*u) * np.ones(u.shape[1])).max() < 1e-12
+        g = np.array([sp.lambdify((x, y, z), sp.diff(Y[k] - red, w), "numpy")(*u) * np.ones(u.shape[1])
+                      for w in (x, y, z)])
+        tang = g - (g * u).sum(axis=0) * u
+        assert np.abs(tang).max() < 1e-12
+
+
+def emit_reduced():
+    out = []
+    out.append("")
+    out.append("// Sphere-reduced form: with z^2 = 1 - x^2 - y^2 each Y_k equals A_k(x, y) + z B_k(x, y)")
+    out.append("// on the unit sphere, deg A_k <= 4, deg B_k <= 3 (the two forms have equal values and")
+    out.append("// equal surface gradients there).  A 25-entry coefficient vector holds block A")
+    out.append("// (x^a y^b, a + b <= 4) at sh_red_a(a) + b and block B (z x^a y^b, a + b <= 3) at")
+    out.append("// sh_red_b(a) + b.")
+    out.append(f"constexpr int kShRed = {len(RED_A) + len(RED_B)};")
+    out.append("__host__ __device__ constexpr int sh_red_a(int a) { return a * 5 - a * (a - 1) / 2; }")
+    out.append(f"__host__ __device__ constexpr int sh_red_b(int a) {{ return {len(RED_A)} + a * 4 - a * (a - 1) / 2; }}")
+    out.append("")
+    out.append("// psi = sum_k phi[k] (reduced form of Y_k): the reduced coefficients of sum_k phi[k] Y_k")
+    out.append("template <typename real>")
+    out.append("__device__ __forceinline__ void sh_reduce(const real* phi, real* psi)")
+    out.append("{")
+    cols = [reduced(Y[k]) for k in KEYS]
+    for j, (a, b) in enumerate(RED_A + RED_B):
+        blk = 0 if j < len(RED_A) else 1
+        jj = j if blk == 0 else j - len(RED_A)
+        terms = []
+        for i, (ca, cb) in enumerate(cols):
+            cf = (ca if blk == 0 else cb)[jj]
+            if cf != 0:
+                terms.append(f"real({sp.N(cf, 17)}) * phi[{i}]")
+        out.append(f"    psi[{j}] = {' + '.join(terms) if terms else 'real(0)'};")
+    out.append("}")
+    return "\n".join(out) + "\n"
+
+
 if __name__ == "__main__":
     check()
+    check_reduced()
     sys.stdout.write(emit())
     sys.stdout.write(emit_per_k())
+    sys.stdout.write(emit_reduced())

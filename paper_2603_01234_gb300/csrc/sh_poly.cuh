@@ -275,3 +275,43 @@ __device__ __forceinline__ void sh_val_grad(int k, const ShMono<real>& m, real& 
         v = gx = gy = gz = real(0);
     }
 }
+
+// Sphere-reduced form: with z^2 = 1 - x^2 - y^2 each Y_k equals A_k(x, y) + z B_k(x, y)
+// on the unit sphere, deg A_k <= 4, deg B_k <= 3 (the two forms have equal values and
+// equal surface gradients there).  A 25-entry coefficient vector holds block A
+// (x^a y^b, a + b <= 4) at sh_red_a(a) + b and block B (z x^a y^b, a + b <= 3) at
+// sh_red_b(a) + b.
+constexpr int kShRed = 25;
+__host__ __device__ constexpr int sh_red_a(int a) { return a * 5 - a * (a - 1) / 2; }
+__host__ __device__ constexpr int sh_red_b(int a) { return 15 + a * 4 - a * (a - 1) / 2; }
+
+// psi = sum_k phi[k] (reduced form of Y_k): the reduced coefficients of sum_k phi[k] Y_k
+template <typename real>
+__device__ __forceinline__ void sh_reduce(const real* phi, real* psi)
+{
+    psi[0] = real(0.63078313050504001) * phi[5] + real(0.84628437532163443) * phi[19];
+    psi[1] = real(0.48860251190291992) * phi[0] + real(1.8281831978578629) * phi[10];
+    psi[2] = real(-0.94617469575756002) * phi[5] + real(-0.54627421529603954) * phi[7] + real(-4.2314218766081722) * phi[19] + real(-2.8385240872726801) * phi[21];
+    psi[3] = real(-0.59004358992664351) * phi[8] + real(-2.2852289973223287) * phi[10];
+    psi[4] = real(3.7024941420321506) * phi[19] + real(3.3116114351514601) * phi[21] + real(0.62583573544917613) * phi[23];
+    psi[5] = real(0.48860251190291992) * phi[2] + real(1.8281831978578629) * phi[12];
+    psi[6] = real(1.0925484305920791) * phi[3] + real(5.6770481745453601) * phi[17];
+    psi[7] = real(-2.2852289973223287) * phi[12] + real(-1.7701307697799305) * phi[14];
+    psi[8] = real(-2.5033429417967045) * phi[15] + real(-6.6232228703029201) * phi[17];
+    psi[9] = real(-0.94617469575756002) * phi[5] + real(0.54627421529603954) * phi[7] + real(-4.2314218766081722) * phi[19] + real(2.8385240872726801) * phi[21];
+    psi[10] = real(1.7701307697799305) * phi[8] + real(-2.2852289973223287) * phi[10];
+    psi[11] = real(7.4049882840643013) * phi[19] + real(-3.7550144126950568) * phi[23];
+    psi[12] = real(-2.2852289973223287) * phi[12] + real(0.59004358992664351) * phi[14];
+    psi[13] = real(2.5033429417967045) * phi[15] + real(-6.6232228703029201) * phi[17];
+    psi[14] = real(3.7024941420321506) * phi[19] + real(-3.3116114351514601) * phi[21] + real(0.62583573544917613) * phi[23];
+    psi[15] = real(0.48860251190291992) * phi[1] + real(0.74635266518023078) * phi[11];
+    psi[16] = real(1.0925484305920791) * phi[4] + real(2.6761861742291567) * phi[18];
+    psi[17] = real(-1.8658816629505770) * phi[11] + real(-1.4453057213202770) * phi[13];
+    psi[18] = real(-1.7701307697799305) * phi[16] + real(-4.6833258049010242) * phi[18];
+    psi[19] = real(1.0925484305920791) * phi[6] + real(2.6761861742291567) * phi[20];
+    psi[20] = real(2.8906114426405541) * phi[9];
+    psi[21] = real(-4.6833258049010242) * phi[20] + real(-5.3103923093397916) * phi[22];
+    psi[22] = real(-1.8658816629505770) * phi[11] + real(1.4453057213202770) * phi[13];
+    psi[23] = real(5.3103923093397916) * phi[16] + real(-4.6833258049010242) * phi[18];
+    psi[24] = real(-4.6833258049010242) * phi[20] + real(1.7701307697799305) * phi[22];
+}
