@@ -331,7 +331,7 @@ int nep_get_timing(nep_model* m, double* stage_ms, long long* steps);
  * start-up (an MD engine, a serving process) forbid hidden allocations.
  *
  * The scratch is one fixed array in device global memory that is part of the
- * library image: 15,193,856 bytes (about 14.5 MiB), held on every GPU that loads the
+ * library image: 15,456,000 bytes (about 14.7 MiB), held on every GPU that loads the
  * library until the process exits.  Limits of one call: n <= 4096 particles, a
  * model of at most 4 types, a cell grid of at most 32768 cells, at most 256
  * radial and 128 angular neighbours per particle.  Larger inputs are rejected with

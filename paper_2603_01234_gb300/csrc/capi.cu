@@ -432,7 +432,7 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->cntA.ensure(sizeof(int) * n));
     NEP_TRY(m->U.ensure(rs * n));
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
-    if (m->precision == NEP_FP64) NEP_TRY(m->phi.ensure(rs * 24 * phi_pad(m->nA) * (size_t)n));  // FP32 keeps Phi in registers
+    if (m->precision == NEP_FP64) NEP_TRY(m->phi.ensure(rs * kPsiComp * phi_pad(m->nA) * (size_t)n));  // FP32 keeps them in registers
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
     // FP32 form: force lines [n][4] u64, virial lines [n][12] u64, thread virial sums [9][n] float
     if (m->precision != NEP_FP64) NEP_TRY(m->acc.ensure(acc_bytes(n)));
@@ -2116,7 +2116,7 @@ int nep_request_workspace(nep_model* const* models, int n_models, int model, int
     const size_t rs = m->real_size;
     // cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, U, e, force_tmp, partial2
     size_t per_particle = 4 + 4 * rs + 4 + 4 + 4 * rs + 4 + 4 + 4 + rs + rs * Tmax * m->KRP + 24 + 1;
-    if (m->precision == NEP_FP64) per_particle += rs * 24 * phi_pad(m->nA);
+    if (m->precision == NEP_FP64) per_particle += rs * kPsiComp * phi_pad(m->nA);
     else per_particle += acc_bytes(1);            // fixed-point lines, thread virial sums
     per_particle += 4 * (size_t)(mnR + mnA);      // neighbour lists
     per_particle += 4 + 24 + 24 + 72 + 8;          // host-call staging: types, positions, F, W, U
@@ -2230,7 +2230,7 @@ constexpr StaticLayout static_layout(size_t n, size_t ncell, size_t rs, size_t n
     L.cntA = p; p = align256(p + 4 * n);
     L.U = p; p = align256(p + rs * n);
     L.e = p; p = align256(p + rs * ekrp * n);
-    L.phi = p; p = align256(p + rs * 24 * nA * n);
+    L.phi = p; p = align256(p + rs * kPsiComp * nA * n);
     L.force = p; p = align256(p + 8 * 3 * n);
     L.nlR = p; p = align256(p + 4 * (size_t)kStaticMNR * n);
     L.nlA = p; p = align256(p + 4 * (size_t)kStaticMNA * n);

@@ -34,6 +34,7 @@
 #include "nep_common.cuh"
 #include "poly32.cuh"
 #include "sh_poly.cuh"
+static_assert(kShRed == nep::kPsiComp, "the FP64 form's coefficient buffer holds the sphere-reduced form");
 
 namespace nep {
 
@@ -958,23 +959,29 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
 #pragma unroll
         for (int k = 0; k < 9; ++k) a.wsum[(size_t)k * a.n + i] = c.W[k];
     } else {
-        // Phi is stored component-major, [24][n][NAP]: for one component the rows of
+        // The sphere-reduced coefficients of each P_n = sum_k Phi_nk Y_k (sh_reduce),
+        // stored component-major, [kShRed][n][NAP]: for one component the rows of
         // consecutive particles are adjacent, so a warp's row loads are contiguous
         constexpr int NAP = phi_pad(NA);
         real* ph = a.phi + (size_t)i * NAP;
         const size_t kstride = (size_t)a.n * NAP;
 #pragma unroll
-        for (int k = 0; k < kNLM; ++k)
+        for (int nn = 0; nn < NA; ++nn) {
+            real phi[kNLM], psi[kShRed];
 #pragma unroll
-            for (int nn = 0; nn < NAP; ++nn) {
-                real v = real(0);
-                if (nn < NA) {
-                    v = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
-                    if constexpr (MBT == 1)
-                        if (k >= 3 && k < 8) v += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
-                }
-                ph[k * kstride + nn] = v;
+            for (int k = 0; k < kNLM; ++k) {
+                phi[k] = real(2) * dq[NR + (l_of(k) - 1) * NA + nn] * A[nn][k];
+                if constexpr (MBT == 1)
+                    if (k >= 3 && k < 8) phi[k] += dq[NR + 4 * NA + nn] * g4[nn][k - 3];
             }
+            sh_reduce(phi, psi);
+#pragma unroll
+            for (int m = 0; m < kShRed; ++m) ph[m * kstride + nn] = psi[m];
+        }
+#pragma unroll
+        for (int nn = NA; nn < NAP; ++nn)
+#pragma unroll
+            for (int m = 0; m < kShRed; ++m) ph[m * kstride + nn] = real(0);
     }
 }
 
@@ -1150,17 +1157,20 @@ __device__ __forceinline__ void force_radial(const EvalArgs<real>& a, const real
     }
 }
 
-// Angular pairs, harmonic components k in [K0, K1) of every pair.  For
-// A = g(r) Y(u): dA/dr = (g' - l g / r) Y u + (g / r) grad Y; the reverse pair uses
-// Y(-u) = (-1)^l Y(u), so f_ji is the same contraction with Phi_j (-1)^l, negated.
-template <typename real, int NA, int KA, int K0, int K1, typename Ctx>
-__device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
-                                                Ctx& c)
+// Angular pairs in gather form: f_ij from i's reduced coefficients at u and f_ji from
+// j's at -u (the reduced form holds the harmonic sum's values on the whole sphere,
+// so no parity factor is needed):
+//   f_ij = D_i u + (ga_i - (u . ga_i) u) / r,  D_i = sum_n g_n' P_in(u), ga_i = sum_n g_n grad P_in(u),
+// and f_ji likewise at -u with j's coefficients and type-pair functions (see
+// force_angular_phi_reg for the derivation).  F_i += f_ij - f_ji, W_i += r_ij (x) f_ji.
+template <typename real, int NA, int KA, typename Ctx>
+__device__ __forceinline__ void force_angular_red(const EvalArgs<real>& a, const real* P, const ParamLayout& off,
+                                                  Ctx& c)
 {
     const int T = c.T, ti = c.ti;
     constexpr int NAP = phi_pad(NA);
     const size_t kstride = (size_t)a.n * NAP;
-    const real* phi_i = a.phi + (size_t)c.i * NAP;
+    const real* psi_i = a.phi + (size_t)c.i * NAP;
     const int cA = min(a.cntA[c.i], a.mnA);
     NbrWalk<real> wa(a.nlA, a.n, c.i, cA, a.rec);
     for (int s = 0; s < cA; ++s) {
@@ -1212,52 +1222,44 @@ __device__ __forceinline__ void force_angular_k(const EvalArgs<real>& a, const r
             }
         }
         const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
-        const ShMono<real> mono = sh_mono(ux, uy, uz);
-        const real* phi_j = a.phi + (size_t)j * NAP;
-        real si = real(0), sj = real(0);
+        const real* psi_j = a.phi + (size_t)j * NAP;
+        real Di = real(0), Dj = real(0);
         real ga[3] = {real(0), real(0), real(0)}, gb[3] = {real(0), real(0), real(0)};
 #pragma unroll
-        for (int k = K0; k < K1; ++k) {
-            const real lr = real(l_of(k)) * inv_r;
-            real pi_[NA], pj[NA];
-            loadN<real, NA>(phi_i + k * kstride, pi_);
-            loadN<real, NA>(phi_j + k * kstride, pj);
-            real Gi_ = real(0), dGi = real(0), Gj_ = real(0), dGj = real(0);
+        for (int nn = 0; nn < NA; ++nn) {
+            real ci[kShRed], cj[kShRed];
 #pragma unroll
-            for (int nn = 0; nn < NA; ++nn) {
-                Gi_ += pi_[nn] * gi[nn];
-                dGi += pi_[nn] * dgi[nn];
-                Gj_ += pj[nn] * gj[nn];
-                dGj += pj[nn] * dgj[nn];
+            for (int m = 0; m < kShRed; ++m) {
+                ci[m] = psi_i[m * kstride + nn];
+                cj[m] = psi_j[m * kstride + nn];
             }
-            if (l_of(k) & 1) {
-                Gj_ = -Gj_;
-                dGj = -dGj;
-            }
-            real y, gx, gy, gz;
-            sh_val_grad(k, mono, y, gx, gy, gz);
-            si += (dGi - lr * Gi_) * y;
-            sj += (dGj - lr * Gj_) * y;
-            const real Gs = Gi_ + Gj_;
-            ga[0] += Gs * gx;
-            ga[1] += Gs * gy;
-            ga[2] += Gs * gz;
-            gb[0] += Gj_ * gx;
-            gb[1] += Gj_ * gy;
-            gb[2] += Gj_ * gz;
+            real v, vx, vy, vz;
+            sh_red_eval(ci, ux, uy, uz, v, vx, vy, vz);
+            Di += dgi[nn] * v;
+            ga[0] += gi[nn] * vx;
+            ga[1] += gi[nn] * vy;
+            ga[2] += gi[nn] * vz;
+            sh_red_eval(cj, -ux, -uy, -uz, v, vx, vy, vz);
+            Dj += dgj[nn] * v;
+            gb[0] += gj[nn] * vx;
+            gb[1] += gj[nn] * vy;
+            gb[2] += gj[nn] * vz;
         }
-        // F_i += f_ij - f_ji;  -f_ji = sj u + gb / r;  W_i += r_ij (x) f_ji
+        // f_ij, and f_ji with u' = -u: f_ji = -Dj u + (gb - (u . gb) u) / r
+        const real pa = (ux * ga[0] + uy * ga[1] + uz * ga[2]) * inv_r;
+        const real pb = (ux * gb[0] + uy * gb[1] + uz * gb[2]) * inv_r;
         const real u[3] = {ux, uy, uz}, d[3] = {dx, dy, dz};
-        real vj[3];
+        real fji[3];
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            c.F[p] += (si + sj) * u[p] + ga[p] * inv_r;
-            vj[p] = sj * u[p] + gb[p] * inv_r;
+            const real fij = (Di - pa) * u[p] + ga[p] * inv_r;
+            fji[p] = (-Dj - pb) * u[p] + gb[p] * inv_r;
+            c.F[p] += fij - fji[p];
         }
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) c.W[3 * p + q] -= d[p] * vj[q];
+            for (int q = 0; q < 3; ++q) c.W[3 * p + q] += d[p] * fji[q];
     }
 }
 
@@ -1335,7 +1337,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(Ev
 #pragma unroll
         for (int k = 0; k < 9; ++k) c.W[k] = real(0);
         force_radial<real, NR, KR>(a, P, off, c, 0, 1);
-        force_angular_k<real, NA, KA, 0, kNLM>(a, P, off, c);
+        force_angular_red<real, NA, KA>(a, P, off, c);
         force_outputs(a, rq, i, c.F, c.W, tot);
     }
     reduce_totals<kBlock>(tot, w, it, rq, a.partial, a.gcounter, a.counter, a.totals);

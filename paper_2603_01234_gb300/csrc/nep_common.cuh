@@ -63,6 +63,9 @@ __host__ __device__ constexpr int coef_stride(int n, int k) { return (n * k) | 1
 // Row length of Phi_i per harmonic component: n_A padded to a multiple of 4 so that
 // every row starts on a 16-byte boundary (vector loads).
 __host__ __device__ constexpr int phi_pad(int nA) { return (nA + 3) & ~3; }
+// Coefficients per n of the sphere-reduced form of sum_k dU/dA_nk Y_k, the FP64 form's
+// per-particle angular adjoint (the kShRed of sh_poly.cuh)
+constexpr int kPsiComp = 25;
 
 __host__ __device__ inline uint32_t pack_entry(int j, int dx, int dy, int dz)
 {
@@ -243,7 +246,8 @@ struct EvalArgs {
     real* U;                    // [n] sorted site energies
     real* e;                    // [n][e_stride] radial gradient folded into the basis
     int e_stride;               // Tmax * KRP
-    real* phi;                  // FP64 form: [24][n][phi_pad(NA)] dU/dA_nlm, zero padded
+    real* phi;                  // FP64 form: [kPsiComp][n][phi_pad(NA)] the sphere-reduced coefficients of
+                                // P_n = sum_lm (dU/dA_nlm) Y_lm, zero padded
     int net_bf16;               // 1: the hidden layer's products in BF16 on tensor cores
     int many_body;              // 1: the four- and five-body descriptors follow the three-body ones
     const int* perm;            // sorted slot -> caller index
