@@ -796,17 +796,21 @@ __device__ __forceinline__ void descriptor_item(const EvalArgs<real>& a, const W
         const int tp = ti * T + rj.t;
         real f[KA];
         basis<real, KA>(r, P[off.rcAi + tp], P[off.rcAl + tp], f);
-        real c[NA * KA];
-        load_coef(P + off.cA + tp * coef_stride(NA, KA), T == 1, c);
         real Y[kNLM];
         sh_eval(dx * inv_r, dy * inv_r, dz * inv_r, Y);
+        const real* crow = P + off.cA + tp * coef_stride(NA, KA);
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) {
+            // one coefficient row at a time: the fence keeps the compiler from loading
+            // every row up front, which would hold 32 more registers across the sums
+            real cr[KA];
+            load_coef(crow + nn * KA, T == 1 && KA % 4 == 0, cr);
             real g = real(0);
 #pragma unroll
-            for (int k = 0; k < KA; ++k) g += c[nn * KA + k] * f[k];
+            for (int k = 0; k < KA; ++k) g += cr[k] * f[k];
 #pragma unroll
             for (int k = 0; k < kNLM; ++k) A[nn][k] += g * Y[k];
+            asm volatile("" ::: "memory");
         }
     }
     // q_nl (Eq. 4)
@@ -1375,18 +1379,20 @@ __device__ __forceinline__ void force_angular_phi_reg(const EvalArgs<real>& a, c
         real f[KA], df[KA];
         basis_d<real, KA>(r, P[off.rcAi + tij], P[off.rcAl + tij], f, df);
         real g[NA], dg[NA];
-        real cc[NA * KA];
-        load_coef(P + off.cA + tij * coef_stride(NA, KA), T == 1, cc);
+        const real* crow = P + off.cA + tij * coef_stride(NA, KA);
 #pragma unroll
         for (int nn = 0; nn < NA; ++nn) {
+            real cr[KA];  // one row at a time (see the angular moments)
+            load_coef(crow + nn * KA, T == 1 && KA % 4 == 0, cr);
             real s0 = real(0), s1 = real(0);
 #pragma unroll
             for (int k = 0; k < KA; ++k) {
-                s0 += cc[nn * KA + k] * f[k];
-                s1 += cc[nn * KA + k] * df[k];
+                s0 += cr[k] * f[k];
+                s1 += cr[k] * df[k];
             }
             g[nn] = s0;
             dg[nn] = s1;
+            asm volatile("" ::: "memory");
         }
         const real ux = dx * inv_r, uy = dy * inv_r, uz = dz * inv_r;
         real D = real(0);
