@@ -1,7 +1,7 @@
 """Generate sh_poly.cuh: real orthonormal spherical harmonics l = 1..4 as homogeneous
-harmonic polynomials of the unit vector, the gradient contraction
-sum_lm G_lm grad Y_lm used by the force kernels, and the harmonics' sphere-reduced
-form (z^2 = 1 - x^2 - y^2) that the fused FP32 angular forces evaluate.
+harmonic polynomials of the unit vector (the angular moments of Eq. 5), and the
+harmonics' sphere-reduced form (z^2 = 1 - x^2 - y^2) from which the angular pair
+forces are evaluated.
 
 Run with sympy available:  python gen_sh.py > sh_poly.cuh
 The script checks harmonicity, homogeneity and orthonormality before writing.
@@ -88,63 +88,6 @@ def emit():
     for i, k in enumerate(KEYS):
         out.append(f"    Y[{i}] = {c(Y[k])};")
     out.append("}")
-    out.append("")
-    out.append("// ga += sum_k A[k] grad Y_k,  gb += sum_k B[k] grad Y_k  (gradient of the polynomial)")
-    out.append("template <typename real>")
-    out.append("__device__ __forceinline__ void sh_grad2(real x, real y, real z, const real* A, const real* B,")
-    out.append("                                         real* ga, real* gb)")
-    out.append("{")
-    out.append(MONO)
-    for i, k in enumerate(KEYS):
-        for d, var in enumerate((x, y, z)):
-            e = sp.diff(Y[k], var)
-            if e == 0:
-                continue
-            out.append(f"    {{ const real t = {c(e)}; ga[{d}] += A[{i}] * t; gb[{d}] += B[{i}] * t; }}")
-    out.append("}")
-    return "\n".join(out) + "\n"
-
-
-def emit_per_k():
-    """sh_val_grad(k, ...): Y_k and the three components of grad Y_k for one k, from
-    precomputed monomials; k is a compile-time constant after loop unrolling."""
-    out = []
-    out.append("")
-    out.append("template <typename real>")
-    out.append("struct ShMono {")
-    out.append("    real x, y, z, x2, y2, z2, x3, y3, z3, x4, y4, z4;")
-    out.append("};")
-    out.append("")
-    out.append("template <typename real>")
-    out.append("__device__ __forceinline__ ShMono<real> sh_mono(real x, real y, real z)")
-    out.append("{")
-    out.append("    ShMono<real> m;")
-    out.append("    m.x = x; m.y = y; m.z = z;")
-    out.append("    m.x2 = x * x; m.y2 = y * y; m.z2 = z * z;")
-    out.append("    m.x3 = m.x2 * x; m.y3 = m.y2 * y; m.z3 = m.z2 * z;")
-    out.append("    m.x4 = m.x2 * m.x2; m.y4 = m.y2 * m.y2; m.z4 = m.z2 * m.z2;")
-    out.append("    return m;")
-    out.append("}")
-    out.append("")
-    out.append("template <typename real>")
-    out.append("__device__ __forceinline__ void sh_val_grad(int k, const ShMono<real>& m, real& v, real& gx, real& gy,")
-    out.append("                                            real& gz)")
-    out.append("{")
-    out.append("    const real x = m.x, y = m.y, z = m.z, x2 = m.x2, y2 = m.y2, z2 = m.z2;")
-    out.append("    const real x3 = m.x3, y3 = m.y3, z3 = m.z3, x4 = m.x4, y4 = m.y4, z4 = m.z4;")
-    out.append("    (void)x3; (void)y3; (void)z3; (void)x4; (void)y4; (void)z4;")
-    out.append("    switch (k) {")
-    for i, key in enumerate(KEYS):
-        out.append(f"    case {i}:")
-        out.append(f"        v = {c(Y[key])};")
-        for name, var in (("gx", x), ("gy", y), ("gz", z)):
-            e = sp.diff(Y[key], var)
-            out.append(f"        {name} = {c(e) if e != 0 else 'real(0)'};")
-        out.append("        break;")
-    out.append("    default:")
-    out.append("        v = gx = gy = gz = real(0);")
-    out.append("    }")
-    out.append("}")
     return "\n".join(out) + "\n"
 
 
@@ -218,5 +161,4 @@ if __name__ == "__main__":
     check()
     check_reduced()
     sys.stdout.write(emit())
-    sys.stdout.write(emit_per_k())
     sys.stdout.write(emit_reduced())
