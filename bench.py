@@ -44,10 +44,10 @@ FLOPS_PEAK_NOTE = "FP32 ALU peak = SMs (device-reported) x 128 FP32 lanes x 2 fl
 # DRAM bytes per particle of one launch of the dominant kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the evaluate.cu
 # source it was taken on, otherwise the bench reports traffic as null.
-KERNEL_TRAFFIC = {"evaluate_cu_sha1": "b4516465c282779279d062179403eecb0ca1f4b8", "bytes_per_particle": 455.2,
+KERNEL_TRAFFIC = {"evaluate_cu_sha1": "707309d819336f66ce5784500ab0b5f81ee79978", "bytes_per_particle": 454.1,
                   "kernel": "descriptor_network",
                   "capture": "ncu --set full, k_descriptor (descriptor + network + angular forces), 100,000-bead water, "
-                             "variants 3,3,4, cold caches: 45.31 MB read + 0.21 MB written per launch"}
+                             "variants 3,3,4, cold caches: 45.31 MB read + 0.09 MB written per launch"}
 
 
 N_BEADS = 100_000
