@@ -21,14 +21,15 @@
 //         radial pairs in gather form (f_ij and f_ji from i's and j's stored
 //         gradient vectors), adds the accumulated angular part and writes the
 //         outputs
-//   FP64  k_descriptor stores Phi; k_force takes both kinds of pair in gather
-//         form, no atomics
+//   FP64  k_descriptor stores the sphere-reduced form of Phi; k_force takes both
+//         kinds of pair in gather form, no atomics
 //
-// Angular pair gradient.  For A = g(r) Y(u), u = r/|r|, with Y a homogeneous
-// polynomial of degree l:  dA/dr = (g' - l g / r) Y u + (g / r) grad Y(u).
-// For the reverse pair, u -> -u gives Y(-u) = (-1)^l Y(u) and
-// grad Y(-u) = (-1)^(l-1) grad Y(u), so f_ji is the same contraction with
-// Phi_j scaled by (-1)^l, negated.
+// Angular pair gradient.  For A = g(r) Y(u), u = r/|r|:
+//   dA/dr = g' Y(u) u + (g / r) (grad Y(u) - (u . grad Y(u)) u),
+// in which only the surface gradient of Y enters.  Both forms evaluate
+// P_n = sum_lm Phi_nlm Y_lm through its sphere-reduced polynomial (sh_reduce,
+// sh_red_eval), which has P_n's values and surface gradients on the unit sphere;
+// the reverse pair is the same evaluation at -u with j's coefficients.
 #include <cuda_bf16.h>
 
 #include "nep_common.cuh"
@@ -1314,8 +1315,8 @@ template <typename real, int NR, int NA, int KR, int KA, int MB>
 __global__ void __launch_bounds__(kBlock, sizeof(real) == 4 ? MB : 1) k_force(EvalArgs<real> a)
 {
     constexpr int KRP = (KR + 3) & ~3;
-    // i's Phi is read through L1 (a shared-memory copy would take L1 capacity that
-    // the neighbours' records and gradients need more)
+    // i's reduced coefficients are read through L1 (a shared-memory copy would take L1
+    // capacity that the neighbours' records and gradients need more)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* P = reinterpret_cast<real*>(smem_raw);
     const int w = blockIdx.x;  // one work item per block (see k_descriptor)
@@ -1524,8 +1525,8 @@ bool evaluate_shape_supported(int nR, int nA, int KR, int KA)
 }
 
 // FP32: the descriptor kernel with the angular forces fused (K1) and the radial /
-// output kernel (K2); FP64: the descriptor kernel storing Phi and the gather-form
-// force kernel.  Variants: resident blocks per SM (register caps), and for the
+// output kernel (K2); FP64: the descriptor kernel storing the reduced form of Phi and
+// the gather-form force kernel.  Variants: resident blocks per SM (register caps), and for the
 // descriptor the network form (NET) and the many-body terms (MBT).
 template <typename real, int A_, int B_, int C_, int D_, int MB>
 cudaError_t set_smem_desc(size_t smem)
