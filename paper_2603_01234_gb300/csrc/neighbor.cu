@@ -393,28 +393,42 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
                     const real bx = ri.x - (real)dx * lx, by = ri.y - (real)dy * ly, bz = ri.z - (real)dz * lz;
                     const uint32_t code = ((uint32_t)((dx + 2) | ((dy + 2) << 3) | ((dz + 2) << 6))) << kJBits;
                     const int kb = a.cell_start[cell], ke = a.cell_start[cell + 1];  // within [0, n] (k_scatter)
-                    // i itself (zero offset) is the one candidate at r = 0 to leave out
-                    const int self = (dx == 0 && dy == 0 && dz == 0) ? i : -1;
-                    // branch-free body: the tests predicate the stores and the counts
-                    auto candidate = [&](int k, const PosRec<real>& rj, real cR2, real cA2) {
+                    // branch-free body: the tests predicate the stores and the counts; i
+                    // itself (zero offset) is the one candidate at r = 0 to leave out, tested
+                    // for only in i's own cell (center: the same for every lane of the warp)
+                    auto candidate = [&](int k, const PosRec<real>& rj, real cR2, real cA2, bool center) {
                         const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
                         const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                         const uint32_t ent = (uint32_t)k | code;
-                        const bool other = k != self;
+                        const bool other = !center || k != i;
                         const bool inR = (r2 < cR2) & other, inA = (r2 < cA2) & other;
                         if (inR & (nr < a.mnR)) a.nlR[(uint32_t)nr * stride + col] = ent;
                         if (inA & (na < a.mnA)) a.nlA[(uint32_t)na * stride + col] = ent;
                         nr += inR;
                         na += inA;
                     };
+                    const bool center = dx == 0 && dy == 0 && dz == 0;
                     if (T == 1) {  // one pair type: deeper unrolling (measured faster)
+                        if (center) {
 #pragma unroll 4
-                        for (int k = kb; k < ke; ++k) candidate(k, ldg_rec(a.rec + k), cR1, cA1);
+                            for (int k = kb; k < ke; ++k) candidate(k, ldg_rec(a.rec + k), cR1, cA1, true);
+                        } else {
+#pragma unroll 4
+                            for (int k = kb; k < ke; ++k) candidate(k, ldg_rec(a.rec + k), cR1, cA1, false);
+                        }
                     } else {  // per-type cutoffs from shared memory (unroll 4 measured slower)
+                        if (center) {
 #pragma unroll 2
-                        for (int k = kb; k < ke; ++k) {
-                            const PosRec<real> rj = ldg_rec(a.rec + k);
-                            candidate(k, rj, cutR[rj.t], cutA[rj.t]);
+                            for (int k = kb; k < ke; ++k) {
+                                const PosRec<real> rj = ldg_rec(a.rec + k);
+                                candidate(k, rj, cutR[rj.t], cutA[rj.t], true);
+                            }
+                        } else {
+#pragma unroll 2
+                            for (int k = kb; k < ke; ++k) {
+                                const PosRec<real> rj = ldg_rec(a.rec + k);
+                                candidate(k, rj, cutR[rj.t], cutA[rj.t], false);
+                            }
                         }
                     }
                 }
