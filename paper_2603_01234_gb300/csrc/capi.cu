@@ -225,6 +225,7 @@ struct nep_model {
     CellGrid md_grid{};
     // workspace
     Buf cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, nlR, nlA, U, e, phi;
+    Buf rec32;  // FP64 form: FP32 copies of the sorted records (neighbour screening)
     Buf cell_count, cell_local, block_off, cell_fill, cell_start;
     Buf partial, partial2, counters, gcounters, totals, flags, thermo, sample_index;
     Buf acc;  // FP32 form: force and virial fixed-point lines, thread virial sums (acc_bytes)
@@ -339,7 +340,7 @@ void set_models(Plan& p, nep_model* const* models, int n_models)
         p.Tmax = std::max(p.Tmax, models[k]->T);
         p.smem_desc = std::max(p.smem_desc, models[k]->smem_desc);
         p.smem_force = std::max(p.smem_force, models[k]->smem_force);
-        p.smem_nbr = std::max(p.smem_nbr, 2 * sizeof(real) * models[k]->T * models[k]->T);
+        p.smem_nbr = std::max(p.smem_nbr, neighbor_smem<real>(models[k]->T));
     }
 }
 
@@ -433,6 +434,7 @@ int ensure_particles(nep_model* m, int n, int n_items, int n_req, int Tmax)
     NEP_TRY(m->U.ensure(rs * n));
     NEP_TRY(m->e.ensure(rs * Tmax * m->KRP * (size_t)n));
     if (m->precision == NEP_FP64) NEP_TRY(m->phi.ensure(rs * kPsiComp * phi_pad(m->nA) * (size_t)n));  // FP32 keeps them in registers
+    if (m->precision == NEP_FP64) NEP_TRY(m->rec32.ensure(16 * (size_t)n));
     NEP_TRY(m->partial.ensure(sizeof(double) * 10 * (size_t)n_items));
     // FP32 form: force lines [n][4] u64, virial lines [n][12] u64, thread virial sums [9][n] float
     if (m->precision != NEP_FP64) NEP_TRY(m->acc.ensure(acc_bytes(n)));
@@ -573,6 +575,7 @@ int run_neighbors(nep_model* m, const Plan& p)
     // lines only when this evaluation returns per-particle virials)
     a.accF = m->precision != NEP_FP64 ? acc_force(m->acc.p) : nullptr;
     a.accW = m->precision != NEP_FP64 && m->eval_per_bead ? acc_virial(m->acc.p, p.n_cap) : nullptr;
+    a.rec32 = m->precision == NEP_FP64 ? m->rec32.as<PosRec<float>>() : nullptr;
     if ((uint64_t)std::max(a.mnR, a.mnA) * (uint64_t)a.n > (1ull << 32))
         return fail(NEP_ERR_ARG, "neighbour lists beyond 2^32 entries (capacity x particles)");
     cudaError_t e = launch_neighbors<real>(a, p.items_cap, p.smem_nbr, m->cur);
@@ -700,7 +703,7 @@ int eval_pipeline(nep_model* m, const Plan& p, const int* types_d, const double*
 void put_workspace_ptrs(std::vector<unsigned char>& key, const nep_model* m)
 {
     const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
-                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
+                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->rec32, &m->cell_count, &m->cell_local,
                          &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters,
                          &m->gcounters, &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->acc, &m->bussi,
                          &m->md_virial, &m->md_site, &m->heat, &m->heat_rows};
@@ -1560,7 +1563,7 @@ int nep_destroy(nep_model* m)
     m->eval_graphs.clear();
     m->timer.destroy();
     Buf* bufs[] = {&m->params, &m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
-                   &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local, &m->block_off,
+                   &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->rec32, &m->cell_count, &m->cell_local, &m->block_off,
                    &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters, &m->gcounters,
                    &m->totals, &m->flags,
                    &m->thermo, &m->sample_index, &m->types_d, &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d,
@@ -2116,7 +2119,7 @@ int nep_request_workspace(nep_model* const* models, int n_models, int model, int
     const size_t rs = m->real_size;
     // cell_of, rec_user, perm_tmp, perm, rec_s, cell_s, cntR, cntA, U, e, force_tmp, partial2
     size_t per_particle = 4 + 4 * rs + 4 + 4 + 4 * rs + 4 + 4 + 4 + rs + rs * Tmax * m->KRP + 24 + 1;
-    if (m->precision == NEP_FP64) per_particle += rs * kPsiComp * phi_pad(m->nA);
+    if (m->precision == NEP_FP64) per_particle += rs * kPsiComp * phi_pad(m->nA) + 16;
     else per_particle += acc_bytes(1);            // fixed-point lines, thread virial sums
     per_particle += 4 * (size_t)(mnR + mnA);      // neighbour lists
     per_particle += 4 + 24 + 24 + 72 + 8;          // host-call staging: types, positions, F, W, U
@@ -2132,7 +2135,7 @@ int nep_workspace_bytes(nep_model* m, size_t* bytes)
 {
     if (!m || !bytes) return fail(NEP_ERR_ARG, "bad argument");
     const Buf* bufs[] = {&m->cell_of, &m->rec_user, &m->perm_tmp, &m->perm, &m->rec_s, &m->cell_s, &m->cntR,
-                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->cell_count, &m->cell_local,
+                         &m->cntA, &m->nlR, &m->nlA, &m->U, &m->e, &m->phi, &m->rec32, &m->cell_count, &m->cell_local,
                          &m->block_off, &m->cell_fill, &m->cell_start, &m->partial, &m->partial2, &m->counters,
                          &m->gcounters, &m->totals, &m->flags, &m->thermo, &m->sample_index, &m->types_d,
                          &m->pos_d, &m->vel_d, &m->force_d, &m->virial_d, &m->site_d, &m->force_tmp,
@@ -2348,7 +2351,7 @@ int compute_static_impl(nep_model* m, int n, const int32_t* types, const double*
     na.maxcnt = flags;
     na.accF = sizeof(real) == 4 ? acc_force(base + L.acc) : nullptr;
     na.accW = sizeof(real) == 4 && virial ? acc_virial(base + L.acc, n) : nullptr;
-    e = launch_neighbors<real>(na, n_items, 2 * sizeof(real) * m->T * m->T, m->cur);
+    e = launch_neighbors<real>(na, n_items, neighbor_smem<real>(m->T), m->cur);
     if (e != cudaSuccess) return fail(NEP_ERR_CUDA, std::string("neighbours: ") + cudaGetErrorString(e));
     EvalArgs<real> a;
     a.n = n;

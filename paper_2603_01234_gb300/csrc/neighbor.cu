@@ -346,6 +346,25 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
         cut[k] = md.params[md.off.rcR2 + k];
         cut[TT + k] = md.params[md.off.rcA2 + k];
     }
+    // FP64 with a.rec32: each distance test is screened in FP32 first.  The FP32 pair
+    // vector, from FP32 copies of the cell-relative coordinates (|x_j| < len,
+    // |b| < 3 len), is within d = sqrt(3) len 2^-20 of the exact one, so its r^2 is
+    // within eps = 2 r_c d + d^2 + 3 2^-24 r_c^2 of the exact r^2 near the cutoff.
+    // Below r_c^2 - 4 eps the FP64 test would accept, above r_c^2 + 4 eps it would
+    // reject; in between the FP64 test decides, so the lists are the FP64 ones.
+    constexpr bool kScreen = sizeof(real) == 8;
+    const bool screened = kScreen && a.rec32 != nullptr;
+    float* screen = reinterpret_cast<float*>(cut + 2 * TT);  // [2 TT][lo, hi]
+    if (screened) {
+        const double lmax = fmax(q.g.len[0], fmax(q.g.len[1], q.g.len[2]));
+        const double d = 1.7320508075688772 * lmax * 0x1p-20;
+        for (int k = threadIdx.x; k < 2 * TT; k += blockDim.x) {
+            const double c2 = k < TT ? (double)md.params[md.off.rcR2 + k] : (double)md.params[md.off.rcA2 + k - TT];
+            const double eps = 4.0 * (2.0 * sqrt(c2) * d + d * d + 3.0 * 0x1p-24 * c2);
+            screen[2 * k] = __double2float_rd(c2 - eps);
+            screen[2 * k + 1] = __double2float_ru(c2 + eps);
+        }
+    }
     __syncthreads();
     const int i = it.begin + threadIdx.x;
     int nr = 0, na = 0;
@@ -359,6 +378,11 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
         const real* cutR = cut + ri.t * T;
         const real* cutA = cut + TT + ri.t * T;
         const real cR1 = cutR[0], cA1 = cutA[0];  // the one pair type of a one-type model
+        const float* scrR = screen + 2 * (ri.t * T);  // FP64 screening bounds of i's row
+        const float* scrA = screen + 2 * (TT + ri.t * T);
+        PosRec<float> ri32 = {};
+        if (screened) ri32 = a.rec32[i];
+        const float lxf = (float)g.len[0], lyf = (float)g.len[1], lzf = (float)g.len[2];
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
         const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
         // slot s of particle i's list is entry s * n + i (slot-major); the launcher
@@ -407,8 +431,42 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
                         nr += inR;
                         na += inA;
                     };
+                    // FP64 screened: the FP32 record decides outside the band around
+                    // each cutoff, the FP64 record inside it
+                    const float bxf = ri32.x - (float)dx * lxf, byf = ri32.y - (float)dy * lyf,
+                                bzf = ri32.z - (float)dz * lzf;
+                    auto screened_candidate = [&](int k, bool center) {
+                        const PosRec<float> rf = ldg_rec(a.rec32 + k);
+                        const float fx = rf.x - bxf, fy = rf.y - byf, fz = rf.z - bzf;
+                        const float r2f = fx * fx + fy * fy + fz * fz;
+                        const int tp = 2 * rf.t;
+                        bool inR = r2f < scrR[tp], inA = r2f < scrA[tp];
+                        if ((r2f < scrR[tp + 1]) != inR || (r2f < scrA[tp + 1]) != inA) {
+                            const PosRec<real> rj = ldg_rec(a.rec + k);
+                            const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
+                            const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            inR = r2 < cutR[rf.t];
+                            inA = r2 < cutA[rf.t];
+                        }
+                        const uint32_t ent = (uint32_t)k | code;
+                        const bool other = !center || k != i;
+                        inR &= other;
+                        inA &= other;
+                        if (inR & (nr < a.mnR)) a.nlR[(uint32_t)nr * stride + col] = ent;
+                        if (inA & (na < a.mnA)) a.nlA[(uint32_t)na * stride + col] = ent;
+                        nr += inR;
+                        na += inA;
+                    };
                     const bool center = dx == 0 && dy == 0 && dz == 0;
-                    if (T == 1) {  // one pair type: deeper unrolling (measured faster)
+                    if (kScreen && screened) {
+                        if (center) {
+#pragma unroll 2
+                            for (int k = kb; k < ke; ++k) screened_candidate(k, true);
+                        } else {
+#pragma unroll 2
+                            for (int k = kb; k < ke; ++k) screened_candidate(k, false);
+                        }
+                    } else if (T == 1) {  // one pair type: deeper unrolling (measured faster)
                         if (center) {
 #pragma unroll 4
                             for (int k = kb; k < ke; ++k) candidate(k, ldg_rec(a.rec + k), cR1, cA1, true);
@@ -569,14 +627,39 @@ __global__ void __launch_bounds__(kBlock) k_neighbors_warp(NeighborArgs<real> a)
 // 0.097 / 0.073.
 constexpr int kNbrWarpMaxItems = 96;
 
+// FP64 form: the FP32 copies of the sorted records that screen the distance tests
+// of k_neighbors (one conversion per particle instead of per candidate)
+__global__ void __launch_bounds__(kBlock) k_round_records(const PlanCounts* __restrict__ pc,
+                                                          const PosRec<double>* __restrict__ rec,
+                                                          PosRec<float>* __restrict__ rec32)
+{
+    const int n = pc->n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const PosRec<double> r = rec[k];
+        PosRec<float> f;
+        f.x = (float)r.x;
+        f.y = (float)r.y;
+        f.z = (float)r.z;
+        f.t = r.t;
+        rec32[k] = f;
+    }
+}
+
 template <typename real>
 cudaError_t launch_neighbors(const NeighborArgs<real>& a, int items_cap, size_t smem, cudaStream_t st)
 {
     // the kernels index the slot-major lists with 32-bit slot * n + i
     if ((unsigned long long)(a.mnR > a.mnA ? a.mnR : a.mnA) * (unsigned long long)a.n > (1ull << 32))
         return cudaErrorInvalidValue;
-    if (items_cap <= kNbrWarpMaxItems)
+    if (items_cap <= kNbrWarpMaxItems)  // FP64 here tests every pair in FP64
         return launch_k(k_neighbors_warp<real>, items_cap * (kBlock / kNbrWarpParticles), kBlock, smem, st, a);
+    if constexpr (sizeof(real) == 8) {
+        if (a.rec32) {
+            const cudaError_t e = launch_k(k_round_records, (a.n + kBlock - 1) / kBlock, kBlock, 0, st, a.counts, a.rec,
+                                           a.rec32);
+            if (e != cudaSuccess) return e;
+        }
+    }
     return launch_k(k_neighbors<real>, items_cap, kBlock, smem, st, a);
 }
 

@@ -219,7 +219,17 @@ struct NeighborArgs {
     int* maxcnt;                // [2]
     unsigned long long* accF;   // FP32 form: [n][4] fixed-point force lines, zeroed here for the evaluation (or null)
     unsigned long long* accW;   // FP32 form with per-particle virials: [n][12] fixed-point virial lines (or null)
+    PosRec<float>* rec32 = nullptr;  // FP64 form: FP32 copies of rec, written here to screen the
+                                     // distance tests (null: every test in FP64)
 };
+
+// Shared memory of the neighbour kernels for T types: the squared cutoffs of both
+// lists, and in FP64 their FP32 screening bounds (see neighbors_item).
+template <typename real>
+constexpr size_t neighbor_smem(int T)
+{
+    return (2 * sizeof(real) + (sizeof(real) == 8 ? 4 * sizeof(float) : 0)) * (size_t)T * (size_t)T;
+}
 
 // Work items per group of the totals' two-level reduction (see reduce_totals).
 constexpr int kGroup = 32;
