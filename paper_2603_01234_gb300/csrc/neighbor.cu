@@ -346,18 +346,20 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
         cut[k] = md.params[md.off.rcR2 + k];
         cut[TT + k] = md.params[md.off.rcA2 + k];
     }
-    // FP64 with a.rec32: each distance test is screened in FP32 first.  The FP32 pair
-    // vector, from FP32 copies of the cell-relative coordinates (|x_j| < len,
-    // |b| < 3 len), is within d = sqrt(3) len 2^-20 of the exact one, so its r^2 is
-    // within eps = 2 r_c d + d^2 + 3 2^-24 r_c^2 of the exact r^2 near the cutoff.
-    // Below r_c^2 - 4 eps the FP64 test would accept, above r_c^2 + 4 eps it would
-    // reject; in between the FP64 test decides, so the lists are the FP64 ones.
+    // FP64 with a.rec32: each distance test is screened in FP32 first.  For
+    // cell-relative coordinates of i and j within 2 len of their cell's origin on
+    // every axis (all of them except particles outside the box on an open axis), the
+    // FP32 pair vector is within d = sqrt(3) len 2^-19 of the exact one, so its r^2
+    // is within eps = 2 r_c d + d^2 + 3 2^-24 r_c^2 of the exact r^2 wherever it
+    // could decide.  Below r_c^2 - 4 eps the FP64 test would accept, above
+    // r_c^2 + 4 eps it would reject; in between, and for any particle beyond the
+    // 2 len range, the FP64 test decides, so the lists are exactly the FP64 ones.
     constexpr bool kScreen = sizeof(real) == 8;
     const bool screened = kScreen && a.rec32 != nullptr;
     float* screen = reinterpret_cast<float*>(cut + 2 * TT);  // [2 TT][lo, hi]
     if (screened) {
         const double lmax = fmax(q.g.len[0], fmax(q.g.len[1], q.g.len[2]));
-        const double d = 1.7320508075688772 * lmax * 0x1p-20;
+        const double d = 1.7320508075688772 * lmax * 0x1p-19;
         for (int k = threadIdx.x; k < 2 * TT; k += blockDim.x) {
             const double c2 = k < TT ? (double)md.params[md.off.rcR2 + k] : (double)md.params[md.off.rcA2 + k - TT];
             const double eps = 4.0 * (2.0 * sqrt(c2) * d + d * d + 3.0 * 0x1p-24 * c2);
@@ -383,6 +385,10 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
         PosRec<float> ri32 = {};
         if (screened) ri32 = a.rec32[i];
         const float lxf = (float)g.len[0], lyf = (float)g.len[1], lzf = (float)g.len[2];
+        // the range the screening bound covers (2 len per axis, rounded down)
+        const float mx = 1.99f * lxf, my = 1.99f * lyf, mz = 1.99f * lzf;
+        const bool i_screened =
+            screened && fabsf(ri32.x) <= mx && fabsf(ri32.y) <= my && fabsf(ri32.z) <= mz;
         const real lx = (real)g.len[0], ly = (real)g.len[1], lz = (real)g.len[2];
         const int ncx = g.nc[0], ncy = g.nc[1], ncz = g.nc[2];
         // slot s of particle i's list is entry s * n + i (slot-major); the launcher
@@ -441,7 +447,8 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
                         const float r2f = fx * fx + fy * fy + fz * fz;
                         const int tp = 2 * rf.t;
                         bool inR = r2f < scrR[tp], inA = r2f < scrA[tp];
-                        if ((r2f < scrR[tp + 1]) != inR || (r2f < scrA[tp + 1]) != inA) {
+                        const bool j_far = !(fabsf(rf.x) <= mx && fabsf(rf.y) <= my && fabsf(rf.z) <= mz);
+                        if (j_far || (r2f < scrR[tp + 1]) != inR || (r2f < scrA[tp + 1]) != inA) {
                             const PosRec<real> rj = ldg_rec(a.rec + k);
                             const real ddx = rj.x - bx, ddy = rj.y - by, ddz = rj.z - bz;
                             const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
@@ -458,7 +465,7 @@ __device__ __forceinline__ void neighbors_item(const NeighborArgs<real>& a, cons
                         na += inA;
                     };
                     const bool center = dx == 0 && dy == 0 && dz == 0;
-                    if (kScreen && screened) {
+                    if (kScreen && i_screened) {
                         if (center) {
 #pragma unroll 2
                             for (int k = kb; k < ke; ++k) screened_candidate(k, true);
